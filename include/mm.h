@@ -1,0 +1,179 @@
+/*
+ * mm.h -- C ABI of libmm, a GB300 (sm_103a) library for the dense product
+ * C = A B of an N x P by a P x M double matrix in the methods surveyed by
+ * I. Hedtke, "Methods of Matrix Multiplication" (arXiv:1106.1347), plus an
+ * FP64-accurate product emulated from BF16 slices on the tcgen05 tensor cores.
+ *
+ * Common conventions (every entry point below):
+ *  - Matrices are row-major double with leading dimensions in elements:
+ *    element (i, j) of A is A[i * lda + j].  Required: lda >= max(1, P),
+ *    ldb >= max(1, M), ldc >= max(1, M); N, P, M >= 0.
+ *  - Matrix, vector and workspace pointers are DEVICE pointers on the current
+ *    CUDA device, owned by the caller.  The library never allocates, frees or
+ *    retains caller memory; scratch space is passed in as (ws, ws_bytes) and
+ *    sized by the matching *_workspace_bytes query.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    enqueue work and return without synchronising.
+ *  - C is overwritten (C := A B; there is no alpha/beta).  N == 0 or M == 0 is
+ *    a no-op; P == 0 writes C = 0.
+ *  - Argument errors are detected before anything is enqueued and return
+ *    MM_ERR_ARG (negative sizes, short leading dimensions, NULL pointers with
+ *    non-zero extent, C overlapping A or B by address range, short workspace).
+ *    A CUDA launch failure returns MM_ERR_CUDA.  mm_last_error() then holds a
+ *    thread-local message.
+ *  - Inputs must be finite; Inf/NaN propagate in method-dependent ways.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MM_OK = 0,
+    MM_ERR_ARG = -1,         /* bad argument; nothing was enqueued */
+    MM_ERR_CUDA = -2,        /* a CUDA call or launch failed */
+    MM_ERR_NOMEM = -3,       /* a fixed capacity was exceeded */
+    MM_ERR_UNSUPPORTED = -4, /* valid request this build does not implement */
+    MM_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    MM_ERR_WORKSPACE = -6    /* ws_bytes smaller than the *_workspace_bytes query */
+} mm_status;
+
+typedef enum { MM_SLICE_BF16 = 0, MM_SLICE_FP8E4M3 = 1 } mm_slice_kind;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int mm_version(void);
+
+/* Thread-local text of the last non-OK status returned on this thread. */
+const char *mm_last_error(void);
+
+/* Reads and clears the device status word the kernels set when a bounded wait
+ * gives up (current device).  Synchronises `stream`.  Returns MM_OK or
+ * MM_ERR_TIMEOUT; *code_out (may be NULL) receives the raw word. */
+int mm_device_status(void *stream, int32_t *code_out);
+
+/*
+ * Section "NormInf": *out = ||A||_inf = max_i sum_j |A_ij| for the N x P
+ * matrix A.  Each row is summed in index order, so the value is bit-identical
+ * to a sequential CPU evaluation.  `out` is one device double; N == 0 or
+ * P == 0 gives 0.
+ */
+int mm_norm_inf(int64_t N, int64_t P, const double *A, int64_t lda, double *out, void *stream);
+
+/*
+ * Section "The naive method" (NaivStandard): C_ij = sum_k A_ik B_kj.
+ * Runs on the FP64 tensor-core MMA (mma.sync m8n8k4 f64); exact on integer
+ * inputs whose partial sums stay below 2^53, otherwise within the usual
+ * inner-product rounding error (products are fused, order is blocked).
+ */
+int mm_naive(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+             double *C, int64_t ldc, void *stream);
+
+/*
+ * Section "NaivKahan": the naive product with every dot product summed by the
+ * paper's compensated update (err = err + x; t = sum + err;
+ * err = (sum - t) + err; sum = t) over x = RN(A_ik B_kj), k in order.
+ * Bit-identical to the sequential CPU evaluation.
+ */
+int mm_kahan(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+             double *C, int64_t ldc, void *stream);
+
+/*
+ * Section "WinogradOriginal": with gamma = floor(P/2),
+ *   y_i = sum_j A_i,2j-1 A_i,2j,  z_k = sum_j B_2j-1,k B_2j,k   (1-based),
+ *   C_ik = (sum_j (A_i,2j-1 + B_2j,k)(A_i,2j + B_2j-1,k) - y_i) - z_k
+ * plus A_i,P B_P,k when P is odd.  y and z are bit-identical to a sequential
+ * evaluation; the paired sum uses FMA.  Workspace: mm_winograd_workspace_bytes.
+ */
+size_t mm_winograd_workspace_bytes(int64_t N, int64_t P, int64_t M);
+int mm_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                double *C, int64_t ldc, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Section "WinogradScaled": lambda = the smallest integer with
+ * 1/2 <= 4^lambda ||A||_inf / ||B||_inf <= 2 (0 if either norm is 0), computed
+ * on the device from bit-exact norms (no host synchronisation), then
+ * Winograd's form on 2^lambda A and 2^-lambda B; the power-of-two scalings
+ * (MultiplyWithScalar) are applied while operand tiles are staged.
+ * `lambda_out` is an optional device int32 (NULL to skip).
+ */
+size_t mm_winograd_scaled_workspace_bytes(int64_t N, int64_t P, int64_t M);
+int mm_winograd_scaled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                       int64_t ldb, double *C, int64_t ldc, int32_t *lambda_out, void *ws, size_t ws_bytes,
+                       void *stream);
+
+/*
+ * Sections "StrassenNaiv" and "StrassenWinograd": recursive block products
+ * with 7 half-size products per level (H1..H7; 18 additions for Strassen's
+ * form, 15 for Winograd's variant), down to a base product on the FP64
+ * tensor-core MMA.
+ *   cutoff == 0: the paper's rule -- X = max{N,P,M}, k = max(0, floor(log2 X) - 4),
+ *                embed in Y x Y with Y = (floor(X/2^k) + 1) 2^k, recurse k levels;
+ *   cutoff  > 0: the smallest depth at which every padded dimension / 2^depth
+ *                is <= cutoff, each dimension padded to a multiple of 2^depth;
+ *   cutoff == -1: depth chosen by the library's tuned table.
+ * Padding is virtual (out-of-range elements read as zero).  The innermost
+ * level forms the operand sums (Plus/Minus) while staging tiles and adds
+ * +-H_i into the C quadrants in the paper's left-to-right order in its
+ * epilogue; outer levels keep their operand sums and H_i in the workspace.
+ * Depth is limited to 10 levels and 7^(depth-1) <= 2401 innermost launches;
+ * deeper requests return MM_ERR_UNSUPPORTED.
+ */
+size_t mm_strassen_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t cutoff);
+int mm_strassen(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                double *C, int64_t ldc, int32_t cutoff, void *ws, size_t ws_bytes, void *stream);
+size_t mm_strassen_winograd_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t cutoff);
+int mm_strassen_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                         int64_t ldb, double *C, int64_t ldc, int32_t cutoff, void *ws, size_t ws_bytes,
+                         void *stream);
+
+/*
+ * FP64-accurate product emulated from slices (not in the paper; its
+ * per-row/per-column power-of-two scaling generalises section
+ * "WinogradScaled").  Each row i of A is scaled by 2^-e_i (e_i the frexp
+ * exponent of max_k |A_ik|), rounded to an integer V_ik with beta*s - 1 bits
+ * and cut into s balanced base-2^beta digits stored as BF16 (beta = 7); B is
+ * split per column the same way.  The slice pairs (sigma, tau) with
+ * sigma + tau <= s - 1 are multiplied on tcgen05 with FP32 accumulation in
+ * TMEM, drained every K-chunk while every partial sum is an exact integer
+ * below 2^24, accumulated exactly in integers, and rounded once to double
+ * with the 2^(e_i + f_j) scaling.  The result equals, bit for bit,
+ * RN(sum of the kept digit products) scaled -- see the oracle's definition.
+ *   kind:     MM_SLICE_BF16 (MM_SLICE_FP8E4M3 returns MM_ERR_UNSUPPORTED);
+ *   nslices:  1..8, or 0 to choose from `tier`;
+ *   tier:     target ||C - AB||_inf / (||A||_inf ||B||_inf) when nslices == 0
+ *             (<= 1e-14 selects 8 slices).
+ * Requires N, M >= 1 and P <= 2^20 (larger P returns MM_ERR_UNSUPPORTED).
+ */
+size_t mm_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t kind, int32_t nslices, double tier);
+int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                double *C, int64_t ldc, int32_t kind, int32_t nslices, double tier, void *ws, size_t ws_bytes,
+                void *stream);
+
+/* Slice count mm_emulated uses for (kind, nslices, tier). */
+int mm_emulated_slices(int32_t kind, int32_t nslices, double tier);
+
+/*
+ * Kernel-level timing (measurement support).  While enabled, every kernel the
+ * library launches on any stream is bracketed by CUDA events recorded on that
+ * stream.  mm_profile_read synchronises those events and fills up to `cap`
+ * entries (kernel name, launch count, total milliseconds), returning the
+ * number of distinct kernels; it also resets the record.
+ */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} mm_kernel_stat;
+int mm_profile_enable(int on);
+int mm_profile_read(mm_kernel_stat *out, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MM_H */

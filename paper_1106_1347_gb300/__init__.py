@@ -1,0 +1,185 @@
+"""GB300 (sm_103a) library for the methods of Hedtke, "Methods of Matrix
+Multiplication" (arXiv:1106.1347), with an FP64-accurate product emulated from
+BF16 slices on the tcgen05 tensor cores.
+
+Thin PyTorch binding over the libmm C ABI (include/mm.h): tensors provide
+device memory and the current CUDA stream; every step runs in libmm's kernels.
+Operands are 2-D float64 CUDA tensors with unit column stride (row-major with
+leading dimension = stride(0)); anything else is made contiguous first.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from ._native import KernelStat, MMError, check, lib
+
+__all__ = ["naive", "kahan", "winograd", "winograd_scaled", "strassen", "strassen_winograd", "norm_inf",
+           "emulated", "emulated_slices", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
+           "SLICE_FP8E4M3"]
+
+SLICE_BF16 = 0
+SLICE_FP8E4M3 = 1
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _mat(x, name):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != torch.float64 or x.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D float64 tensor")
+    if x.stride(1) != 1 or (x.shape[0] > 1 and x.stride(0) < max(1, x.shape[1])):
+        x = x.contiguous()
+    return x
+
+
+def _ld(x):
+    return max(1, x.stride(0) if x.shape[0] > 1 else x.shape[1])
+
+
+def _stream(device):
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _prep(a, b, out):
+    torch = _torch()
+    a, b = _mat(a, "A"), _mat(b, "B")
+    if a.shape[1] != b.shape[0]:
+        raise ValueError(f"inner dimensions differ: {tuple(a.shape)} x {tuple(b.shape)}")
+    if a.device != b.device:
+        raise ValueError("A and B are on different devices")
+    n, p = a.shape
+    m = b.shape[1]
+    if out is None:
+        out = torch.empty((n, m), dtype=torch.float64, device=a.device)
+    else:
+        if out.shape != (n, m) or out.dtype != torch.float64 or out.device != a.device or out.stride(1) != 1:
+            raise ValueError("out must be an N x M float64 tensor with unit column stride on A's device")
+    return a, b, out, n, p, m
+
+
+def _ptr(x):
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _ws(nbytes, device):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def _gemm_args(a, b, c, n, p, m):
+    return [n, p, m, _ptr(a), _ld(a), _ptr(b), _ld(b), _ptr(c), _ld(c)]
+
+
+def naive(a, b, out=None):
+    """Section "The naive method": C = A B on the FP64 tensor-core MMA."""
+    a, b, c, n, p, m = _prep(a, b, out)
+    check("mm_naive", lib().mm_naive(*_gemm_args(a, b, c, n, p, m), _stream(a.device)))
+    return c
+
+
+def kahan(a, b, out=None):
+    """Section "NaivKahan": naive product with the paper's compensated sum."""
+    a, b, c, n, p, m = _prep(a, b, out)
+    check("mm_kahan", lib().mm_kahan(*_gemm_args(a, b, c, n, p, m), _stream(a.device)))
+    return c
+
+
+def winograd(a, b, out=None):
+    """Section "WinogradOriginal"."""
+    a, b, c, n, p, m = _prep(a, b, out)
+    need = lib().mm_winograd_workspace_bytes(n, p, m)
+    ws = _ws(need, a.device)
+    check("mm_winograd", lib().mm_winograd(*_gemm_args(a, b, c, n, p, m), _ptr(ws), need, _stream(a.device)))
+    return c
+
+
+def winograd_scaled(a, b, out=None, return_lambda=False):
+    """Section "WinogradScaled".  With return_lambda=True returns (C, lambda tensor)."""
+    torch = _torch()
+    a, b, c, n, p, m = _prep(a, b, out)
+    need = lib().mm_winograd_scaled_workspace_bytes(n, p, m)
+    ws = _ws(need, a.device)
+    lam = torch.zeros(1, dtype=torch.int32, device=a.device)
+    check("mm_winograd_scaled", lib().mm_winograd_scaled(*_gemm_args(a, b, c, n, p, m), _ptr(lam), _ptr(ws), need,
+                                                         _stream(a.device)))
+    return (c, lam) if return_lambda else c
+
+
+def _strassen(name, a, b, cutoff, out):
+    a, b, c, n, p, m = _prep(a, b, out)
+    need = getattr(lib(), name + "_workspace_bytes")(n, p, m, int(cutoff))
+    ws = _ws(need, a.device)
+    check(name, getattr(lib(), name)(*_gemm_args(a, b, c, n, p, m), int(cutoff), _ptr(ws), need,
+                                     _stream(a.device)))
+    return c
+
+
+def strassen(a, b, cutoff=-1, out=None):
+    """Section "StrassenNaiv".  cutoff: 0 = the paper's rule, >0 = base size, -1 = tuned."""
+    return _strassen("mm_strassen", a, b, cutoff, out)
+
+
+def strassen_winograd(a, b, cutoff=-1, out=None):
+    """Section "StrassenWinograd"."""
+    return _strassen("mm_strassen_winograd", a, b, cutoff, out)
+
+
+def norm_inf(a):
+    """Section "NormInf": returns a 0-d float64 device tensor."""
+    torch = _torch()
+    a = _mat(a, "A")
+    out = torch.empty((), dtype=torch.float64, device=a.device)
+    check("mm_norm_inf", lib().mm_norm_inf(a.shape[0], a.shape[1], _ptr(a), _ld(a), _ptr(out), _stream(a.device)))
+    return out
+
+
+def emulated_slices(nslices=0, tier=1e-14, kind=SLICE_BF16):
+    return int(lib().mm_emulated_slices(kind, nslices, tier))
+
+
+def emulated(a, b, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
+    """FP64-accurate product from BF16 slices on tcgen05 (see include/mm.h)."""
+    a, b, c, n, p, m = _prep(a, b, out)
+    need = lib().mm_emulated_workspace_bytes(n, p, m, kind, nslices, tier)
+    ws = _ws(need, a.device)
+    check("mm_emulated", lib().mm_emulated(*_gemm_args(a, b, c, n, p, m), kind, nslices, float(tier), _ptr(ws), need,
+                                           _stream(a.device)))
+    return c
+
+
+class profile:
+    """Context manager recording every libmm kernel launch with CUDA events on
+    its own stream.  After exit, ``stats`` maps kernel name -> (launches, ms)."""
+
+    def __enter__(self):
+        lib().mm_profile_read(None, 0)
+        check("mm_profile_enable", lib().mm_profile_enable(1))
+        self.stats = {}
+        return self
+
+    def __exit__(self, *exc):
+        lib().mm_profile_enable(0)
+        buf = (KernelStat * 64)()
+        n = lib().mm_profile_read(buf, 64)
+        if n < 0:
+            check("mm_profile_read", n)
+        self.stats = {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n, 64))}
+        return False
+
+
+def device_status(device=None):
+    """Reads and clears the kernels' timeout status word; returns the raw code."""
+    torch = _torch()
+    code = ctypes.c_int32(0)
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    rc = lib().mm_device_status(_stream(dev), ctypes.byref(code))
+    if rc not in (0, -5):
+        check("mm_device_status", rc)
+    return int(code.value)

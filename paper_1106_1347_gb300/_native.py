@@ -1,0 +1,73 @@
+"""ctypes declarations of the libmm C ABI (include/mm.h).  Argument marshalling
+only: every step of every method runs in the library's CUDA kernels.  There is
+no fallback -- if the library is missing this module raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libmm.so")
+
+_lib = None
+_lock = threading.Lock()
+
+i64, i32, dbl, vp, sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+GEMM = [i64, i64, i64, vp, i64, vp, i64, vp, i64]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+# name -> (restype, argtypes); mirrors include/mm.h
+SIGNATURES = {
+    "mm_version": (ctypes.c_int, []),
+    "mm_last_error": (ctypes.c_char_p, []),
+    "mm_device_status": (ctypes.c_int, [vp, ctypes.POINTER(i32)]),
+    "mm_norm_inf": (ctypes.c_int, [i64, i64, vp, i64, vp, vp]),
+    "mm_naive": (ctypes.c_int, GEMM + [vp]),
+    "mm_kahan": (ctypes.c_int, GEMM + [vp]),
+    "mm_winograd_workspace_bytes": (sz, [i64, i64, i64]),
+    "mm_winograd": (ctypes.c_int, GEMM + [vp, sz, vp]),
+    "mm_winograd_scaled_workspace_bytes": (sz, [i64, i64, i64]),
+    "mm_winograd_scaled": (ctypes.c_int, GEMM + [vp, vp, sz, vp]),
+    "mm_strassen_workspace_bytes": (sz, [i64, i64, i64, i32]),
+    "mm_strassen": (ctypes.c_int, GEMM + [i32, vp, sz, vp]),
+    "mm_strassen_winograd_workspace_bytes": (sz, [i64, i64, i64, i32]),
+    "mm_strassen_winograd": (ctypes.c_int, GEMM + [i32, vp, sz, vp]),
+    "mm_emulated_workspace_bytes": (sz, [i64, i64, i64, i32, i32, dbl]),
+    "mm_emulated": (ctypes.c_int, GEMM + [i32, i32, dbl, vp, sz, vp]),
+    "mm_emulated_slices": (ctypes.c_int, [i32, i32, dbl]),
+    "mm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "mm_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelStat), i32]),
+}
+
+
+class MMError(RuntimeError):
+    def __init__(self, fn: str, status: int, message: str):
+        super().__init__(f"{fn} failed with status {status}: {message}")
+        self.status = status
+
+
+def lib():
+    """Load libmm.so (built in-tree by paper_1106_1347_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libmm.so is not built ({LIB_PATH}); run paper_1106_1347_gb300.build.build()")
+            handle = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = handle
+    return _lib
+
+
+def check(fn: str, status: int) -> None:
+    if status != 0:
+        msg = lib().mm_last_error()
+        raise MMError(fn, status, msg.decode() if msg else "")

@@ -1,0 +1,332 @@
+// libmm C ABI: argument checking, status reporting, kernel timing and dispatch
+// to the per-method launchers.  See include/mm.h for the contract.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+// Device status word raised by bounded waits (one per device context).
+static __device__ int g_device_status;
+
+namespace mm {
+
+static thread_local std::string t_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+}
+
+int fail(int status, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return MM_ERR_CUDA;
+}
+
+int *device_status_ptr() {
+    static std::mutex mu;
+    static std::map<int, int *> per_dev;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    auto it = per_dev.find(dev);
+    if (it != per_dev.end()) return it->second;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
+    per_dev[dev] = (int *)p;
+    return (int *)p;
+}
+
+EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// ------------------------------------------------------------ kernel timing
+
+namespace {
+struct ProfRec {
+    std::string name;
+    cudaEvent_t start, stop;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_recs;
+std::vector<cudaEvent_t> g_event_pool;
+thread_local int t_open = -1;
+
+cudaEvent_t take_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+void prof_begin(const char *name, cudaStream_t stream) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    if (!g_prof_on) return;
+    ProfRec r{name, take_event(), take_event()};
+    cudaEventRecord(r.start, stream);
+    g_prof_recs.push_back(r);
+    t_open = (int)g_prof_recs.size() - 1;
+}
+
+void prof_end(cudaStream_t stream) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    if (!g_prof_on || t_open < 0) return;
+    cudaEventRecord(g_prof_recs[t_open].stop, stream);
+    t_open = -1;
+}
+
+int check_gemm_args(const char *fn, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                    int64_t ldb, const double *C, int64_t ldc) {
+    if (N < 0 || P < 0 || M < 0) return fail(MM_ERR_ARG, "%s: negative size (N=%lld P=%lld M=%lld)", fn,
+                                             (long long)N, (long long)P, (long long)M);
+    if (lda < std::max<int64_t>(1, P) || ldb < std::max<int64_t>(1, M) || ldc < std::max<int64_t>(1, M))
+        return fail(MM_ERR_ARG, "%s: leading dimension too small (lda=%lld ldb=%lld ldc=%lld)", fn, (long long)lda,
+                    (long long)ldb, (long long)ldc);
+    if ((N > 0 && P > 0 && !A) || (P > 0 && M > 0 && !B) || (N > 0 && M > 0 && !C))
+        return fail(MM_ERR_ARG, "%s: NULL pointer with non-zero extent", fn);
+    size_t cb = span_bytes(N, M, ldc);
+    if (cb && (ranges_overlap(C, cb, A, span_bytes(N, P, lda)) || ranges_overlap(C, cb, B, span_bytes(P, M, ldb))))
+        return fail(MM_ERR_ARG, "%s: C overlaps A or B", fn);
+    return MM_OK;
+}
+
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" {
+
+int mm_version(void) { return 100; }
+
+const char *mm_last_error(void) { return t_err.c_str(); }
+
+int mm_device_status(void *stream, int32_t *code_out) {
+    int *p = device_status_ptr();
+    if (!p) return fail(MM_ERR_CUDA, "mm_device_status: no device status symbol");
+    int v = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&v, p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "mm_device_status");
+    if (code_out) *code_out = v;
+    if (v) return fail(MM_ERR_TIMEOUT, "a device-side wait gave up (code %d)", v);
+    return MM_OK;
+}
+
+int mm_norm_inf(int64_t N, int64_t P, const double *A, int64_t lda, double *out, void *stream) {
+    if (N < 0 || P < 0) return fail(MM_ERR_ARG, "mm_norm_inf: negative size");
+    if (lda < std::max<int64_t>(1, P)) return fail(MM_ERR_ARG, "mm_norm_inf: lda too small");
+    if (!out || (N > 0 && P > 0 && !A)) return fail(MM_ERR_ARG, "mm_norm_inf: NULL pointer");
+    return run_norm_inf(N, P, A, lda, out, (cudaStream_t)stream);
+}
+
+int mm_naive(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+             int64_t ldc, void *stream) {
+    int rc = check_gemm_args("mm_naive", N, P, M, A, lda, B, ldb, C, ldc);
+    if (rc) return rc;
+    if (N == 0 || M == 0) return MM_OK;
+    if (P == 0) return run_zero(N, M, C, ldc, (cudaStream_t)stream);
+    return run_naive(N, P, M, A, lda, B, ldb, C, ldc, (cudaStream_t)stream);
+}
+
+int mm_kahan(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+             int64_t ldc, void *stream) {
+    int rc = check_gemm_args("mm_kahan", N, P, M, A, lda, B, ldb, C, ldc);
+    if (rc) return rc;
+    if (N == 0 || M == 0) return MM_OK;
+    if (P == 0) return run_zero(N, M, C, ldc, (cudaStream_t)stream);
+    return run_kahan(N, P, M, A, lda, B, ldb, C, ldc, (cudaStream_t)stream);
+}
+
+size_t mm_winograd_workspace_bytes(int64_t N, int64_t P, int64_t M) { return winograd_ws_bytes(N, P, M, false); }
+
+size_t mm_winograd_scaled_workspace_bytes(int64_t N, int64_t P, int64_t M) {
+    return winograd_ws_bytes(N, P, M, true);
+}
+
+static int winograd_common(const char *fn, bool scaled, int64_t N, int64_t P, int64_t M, const double *A,
+                           int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc, int32_t *lambda_out,
+                           void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_gemm_args(fn, N, P, M, A, lda, B, ldb, C, ldc);
+    if (rc) return rc;
+    size_t need = winograd_ws_bytes(N, P, M, scaled);
+    if (ws_bytes < need || (need && !ws))
+        return fail(MM_ERR_WORKSPACE, "%s: workspace %zu bytes < %zu required", fn, ws_bytes, need);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N == 0 || M == 0) {
+        if (scaled && lambda_out) {
+            cudaError_t e = cudaMemsetAsync(lambda_out, 0, sizeof(int32_t), st);
+            if (e != cudaSuccess) return cuda_fail(e, fn);
+        }
+        return MM_OK;
+    }
+    return run_winograd(N, P, M, A, lda, B, ldb, C, ldc, scaled, lambda_out, ws, st);
+}
+
+int mm_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                double *C, int64_t ldc, void *ws, size_t ws_bytes, void *stream) {
+    return winograd_common("mm_winograd", false, N, P, M, A, lda, B, ldb, C, ldc, nullptr, ws, ws_bytes, stream);
+}
+
+int mm_winograd_scaled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                       double *C, int64_t ldc, int32_t *lambda_out, void *ws, size_t ws_bytes, void *stream) {
+    return winograd_common("mm_winograd_scaled", true, N, P, M, A, lda, B, ldb, C, ldc, lambda_out, ws, ws_bytes,
+                           stream);
+}
+
+static size_t strassen_ws_query(int variant, int64_t N, int64_t P, int64_t M, int32_t cutoff) {
+    int depth;
+    int64_t Np, Pp, Mp;
+    if (N <= 0 || P <= 0 || M <= 0) return 0;
+    if (strassen_plan(N, P, M, cutoff, &depth, &Np, &Pp, &Mp) != MM_OK) return 0;
+    return strassen_ws_bytes(variant, depth, Np, Pp, Mp);
+}
+
+size_t mm_strassen_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t cutoff) {
+    return strassen_ws_query(0, N, P, M, cutoff);
+}
+size_t mm_strassen_winograd_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t cutoff) {
+    return strassen_ws_query(1, N, P, M, cutoff);
+}
+
+static int strassen_common(const char *fn, int variant, int64_t N, int64_t P, int64_t M, const double *A,
+                           int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc, int32_t cutoff,
+                           void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_gemm_args(fn, N, P, M, A, lda, B, ldb, C, ldc);
+    if (rc) return rc;
+    if (cutoff < -1) return fail(MM_ERR_ARG, "%s: cutoff must be -1, 0 or positive", fn);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N == 0 || M == 0) return MM_OK;
+    if (P == 0) return run_zero(N, M, C, ldc, st);
+    int depth;
+    int64_t Np, Pp, Mp;
+    rc = strassen_plan(N, P, M, cutoff, &depth, &Np, &Pp, &Mp);
+    if (rc) return rc;
+    size_t need = strassen_ws_bytes(variant, depth, Np, Pp, Mp);
+    if (ws_bytes < need || (need && !ws))
+        return fail(MM_ERR_WORKSPACE, "%s: workspace %zu bytes < %zu required", fn, ws_bytes, need);
+    return run_strassen(variant, N, P, M, A, lda, B, ldb, C, ldc, depth, Np, Pp, Mp, ws, st);
+}
+
+int mm_strassen(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                double *C, int64_t ldc, int32_t cutoff, void *ws, size_t ws_bytes, void *stream) {
+    return strassen_common("mm_strassen", 0, N, P, M, A, lda, B, ldb, C, ldc, cutoff, ws, ws_bytes, stream);
+}
+
+int mm_strassen_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                         int64_t ldb, double *C, int64_t ldc, int32_t cutoff, void *ws, size_t ws_bytes,
+                         void *stream) {
+    return strassen_common("mm_strassen_winograd", 1, N, P, M, A, lda, B, ldb, C, ldc, cutoff, ws, ws_bytes,
+                           stream);
+}
+
+int mm_emulated_slices(int32_t kind, int32_t nslices, double tier) { return emulated_slices(kind, nslices, tier); }
+
+size_t mm_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t kind, int32_t nslices, double tier) {
+    int s = emulated_slices(kind, nslices, tier);
+    if (s <= 0 || N < 0 || P < 0 || M < 0) return 0;
+    return emulated_ws_bytes(N, P, M, s);
+}
+
+int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                double *C, int64_t ldc, int32_t kind, int32_t nslices, double tier, void *ws, size_t ws_bytes,
+                void *stream) {
+    int rc = check_gemm_args("mm_emulated", N, P, M, A, lda, B, ldb, C, ldc);
+    if (rc) return rc;
+    if (kind == MM_SLICE_FP8E4M3) return fail(MM_ERR_UNSUPPORTED, "mm_emulated: FP8-E4M3 slices are not built");
+    if (kind != MM_SLICE_BF16) return fail(MM_ERR_ARG, "mm_emulated: unknown slice kind %d", kind);
+    if (nslices < 0 || nslices > 8) return fail(MM_ERR_ARG, "mm_emulated: nslices must be 0..8");
+    if (nslices == 0 && !(tier > 0.0)) return fail(MM_ERR_ARG, "mm_emulated: tier must be > 0 when nslices == 0");
+    if (P > (int64_t(1) << 20)) return fail(MM_ERR_UNSUPPORTED, "mm_emulated: P > 2^20");
+    int s = emulated_slices(kind, nslices, tier);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N == 0 || M == 0) return MM_OK;
+    if (P == 0) return run_zero(N, M, C, ldc, st);
+    size_t need = emulated_ws_bytes(N, P, M, s);
+    if (ws_bytes < need || !ws)
+        return fail(MM_ERR_WORKSPACE, "mm_emulated: workspace %zu bytes < %zu required", ws_bytes, need);
+    return run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, ws, st);
+}
+
+int mm_profile_enable(int on) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof_on = on != 0;
+    return MM_OK;
+}
+
+int mm_profile_read(mm_kernel_stat *out, int32_t cap) {
+    std::vector<ProfRec> recs;
+    {
+        std::lock_guard<std::mutex> g(g_prof_mu);
+        recs.swap(g_prof_recs);
+    }
+    std::vector<mm_kernel_stat> stats;
+    int rc = MM_OK;
+    for (auto &r : recs) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.stop);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.start, r.stop);
+        if (e != cudaSuccess) rc = cuda_fail(e, "mm_profile_read");
+        auto it = std::find_if(stats.begin(), stats.end(),
+                               [&](const mm_kernel_stat &s) { return r.name == s.name; });
+        if (it == stats.end()) {
+            mm_kernel_stat s{};
+            snprintf(s.name, sizeof s.name, "%s", r.name.c_str());
+            stats.push_back(s);
+            it = stats.end() - 1;
+        }
+        it->launches += 1;
+        it->total_ms += ms;
+    }
+    {
+        std::lock_guard<std::mutex> g(g_prof_mu);
+        for (auto &r : recs) {
+            g_event_pool.push_back(r.start);
+            g_event_pool.push_back(r.stop);
+        }
+    }
+    if (rc != MM_OK) return rc;
+    for (int32_t i = 0; i < cap && i < (int32_t)stats.size(); ++i) out[i] = stats[i];
+    return (int)stats.size();
+}
+
+}  // extern "C"

@@ -1,0 +1,533 @@
+// FP64-accurate product emulated from BF16 slices on the tcgen05 tensor cores.
+//
+// Not in the paper; its power-of-two row/column scaling generalises the exact
+// scaling of section "WinogradScaled" from one global lambda to one exponent
+// per row of A (e_i) and per column of B (f_j).  Definition (identical to the
+// CPU oracle's):
+//   V_ik = RN(A_ik 2^(beta s - 1 - e_i)),  |V| <= 2^(beta s - 1),  beta = 7;
+//   V = sum_t v_t 2^(beta t) in balanced digits (low digits in [-64, 64),
+//   top digit in [-64, 64]); slice sigma holds the digit of weight
+//   2^(beta (s-1-sigma)) as an exact BF16; B is cut per column likewise;
+//   T_d = sum_k sum_{sigma+tau=d} a^(sigma)_ik b^(tau)_kj  for d = 0..s-1;
+//   C_ij = RN(sum_d T_d 2^(beta (s-1-d))) * 2^(e_i + f_j + 2 - beta (s+1)).
+//
+// Kernels (all integer work on the FP64 bit patterns; FP64 arithmetic on this
+// part runs at ~1/100 of the BF16 tensor rate, so none is spent per slice):
+//   split_rows  -- one warp per row of A: max |A_ik| by integer max on the bit
+//                  patterns, then the digits, written as BF16 slices [s][N][P]
+//                  (K-major, coalesced).
+//   col_max / split_cols -- per-column maxima of B, then digits transposed
+//                  through shared memory into slices [s][M][P] (K-major).
+//   slice_gemm  -- 128x64 output tile per CTA.  Warp 0 issues TMA loads of all
+//                  s slices of a 32-wide K-block of A and B (3-D boxes,
+//                  64-byte swizzle) into a ring of shared-memory stages; warp 1
+//                  issues tcgen05.mma kind::f16 for every pair with
+//                  sigma + tau = d into TMEM accumulator d (s x 64 FP32
+//                  columns); eight epilogue warps drain the accumulators every
+//                  K-chunk Kc, chosen so every partial sum is an integer below
+//                  2^24 and FP32 accumulation is exact, into two int64
+//                  registers per output, and at the end round the exact
+//                  128-bit integer once to double and apply 2^(e_i + f_j ...).
+// Every mbarrier wait is bounded; on timeout the kernel raises the device
+// status word, waits (bounded) for its own copies and MMAs, frees TMEM and exits.
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kBeta = 7;
+constexpr int BM = 128, BN = 64, BKE = 32;  // tile rows, tile cols, K-block (bf16: 64 bytes)
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kSmemLimit = 232448;  // opt-in dynamic shared memory per block on sm_103
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+// |x| as its bit pattern (order-preserving for the non-negative doubles).
+__device__ __forceinline__ unsigned long long absbits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & ~(1ull << 63);
+}
+
+__device__ __forceinline__ int frexp_exp_bits(unsigned long long absbits) {
+    if (absbits == 0) return 0;
+    int e;
+    (void)frexp(__longlong_as_double((long long)absbits), &e);
+    return e;
+}
+
+// RN(x * 2^sh) as an integer, computed on the bit pattern (ties to even).
+__device__ __forceinline__ int64_t round_scaled(double x, int sh) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const bool neg = (b >> 63) != 0;
+    int E = (int)((b >> 52) & 0x7FF);
+    uint64_t m = b & ((1ull << 52) - 1);
+    if (E == 0) {
+        if (m == 0) return 0;
+        E = 1;
+    } else {
+        m |= 1ull << 52;
+    }
+    const int e2 = E - 1075 + sh;
+    uint64_t q;
+    if (e2 >= 0) {
+        q = m << e2;
+    } else {
+        const int r = -e2;
+        if (r > 63) {
+            q = 0;
+        } else {
+            q = m >> r;
+            const uint64_t rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
+            if (rem > half || (rem == half && (q & 1))) ++q;
+        }
+    }
+    return neg ? -(int64_t)q : (int64_t)q;
+}
+
+// Balanced base-2^7 digits, most significant first: dig[0] is the top digit.
+__device__ __forceinline__ void balanced_digits(int64_t V, int s, int (&dig)[8]) {
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+        if (t < s - 1) {
+            int d = (int)(V & 127);
+            if (d >= 64) d -= 128;
+            dig[s - 1 - t] = d;
+            V = (V - d) >> 7;
+        }
+    }
+    dig[0] = (int)V;
+}
+
+__global__ void __launch_bounds__(256) split_rows_kernel(int64_t N, int64_t P, const double *__restrict__ A,
+                                                         int64_t lda, int s, int64_t Nr, int64_t Pp,
+                                                         int32_t *__restrict__ ea,
+                                                         __nv_bfloat16 *__restrict__ slices) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + warp;
+    if (row >= N) return;
+    const double *a = A + row * lda;
+    unsigned long long mx = 0;
+    for (int64_t c = lane; c < P; c += 32) mx = umax64(mx, absbits(a[c]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        mx = umax64(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mx, o));
+    const int e = frexp_exp_bits(mx);
+    if (lane == 0) ea[row] = e;
+    const int sh = kBeta * s - 1 - e;
+    // Columns [P, Pp) are written as zero digits so every K-block read stays defined.
+    for (int64_t c0 = 0; c0 < Pp; c0 += 64) {
+        const int64_t c = c0 + 2 * lane;
+        if (c >= Pp) break;
+        int d0[8], d1[8];
+        balanced_digits(c < P ? round_scaled(a[c], sh) : 0, s, d0);
+        const bool two = c + 1 < Pp;
+        balanced_digits((two && c + 1 < P) ? round_scaled(a[c + 1], sh) : 0, s, d1);
+        for (int t = 0; t < s; ++t) {
+            __nv_bfloat16 *dst = slices + ((int64_t)t * Nr + row) * Pp + c;
+            if (two) {
+                *reinterpret_cast<__nv_bfloat162 *>(dst) = __floats2bfloat162_rn((float)d0[t], (float)d1[t]);
+            } else {
+                dst[0] = __float2bfloat16_rn((float)d0[t]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) col_max_kernel(int64_t P, int64_t M, const double *__restrict__ B,
+                                                      int64_t ldb, unsigned long long *__restrict__ colmax) {
+    const int64_t j = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (j >= M) return;
+    const int64_t k0 = (int64_t)blockIdx.y * 256, k1 = min(P, k0 + 256);
+    unsigned long long mx = 0;
+    for (int64_t k = k0; k < k1; ++k) mx = umax64(mx, absbits(B[k * ldb + j]));
+    if (mx) atomicMax(colmax + j, mx);
+}
+
+constexpr int SC_K = 32, SC_J = 64;
+
+__global__ void __launch_bounds__(256) split_cols_kernel(int64_t P, int64_t M, const double *__restrict__ B,
+                                                         int64_t ldb, int s, const unsigned long long *colmax,
+                                                         int64_t Mr, int64_t Pp, int32_t *__restrict__ fb,
+                                                         __nv_bfloat16 *__restrict__ slices) {
+    extern __shared__ __align__(16) __nv_bfloat16 sm[];  // [s][SC_J][SC_K + 2]
+    constexpr int LD = SC_K + 2;
+    const int tid = threadIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.x * SC_J, k0 = (int64_t)blockIdx.y * SC_K;
+    const int jj = tid & 63;
+    const int64_t j = j0 + jj;
+    const int f = (j < M) ? frexp_exp_bits(colmax[j]) : 0;
+    if (blockIdx.y == 0 && tid < 64 && j < M) fb[j] = f;
+    const int sh = kBeta * s - 1 - f;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int kk = (tid >> 6) + 4 * r;
+        const int64_t k = k0 + kk;
+        int dig[8];
+        balanced_digits((k < P && j < M) ? round_scaled(B[k * ldb + j], sh) : 0, s, dig);
+        for (int t = 0; t < s; ++t) sm[(t * SC_J + jj) * LD + kk] = __float2bfloat16_rn((float)dig[t]);
+    }
+    __syncthreads();
+    // Write each slice's 64 columns x 32 k as K-major rows (16 threads per 64-byte row).
+    for (int t = 0; t < s; ++t) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int w = tid + 256 * q;
+            const int jr = w >> 4, kp = (w & 15) * 2;
+            const int64_t gj = j0 + jr, gk = k0 + kp;
+            if (gj >= M || gk >= Pp) continue;  // [P, Pp) receives zero digits
+            const __nv_bfloat16 *src = sm + (t * SC_J + jr) * LD + kp;
+            __nv_bfloat16 *dst = slices + ((int64_t)t * Mr + gj) * Pp + gk;
+            if (gk + 1 < Pp) {
+                __nv_bfloat162 v;
+                v.x = src[0];
+                v.y = src[1];
+                *reinterpret_cast<__nv_bfloat162 *>(dst) = v;
+            } else {
+                dst[0] = src[0];
+            }
+        }
+    }
+}
+
+struct EmuParams {
+    int64_t N, P, M;
+    int s, stages, chunk_blocks, hsplit, tmem_cols;
+    int tiles_m, tiles_n;
+    const int32_t *ea, *fb;
+    double *C;
+    int64_t ldc;
+    int *status;
+};
+
+__device__ __forceinline__ void raise_status(int *status, int code) {
+    if (status) atomicOr(status, code);
+}
+
+// Exact signed 128-bit integer (hi, lo) rounded to the nearest double (ties to even).
+__device__ __forceinline__ double int128_to_double(int64_t hi, uint64_t lo) {
+    const bool neg = hi < 0;
+    uint64_t uh = (uint64_t)hi, ul = lo;
+    if (neg) {
+        ul = ~ul + 1;
+        uh = ~uh + (ul == 0 ? 1 : 0);
+    }
+    double r;
+    if (uh == 0) {
+        r = __ull2double_rn(ul);
+    } else {
+        const int lz = __clzll((long long)uh);
+        const uint64_t top = lz ? ((uh << lz) | (ul >> (64 - lz))) : uh;
+        const uint64_t rest = ul << lz;
+        r = __ull2double_rn(top | (rest != 0 ? 1ull : 0ull));  // sticky bit below the rounding point
+        r = ldexp(r, 64 - lz);
+    }
+    return neg ? -r : r;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const EmuParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bars[2 * 8 + 3];
+    __shared__ uint32_t tmem_slot;
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int s = p.s, S = p.stages;
+    const uint32_t a_bytes = (uint32_t)s * BM * BKE * 2, b_bytes = (uint32_t)s * BN * BKE * 2;
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    uint64_t *full = bars, *empty = bars + 8, *acc_full = bars + 16, *acc_empty = bars + 17, *mma_done = bars + 18;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // Grouped rasterisation: runs of 8 tile-rows share B slices in L2.
+    const int id = blockIdx.x, per_group = 8 * p.tiles_n;
+    const int group = id / per_group, first_m = group * 8;
+    const int gsize = min(p.tiles_m - first_m, 8);
+    const int tm = first_m + (id % per_group) % gsize, tn = (id % per_group) / gsize;
+    const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BN;
+    const int nkb = (int)((p.P + BKE - 1) / BKE);
+    const int nchunks = (nkb + p.chunk_blocks - 1) / p.chunk_blocks;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            mmdev::mbar_init(&full[i], 1);
+            mmdev::mbar_init(&empty[i], 1);
+        }
+        mmdev::mbar_init(acc_full, 1);
+        mmdev::mbar_init(acc_empty, kEpiWarps);
+        mmdev::mbar_init(mma_done, 1);
+        mmdev::fence_mbar_init();
+    }
+    if (warp == 1) {
+        mmdev::tmem_alloc(&tmem_slot, (uint32_t)p.tmem_cols);
+        mmdev::tmem_relinquish();
+    }
+    mmdev::tc_fence_before();
+    __syncthreads();
+    mmdev::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mmdev::prefetch_tmap(&tmA);
+            mmdev::prefetch_tmap(&tmB);
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int st = kb % S, use = kb / S;
+                if (use > 0 && !mmdev::mbar_wait(&empty[st], (uint32_t)((use - 1) & 1))) {
+                    raise_status(p.status, mm::kStatusTimeoutTma);
+                    break;
+                }
+                uint8_t *sa = smem + (size_t)st * stage_bytes;
+                mmdev::mbar_arrive_expect_tx(&full[st], stage_bytes);
+                mmdev::tma_load_3d(sa, &tmA, &full[st], kb * BKE, (int32_t)m0, 0);
+                mmdev::tma_load_3d(sa + a_bytes, &tmB, &full[st], kb * BKE, (int32_t)n0, 0);
+                issued = kb + 1;
+            }
+            // Wait (bounded) for the last load into each stage, so no copy is in flight at exit.
+            for (int kb = max(0, issued - S); kb < issued; ++kb)
+                (void)mmdev::mbar_wait(&full[kb % S], (uint32_t)((kb / S) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = mmdev::idesc_bf16_f32(BM, BN);
+            bool ok = true;
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                const int st = kb % S, use = kb / S;
+                const int kin = kb % p.chunk_blocks, chunk = kb / p.chunk_blocks;
+                if (kin == 0 && chunk > 0) {
+                    if (!mmdev::mbar_wait(acc_empty, (uint32_t)((chunk - 1) & 1))) {
+                        raise_status(p.status, mm::kStatusTimeoutMma);
+                        ok = false;
+                        break;
+                    }
+                    mmdev::tc_fence_after();
+                }
+                if (!mmdev::mbar_wait(&full[st], (uint32_t)(use & 1))) {
+                    raise_status(p.status, mm::kStatusTimeoutMma);
+                    ok = false;
+                    break;
+                }
+                mmdev::tc_fence_after();
+                const uint32_t a_base = mmdev::smem_u32(smem + (size_t)st * stage_bytes);
+                const uint32_t b_base = a_base + a_bytes;
+                for (int d = 0; d < s; ++d) {
+                    for (int sg = 0; sg <= d; ++sg) {
+                        const int tu = d - sg;
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint64_t ad = mmdev::smem_desc_sw64(a_base + (uint32_t)sg * (BM * BKE * 2) + kk * 32);
+                            const uint64_t bd = mmdev::smem_desc_sw64(b_base + (uint32_t)tu * (BN * BKE * 2) + kk * 32);
+                            const uint32_t accum = (kin == 0 && sg == 0 && kk == 0) ? 0u : 1u;
+                            mmdev::mma_bf16(tmem + (uint32_t)(d * BN), ad, bd, idesc, accum);
+                        }
+                    }
+                }
+                mmdev::mma_commit(&empty[st]);
+                if (kin == p.chunk_blocks - 1 || kb == nkb - 1) mmdev::mma_commit(acc_full);
+            }
+            // Every MMA issued above has completed once mma_done flips.
+            mmdev::mma_commit(mma_done);
+            (void)mmdev::mbar_wait(mma_done, 0);
+        }
+    } else {
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int64_t row = m0 + 32 * q + lane;
+        int64_t whi[32], wlo[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) whi[j] = wlo[j] = 0;
+        const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h);
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            if (!mmdev::mbar_wait(acc_full, (uint32_t)(c & 1))) {
+                raise_status(p.status, mm::kStatusTimeoutEpi);
+                ok = false;
+                break;
+            }
+            mmdev::tc_fence_after();
+            for (int d = 0; d < s; ++d) {
+                uint32_t v[32];
+                mmdev::tmem_ld_32x32b_x32(tbase + (uint32_t)(d * BN), v);
+                mmdev::tmem_wait_ld();
+                if (d < p.hsplit) {
+                    const int sh = kBeta * (p.hsplit - 1 - d);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) whi[j] += (int64_t)__float2int_rn(__uint_as_float(v[j])) << sh;
+                } else {
+                    const int sh = kBeta * (s - 1 - d);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) wlo[j] += (int64_t)__float2int_rn(__uint_as_float(v[j])) << sh;
+                }
+            }
+            mmdev::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mmdev::mbar_arrive(acc_empty);
+        }
+        if (ok && row < p.N) {
+            const int e = p.ea[row];
+            const int sh2 = kBeta * (s - p.hsplit);
+            double *crow = p.C + row * p.ldc;
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+                double out[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int64_t col = n0 + 32 * h + j + u;
+                    const int64_t wh = whi[j + u], wl = wlo[j + u];
+                    // W = wh * 2^sh2 + wl as a signed 128-bit integer.
+                    uint64_t lo = sh2 ? ((uint64_t)wh << sh2) : (uint64_t)wh;
+                    int64_t hi = sh2 ? (wh >> (64 - sh2)) : (wh >> 63);
+                    const uint64_t lo2 = lo + (uint64_t)wl;
+                    hi += (wl >> 63) + (lo2 < lo ? 1 : 0);
+                    lo = lo2;
+                    const int f = (col < p.M) ? p.fb[col] : 0;
+                    out[u] = ldexp(int128_to_double(hi, lo), e + f + 2 - kBeta * (s + 1));
+                }
+                const int64_t col = n0 + 32 * h + j;
+                double *dst = crow + col;
+                if (col + 1 < p.M && (((uintptr_t)dst & 15) == 0)) {
+                    *reinterpret_cast<double2 *>(dst) = make_double2(out[0], out[1]);
+                } else {
+                    if (col < p.M) dst[0] = out[0];
+                    if (col + 1 < p.M) dst[1] = out[1];
+                }
+            }
+        }
+    }
+
+    mmdev::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        mmdev::tc_fence_after();
+        mmdev::tmem_dealloc(tmem, (uint32_t)p.tmem_cols);
+    }
+}
+
+struct Layout {
+    int s;
+    int64_t Nr, Mr, Pp;
+    size_t off_ea, off_fb, off_colmax, off_a, off_b, total;
+};
+
+Layout layout(int64_t N, int64_t P, int64_t M, int s) {
+    Layout L{};
+    L.s = s;
+    L.Nr = mm::ceil_div(std::max<int64_t>(N, 1), BM) * BM;
+    L.Mr = mm::ceil_div(std::max<int64_t>(M, 1), BN) * BN;
+    L.Pp = std::max<int64_t>(mm::ceil_div(std::max<int64_t>(P, 1), 8) * 8, BKE);
+    size_t o = 0;
+    L.off_ea = o;
+    o += mm::align_up((size_t)L.Nr * 4, 1024);
+    L.off_fb = o;
+    o += mm::align_up((size_t)L.Mr * 4, 1024);
+    L.off_colmax = o;
+    o += mm::align_up((size_t)L.Mr * 8, 1024);
+    L.off_a = o;
+    o += mm::align_up((size_t)s * L.Nr * L.Pp * 2, 1024);
+    L.off_b = o;
+    o += mm::align_up((size_t)s * L.Mr * L.Pp * 2, 1024);
+    L.total = o;
+    return L;
+}
+
+// Slices [s][rows][Pp] bf16; the K extent is Pp (zero-padded by the split
+// kernels), K-blocks past Pp read the TMA zero fill.
+int encode_slices(CUtensorMap *map, void *base, int64_t rows, int64_t Pp, int s, int box_rows) {
+    mm::EncodeTiledFn enc = mm::encode_tiled_fn();
+    if (!enc) return mm::fail(MM_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[3] = {(cuuint64_t)Pp, (cuuint64_t)rows, (cuuint64_t)s};
+    cuuint64_t strides[2] = {(cuuint64_t)Pp * 2, (cuuint64_t)(rows * Pp * 2)};
+    cuuint32_t box[3] = {(cuuint32_t)BKE, (cuuint32_t)box_rows, (cuuint32_t)s};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return mm::fail(MM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return MM_OK;
+}
+
+}  // namespace
+
+namespace mm {
+
+int emulated_slices(int32_t kind, int32_t nslices, double tier) {
+    if (kind != MM_SLICE_BF16) return -1;
+    if (nslices > 0) return nslices <= 8 ? nslices : -1;
+    if (!(tier > 0.0)) return -1;
+    // beta*s - 1 bits of each row/column; about 8 more bits than -log2(tier) keep the
+    // normwise error below the tier on wide-exponent inputs.
+    const double need = (-log2(tier) + 9.0) / kBeta;
+    int s = (int)ceil(need);
+    return std::min(8, std::max(1, s));
+}
+
+size_t emulated_ws_bytes(int64_t N, int64_t P, int64_t M, int s) { return layout(N, P, M, s).total; }
+
+int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                 double *C, int64_t ldc, int s, void *ws, cudaStream_t st) {
+    const Layout L = layout(N, P, M, s);
+    char *w = (char *)ws;
+    int32_t *ea = (int32_t *)(w + L.off_ea);
+    int32_t *fb = (int32_t *)(w + L.off_fb);
+    unsigned long long *colmax = (unsigned long long *)(w + L.off_colmax);
+    __nv_bfloat16 *sa = (__nv_bfloat16 *)(w + L.off_a);
+    __nv_bfloat16 *sb = (__nv_bfloat16 *)(w + L.off_b);
+    int rc;
+    cudaError_t e = cudaMemsetAsync(colmax, 0, (size_t)M * 8, st);
+    if (e != cudaSuccess) return cuda_fail(e, "mm_emulated");
+    rc = launch("emu_split_rows", st, [&] {
+        split_rows_kernel<<<(unsigned)ceil_div(N, 8), 256, 0, st>>>(N, P, A, lda, s, L.Nr, L.Pp, ea, sa);
+    });
+    if (rc) return rc;
+    rc = launch("emu_col_max", st, [&] {
+        dim3 g((unsigned)ceil_div(M, 128), (unsigned)ceil_div(P, 256));
+        col_max_kernel<<<g, 128, 0, st>>>(P, M, B, ldb, colmax);
+    });
+    if (rc) return rc;
+    rc = launch("emu_split_cols", st, [&] {
+        dim3 g((unsigned)ceil_div(M, SC_J), (unsigned)ceil_div(L.Pp, SC_K));
+        const size_t sm = (size_t)s * SC_J * (SC_K + 2) * sizeof(__nv_bfloat16);
+        split_cols_kernel<<<g, 256, sm, st>>>(P, M, B, ldb, s, colmax, L.Mr, L.Pp, fb, sb);
+    });
+    if (rc) return rc;
+
+    CUtensorMap tmA, tmB;
+    if ((rc = encode_slices(&tmA, sa, L.Nr, L.Pp, s, BM))) return rc;
+    if ((rc = encode_slices(&tmB, sb, L.Mr, L.Pp, s, BN))) return rc;
+
+    EmuParams prm{};
+    prm.N = N;
+    prm.P = P;
+    prm.M = M;
+    prm.s = s;
+    const uint32_t stage_bytes = (uint32_t)s * (BM + BN) * BKE * 2;
+    prm.stages = std::min(4, (int)((kSmemLimit - 2048) / stage_bytes));
+    prm.chunk_blocks = std::max(1, (int)((1 << 24) / ((int64_t)s * 4096) / BKE));
+    prm.hsplit = (s + 1) / 2;
+    int cols = 32;
+    while (cols < s * BN) cols <<= 1;
+    prm.tmem_cols = cols;
+    prm.tiles_m = (int)ceil_div(N, BM);
+    prm.tiles_n = (int)ceil_div(M, BN);
+    prm.ea = ea;
+    prm.fb = fb;
+    prm.C = C;
+    prm.ldc = ldc;
+    prm.status = device_status_ptr();
+    const size_t smem = (size_t)prm.stages * stage_bytes + 1024;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kSmemLimit - 1024);
+    });
+    if (attr_err != cudaSuccess) return cuda_fail(attr_err, "mm_emulated: shared memory attribute");
+    const int64_t tiles = (int64_t)prm.tiles_m * prm.tiles_n;
+    return launch("emu_slice_gemm_tcgen05", st,
+                  [&] { slice_gemm_kernel<<<(unsigned)tiles, kThreads, smem, st>>>(tmA, tmB, prm); });
+}
+
+}  // namespace mm

@@ -1,0 +1,543 @@
+// FP64 base product on the FP64 tensor-core MMA (mma.sync m8n8k4 f64), and
+// the Strassen / Strassen-Winograd recursion built on it.
+//
+// One kernel, `level_kernel`, computes a list of products
+//   H_h = (expression over quadrants of A) x (expression over quadrants of B)
+// and folds each into up to four C quadrants, C_q := +-H_h (first touch) or
+// C_q := C_q +- H_h, in list order.  With one product and no quadrants it is
+// the naive method (section "The naive method"); with the seven products of
+// section "StrassenNaiv" or "StrassenWinograd" it is one recursion level whose
+// Plus/Minus operand sums are formed while tiles are staged into shared
+// memory and whose C-block sums are formed in the epilogue -- no separate
+// elementwise pass touches HBM.  Each CTA owns the same output tile of all
+// four C quadrants and walks the products in an order that reproduces the
+// paper's left-to-right sums:
+//   Strassen:  H1 H3 H2 H4 H5 H6 H7 gives C11 = ((H1+H4)-H5)+H7, C12 = H3+H5,
+//              C21 = H2+H4, C22 = ((H1+H3)-H2)+H6;
+//   Winograd:  H1..H7 gives C11 = H1+H2, C12 = ((H1+H3)+H4)+H6 = H9+H6,
+//              C21 = ((H1+H3)+H5)+H7 = (H8+H5)+H7, C22 = ((H1+H3)+H4)+H5 = H9+H5.
+// Padding to the recursion's sizes is virtual: reads outside an operand's
+// valid region return zero, writes outside C's region are dropped.
+// Outer recursion levels (depth >= 2) keep their operand sums and H_i in the
+// caller's workspace, like the paper's Aux matrices, and combine them with an
+// elementwise kernel; only the innermost level is fused.
+//
+// Tiling: 64x64 output tile, K-step 16, 4 warps each owning 32x32 (4x4 MMA
+// tiles of 8x8x4).  The kernel is bound by the FP64 MMA pipe (~4.2 TFLOP/s
+// measured on GB300 against ~1.0 for DFMA), so operand tiles are staged with
+// plain coalesced loads into padded, bank-conflict-free shared memory (the
+// expression evaluation happens in those loads), prefetched one K-step ahead.
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int AST = BK + 4;  // A tile row stride (doubles): conflict-free fragment reads
+constexpr int BST = BN + 4;  // B tile row stride
+
+enum : uint8_t { T11 = 0, T12 = 1, T21 = 2, T22 = 3, OP_ADD = 8, OP_SUB = 9 };
+
+struct Expr {
+    uint8_t code[8];
+    uint8_t len;
+};
+struct Target {
+    uint8_t quad;
+    int8_t sign;
+    uint8_t first;
+};
+struct Product {
+    Expr a, b;
+    uint8_t ntgt;
+    Target tgt[4];
+};
+struct View {
+    const double *p;
+    int64_t ld, rows, cols;
+};
+struct LevelArgs {
+    View A, B;
+    double *C;
+    int64_t ldc, crows, ccols;
+    int64_t n, p, m;  // product size: H is n x m with inner dimension p (quadrant size for a level)
+    int nprod;
+    Product prod[7];
+};
+
+__device__ __forceinline__ double view_at(const View &v, int64_t r, int64_t c) {
+    return (r < v.rows && c < v.cols) ? v.p[r * v.ld + c] : 0.0;
+}
+
+// Postfix evaluation of an operand element; quadrant (qr, qc) of term t sits
+// at row offset (t >> 1) * rstep and column offset (t & 1) * cstep.
+__device__ __forceinline__ double eval_expr(const Expr &e, const View &v, int64_t r, int64_t c, int64_t rstep,
+                                            int64_t cstep) {
+    if (e.len == 1) return view_at(v, r + (e.code[0] >> 1) * rstep, c + (e.code[0] & 1) * cstep);
+    double st[4];
+    int sp = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        if (t < e.len) {
+            const uint8_t op = e.code[t];
+            if (op < 4) {
+                const double x = view_at(v, r + (op >> 1) * rstep, c + (op & 1) * cstep);
+                st[sp] = x;
+                ++sp;
+            } else {
+                const double y = st[sp - 1], x = st[sp - 2];
+                sp -= 2;
+                st[sp] = (op == OP_ADD) ? __dadd_rn(x, y) : __dsub_rn(x, y);
+                ++sp;
+            }
+        }
+    }
+    return st[0];
+}
+
+__device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(c[0]), "+d"(c[1])
+                 : "d"(a), "d"(b));
+}
+
+template <bool kSingle>
+__global__ void __launch_bounds__(128) level_kernel(const __grid_constant__ LevelArgs args) {
+    __shared__ __align__(16) double As[BM][AST];
+    __shared__ __align__(16) double Bs[BK][BST];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+    const int64_t n = args.n, p = args.p, m = args.m;
+
+    for (int pi = 0; pi < args.nprod; ++pi) {
+        const Product &pr = args.prod[pi];
+        double acc[4][4][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+        double ra[8], rb[8];
+        auto fetch = [&](int64_t k0) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int e = tid + 128 * r;
+                const int64_t gi = i0 + (e >> 4), gk = k0 + (e & 15);
+                double v = 0.0;
+                if (gi < n && gk < p) {
+                    if (kSingle)
+                        v = view_at(args.A, gi, gk);
+                    else
+                        v = eval_expr(pr.a, args.A, gi, gk, n, p);
+                }
+                ra[r] = v;
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int e = tid + 128 * r;
+                const int64_t gk = k0 + (e >> 6), gj = j0 + (e & 63);
+                double v = 0.0;
+                if (gk < p && gj < m) {
+                    if (kSingle)
+                        v = view_at(args.B, gk, gj);
+                    else
+                        v = eval_expr(pr.b, args.B, gk, gj, p, m);
+                }
+                rb[r] = v;
+            }
+        };
+        fetch(0);
+        for (int64_t k0 = 0; k0 < p; k0 += BK) {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int e = tid + 128 * r;
+                As[e >> 4][e & 15] = ra[r];
+                Bs[e >> 6][e & 63] = rb[r];
+            }
+            __syncthreads();
+            if (k0 + BK < p) fetch(k0 + BK);
+#pragma unroll
+            for (int kk = 0; kk < BK; kk += 4) {
+                double af[4], bf[4];
+#pragma unroll
+                for (int mi = 0; mi < 4; ++mi) af[mi] = As[wm * 32 + mi * 8 + g][kk + t4];
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) bf[ni] = Bs[kk + t4][wn * 32 + ni * 8 + g];
+#pragma unroll
+                for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                    for (int ni = 0; ni < 4; ++ni) dmma_8x8x4(acc[mi][ni], af[mi], bf[ni]);
+            }
+        }
+        // Epilogue: fold +-H into each target quadrant (vectorised when aligned).
+        for (int ti = 0; ti < pr.ntgt; ++ti) {
+            const Target tg = pr.tgt[ti];
+            const int64_t roff = (tg.quad >> 1) * n, coff = (tg.quad & 1) * m;
+            const double sgn = (double)tg.sign;
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi) {
+                const int64_t row = i0 + wm * 32 + mi * 8 + g;
+                const int64_t crow = row + roff;
+                if (row >= n || crow >= args.crows) continue;
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) {
+                    const int64_t col = j0 + wn * 32 + ni * 8 + 2 * t4;
+                    const int64_t ccol = col + coff;
+                    double *dst = args.C + crow * args.ldc + ccol;
+                    const double v0 = sgn * acc[mi][ni][0], v1 = sgn * acc[mi][ni][1];
+                    const bool ok0 = col < m && ccol < args.ccols;
+                    const bool ok1 = col + 1 < m && ccol + 1 < args.ccols;
+                    if (ok0 && ok1 && (((uintptr_t)dst & 15) == 0)) {
+                        double2 o;
+                        if (tg.first) {
+                            o = make_double2(v0, v1);
+                        } else {
+                            const double2 c = *reinterpret_cast<const double2 *>(dst);
+                            o = make_double2(__dadd_rn(c.x, v0), __dadd_rn(c.y, v1));
+                        }
+                        *reinterpret_cast<double2 *>(dst) = o;
+                    } else {
+                        if (ok0) dst[0] = tg.first ? v0 : __dadd_rn(dst[0], v0);
+                        if (ok1) dst[1] = tg.first ? v1 : __dadd_rn(dst[1], v1);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Elementwise out(i, j) = expression over up to four term views, for
+// i < rows, j < cols (the outer recursion levels' Plus/Minus passes).
+struct CombineArgs {
+    View term[4];
+    Expr e;
+    double *out;
+    int64_t ldo, rows, cols;
+};
+
+__global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ CombineArgs a) {
+    const int64_t j = (int64_t)blockIdx.x * 64 + (threadIdx.x & 63);
+    const int64_t i = (int64_t)blockIdx.y * 4 + (threadIdx.x >> 6);
+    if (i >= a.rows || j >= a.cols) return;
+    double st[4];
+    int sp = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        if (t < a.e.len) {
+            const uint8_t op = a.e.code[t];
+            if (op < 4) {
+                st[sp] = view_at(a.term[op], i, j);
+                ++sp;
+            } else {
+                const double y = st[sp - 1], x = st[sp - 2];
+                sp -= 2;
+                st[sp] = (op == OP_ADD) ? __dadd_rn(x, y) : __dsub_rn(x, y);
+                ++sp;
+            }
+        }
+    }
+    a.out[i * a.ldo + j] = st[0];
+}
+
+Expr ex(std::initializer_list<uint8_t> c) {
+    Expr e{};
+    e.len = 0;
+    for (uint8_t x : c) e.code[e.len++] = x;
+    return e;
+}
+Target tgt(uint8_t q, int s, bool first) { return Target{q, (int8_t)s, (uint8_t)(first ? 1 : 0)}; }
+
+// One recursion level of section "StrassenNaiv", in the order H1 H3 H2 H4 H5 H6 H7.
+void strassen_products(Product (&pr)[7]) {
+    pr[0] = Product{ex({T11, T22, OP_ADD}), ex({T11, T22, OP_ADD}), 2, {tgt(T11, 1, true), tgt(T22, 1, true)}};
+    pr[1] = Product{ex({T11}), ex({T12, T22, OP_SUB}), 2, {tgt(T12, 1, true), tgt(T22, 1, false)}};
+    pr[2] = Product{ex({T21, T22, OP_ADD}), ex({T11}), 2, {tgt(T21, 1, true), tgt(T22, -1, false)}};
+    pr[3] = Product{ex({T22}), ex({T21, T11, OP_SUB}), 2, {tgt(T11, 1, false), tgt(T21, 1, false)}};
+    pr[4] = Product{ex({T11, T12, OP_ADD}), ex({T22}), 2, {tgt(T11, -1, false), tgt(T12, 1, false)}};
+    pr[5] = Product{ex({T21, T11, OP_SUB}), ex({T11, T12, OP_ADD}), 1, {tgt(T22, 1, false)}};
+    pr[6] = Product{ex({T12, T22, OP_SUB}), ex({T21, T22, OP_ADD}), 1, {tgt(T11, 1, false)}};
+}
+
+// One recursion level of section "StrassenWinograd", H1..H7, with
+// A1 = A11-A21, A2 = A22-A1, B1 = B22-B12, B2 = B1+B11 written out per use.
+void strassen_winograd_products(Product (&pr)[7]) {
+    pr[0] = Product{ex({T11}), ex({T11}), 4,
+                    {tgt(T11, 1, true), tgt(T12, 1, true), tgt(T21, 1, true), tgt(T22, 1, true)}};
+    pr[1] = Product{ex({T12}), ex({T21}), 1, {tgt(T11, 1, false)}};
+    pr[2] = Product{ex({T22, T11, T21, OP_SUB, OP_SUB}), ex({T22, T12, OP_SUB, T11, OP_ADD}), 3,
+                    {tgt(T12, 1, false), tgt(T21, 1, false), tgt(T22, 1, false)}};
+    pr[3] = Product{ex({T21, T22, OP_ADD}), ex({T12, T11, OP_SUB}), 2, {tgt(T12, 1, false), tgt(T22, 1, false)}};
+    pr[4] = Product{ex({T11, T21, OP_SUB}), ex({T22, T12, OP_SUB}), 2, {tgt(T21, 1, false), tgt(T22, 1, false)}};
+    pr[5] = Product{ex({T12, T22, T11, T21, OP_SUB, OP_SUB, OP_SUB}), ex({T22}), 1, {tgt(T12, 1, false)}};
+    pr[6] = Product{ex({T22}), ex({T21, T22, T12, OP_SUB, T11, OP_ADD, OP_SUB}), 1, {tgt(T21, 1, false)}};
+}
+
+int launch_level(const LevelArgs &a, bool single, cudaStream_t st) {
+    dim3 grid((unsigned)mm::ceil_div(a.m, BN), (unsigned)mm::ceil_div(a.n, BM));
+    if (grid.x == 0 || grid.y == 0) return MM_OK;
+    if (grid.y > 65535) return mm::fail(MM_ERR_UNSUPPORTED, "product too tall for one launch");
+    if (single)
+        return mm::launch("gemm_f64_dmma", st, [&] { level_kernel<true><<<grid, 128, 0, st>>>(a); });
+    return mm::launch("strassen_level_dmma", st, [&] { level_kernel<false><<<grid, 128, 0, st>>>(a); });
+}
+
+int launch_combine(const CombineArgs &a, cudaStream_t st) {
+    if (a.rows <= 0 || a.cols <= 0) return MM_OK;
+    dim3 grid((unsigned)mm::ceil_div(a.cols, 64), (unsigned)mm::ceil_div(a.rows, 4));
+    return mm::launch("strassen_combine", st, [&] { combine_kernel<<<grid, 256, 0, st>>>(a); });
+}
+
+View quadrant(const View &v, int q, int64_t hr, int64_t hc) {
+    const int64_t r0 = (q >> 1) * hr, c0 = (q & 1) * hc;
+    View o;
+    o.p = v.p + r0 * v.ld + c0;
+    o.ld = v.ld;
+    o.rows = std::max<int64_t>(0, std::min<int64_t>(hr, v.rows - r0));
+    o.cols = std::max<int64_t>(0, std::min<int64_t>(hc, v.cols - c0));
+    if (o.rows == 0 || o.cols == 0) o.p = v.p;  // never dereferenced
+    return o;
+}
+
+struct Arena {
+    char *base;
+    size_t used;
+    double *take(int64_t elems) {
+        double *p = (double *)(base + used);
+        used += mm::align_up((size_t)elems * sizeof(double), 256);
+        return p;
+    }
+};
+
+size_t node_bytes(int variant, int64_t n, int64_t p, int64_t m) {
+    auto b = [](int64_t e) { return mm::align_up((size_t)e * sizeof(double), 256); };
+    const int64_t hn = n / 2, hp = p / 2, hm = m / 2;
+    size_t s = b(hn * hp) + b(hp * hm) + 7 * b(hn * hm);
+    if (variant == 1) s += 2 * b(hn * hp) + 2 * b(hp * hm);
+    return s;
+}
+
+// Materialise expression `e` over quadrants of `v` into a dense hr x hc buffer.
+int materialize(const Expr &e, const View &v, int64_t hr, int64_t hc, double *out, cudaStream_t st) {
+    CombineArgs c{};
+    for (int q = 0; q < 4; ++q) c.term[q] = quadrant(v, q, hr, hc);
+    c.e = e;
+    c.out = out;
+    c.ldo = hc;
+    c.rows = hr;
+    c.cols = hc;
+    return launch_combine(c, st);
+}
+
+int node(int variant, int depth, int64_t n, int64_t p, int64_t m, const View &A, const View &B, double *C,
+         int64_t ldc, int64_t crows, int64_t ccols, Arena arena, cudaStream_t st) {
+    if (depth == 1) {
+        LevelArgs a{};
+        a.A = A;
+        a.B = B;
+        a.C = C;
+        a.ldc = ldc;
+        a.crows = crows;
+        a.ccols = ccols;
+        a.n = n / 2;
+        a.p = p / 2;
+        a.m = m / 2;
+        a.nprod = 7;
+        if (variant == 0)
+            strassen_products(a.prod);
+        else
+            strassen_winograd_products(a.prod);
+        return launch_level(a, false, st);
+    }
+    const int64_t hn = n / 2, hp = p / 2, hm = m / 2;
+    double *S = arena.take(hn * hp), *T = arena.take(hp * hm);
+    double *H[8];
+    for (int h = 1; h <= 7; ++h) H[h] = arena.take(hn * hm);
+    auto dense = [](const double *ptr, int64_t r, int64_t c) { return View{ptr, c, r, c}; };
+    auto qa = [&](int q) { return quadrant(A, q, hn, hp); };
+    auto qb = [&](int q) { return quadrant(B, q, hp, hm); };
+    int rc = MM_OK;
+    auto child = [&](const View &a, const View &b, double *h) {
+        if (rc == MM_OK) rc = node(variant, depth - 1, hn, hp, hm, a, b, h, hm, hn, hm, arena, st);
+    };
+    auto mat_a = [&](const Expr &e) {
+        if (rc == MM_OK) rc = materialize(e, A, hn, hp, S, st);
+        return dense(S, hn, hp);
+    };
+    auto mat_b = [&](const Expr &e) {
+        if (rc == MM_OK) rc = materialize(e, B, hp, hm, T, st);
+        return dense(T, hp, hm);
+    };
+    auto combine_into = [&](int q, std::initializer_list<int> hs, const Expr &e) {
+        CombineArgs c{};
+        int i = 0;
+        for (int h : hs) c.term[i++] = dense(H[h], hn, hm);
+        c.e = e;
+        const int64_t r0 = (q >> 1) * hn, c0 = (q & 1) * hm;
+        c.out = C + r0 * ldc + c0;
+        c.ldo = ldc;
+        c.rows = std::max<int64_t>(0, std::min<int64_t>(hn, crows - r0));
+        c.cols = std::max<int64_t>(0, std::min<int64_t>(hm, ccols - c0));
+        if (rc == MM_OK) rc = launch_combine(c, st);
+    };
+    if (variant == 0) {
+        child(mat_a(ex({T11, T22, OP_ADD})), mat_b(ex({T11, T22, OP_ADD})), H[1]);
+        child(mat_a(ex({T21, T22, OP_ADD})), qb(T11), H[2]);
+        child(qa(T11), mat_b(ex({T12, T22, OP_SUB})), H[3]);
+        child(qa(T22), mat_b(ex({T21, T11, OP_SUB})), H[4]);
+        child(mat_a(ex({T11, T12, OP_ADD})), qb(T22), H[5]);
+        {
+            View sa = mat_a(ex({T21, T11, OP_SUB}));
+            View tb = mat_b(ex({T11, T12, OP_ADD}));
+            child(sa, tb, H[6]);
+        }
+        {
+            View sa = mat_a(ex({T12, T22, OP_SUB}));
+            View tb = mat_b(ex({T21, T22, OP_ADD}));
+            child(sa, tb, H[7]);
+        }
+        // C11 = ((H1+H4)-H5)+H7, C12 = H3+H5, C21 = H2+H4, C22 = ((H1+H3)-H2)+H6
+        combine_into(T11, {1, 4, 5, 7}, ex({0, 1, OP_ADD, 2, OP_SUB, 3, OP_ADD}));
+        combine_into(T12, {3, 5}, ex({0, 1, OP_ADD}));
+        combine_into(T21, {2, 4}, ex({0, 1, OP_ADD}));
+        combine_into(T22, {1, 3, 2, 6}, ex({0, 1, OP_ADD, 2, OP_SUB, 3, OP_ADD}));
+    } else {
+        double *A1 = arena.take(hn * hp), *A2 = arena.take(hn * hp);
+        double *B1 = arena.take(hp * hm), *B2 = arena.take(hp * hm);
+        // A1 = A11 - A21, A2 = A22 - A1, B1 = B22 - B12, B2 = B1 + B11
+        if (rc == MM_OK) rc = materialize(ex({T11, T21, OP_SUB}), A, hn, hp, A1, st);
+        if (rc == MM_OK) {
+            CombineArgs c{};
+            c.term[0] = qa(T22);
+            c.term[1] = dense(A1, hn, hp);
+            c.e = ex({0, 1, OP_SUB});
+            c.out = A2;
+            c.ldo = hp;
+            c.rows = hn;
+            c.cols = hp;
+            rc = launch_combine(c, st);
+        }
+        if (rc == MM_OK) rc = materialize(ex({T22, T12, OP_SUB}), B, hp, hm, B1, st);
+        if (rc == MM_OK) {
+            CombineArgs c{};
+            c.term[0] = dense(B1, hp, hm);
+            c.term[1] = qb(T11);
+            c.e = ex({0, 1, OP_ADD});
+            c.out = B2;
+            c.ldo = hm;
+            c.rows = hp;
+            c.cols = hm;
+            rc = launch_combine(c, st);
+        }
+        child(qa(T11), qb(T11), H[1]);
+        child(qa(T12), qb(T21), H[2]);
+        child(dense(A2, hn, hp), dense(B2, hp, hm), H[3]);
+        {
+            View sa = mat_a(ex({T21, T22, OP_ADD}));
+            View tb = mat_b(ex({T12, T11, OP_SUB}));
+            child(sa, tb, H[4]);
+        }
+        child(dense(A1, hn, hp), dense(B1, hp, hm), H[5]);
+        if (rc == MM_OK) {  // S = A12 - A2
+            CombineArgs c{};
+            c.term[0] = qa(T12);
+            c.term[1] = dense(A2, hn, hp);
+            c.e = ex({0, 1, OP_SUB});
+            c.out = S;
+            c.ldo = hp;
+            c.rows = hn;
+            c.cols = hp;
+            rc = launch_combine(c, st);
+        }
+        child(dense(S, hn, hp), qb(T22), H[6]);
+        if (rc == MM_OK) {  // T = B21 - B2
+            CombineArgs c{};
+            c.term[0] = qb(T21);
+            c.term[1] = dense(B2, hp, hm);
+            c.e = ex({0, 1, OP_SUB});
+            c.out = T;
+            c.ldo = hm;
+            c.rows = hp;
+            c.cols = hm;
+            rc = launch_combine(c, st);
+        }
+        child(qa(T22), dense(T, hp, hm), H[7]);
+        // C11 = H1+H2, C12 = ((H1+H3)+H4)+H6, C21 = ((H1+H3)+H5)+H7, C22 = ((H1+H3)+H4)+H5
+        combine_into(T11, {1, 2}, ex({0, 1, OP_ADD}));
+        combine_into(T12, {1, 3, 4, 6}, ex({0, 1, OP_ADD, 2, OP_ADD, 3, OP_ADD}));
+        combine_into(T21, {1, 3, 5, 7}, ex({0, 1, OP_ADD, 2, OP_ADD, 3, OP_ADD}));
+        combine_into(T22, {1, 3, 4, 5}, ex({0, 1, OP_ADD, 2, OP_ADD, 3, OP_ADD}));
+    }
+    return rc;
+}
+
+}  // namespace
+
+namespace mm {
+
+int run_naive(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+              int64_t ldc, cudaStream_t st) {
+    LevelArgs a{};
+    a.A = View{A, lda, N, P};
+    a.B = View{B, ldb, P, M};
+    a.C = C;
+    a.ldc = ldc;
+    a.crows = N;
+    a.ccols = M;
+    a.n = N;
+    a.p = P;
+    a.m = M;
+    a.nprod = 1;
+    a.prod[0] = Product{ex({T11}), ex({T11}), 1, {tgt(T11, 1, true)}};
+    return launch_level(a, true, st);
+}
+
+// Depth and padded sizes of the recursion (see mm_strassen in mm.h).
+int strassen_plan(int64_t N, int64_t P, int64_t M, int32_t cutoff, int *depth, int64_t *Np, int64_t *Pp,
+                  int64_t *Mp) {
+    const int64_t X = std::max(N, std::max(P, M));
+    int d = 0;
+    if (cutoff == 0) {  // the paper's rule, square embedding
+        int lg = -1;
+        for (int64_t t = X; t > 0; t >>= 1) ++lg;
+        d = std::max(0, lg - 4);
+        const int64_t Y = ((X >> d) + 1) << d;
+        *depth = d;
+        *Np = *Pp = *Mp = Y;
+    } else {
+        if (cutoff > 0) {
+            while (ceil_div(X, (int64_t)1 << d) > cutoff) ++d;
+        } else {  // tuned: one level per doubling above 1024
+            for (int64_t t = X; t >= 2048 && d < 3; t >>= 1) ++d;
+        }
+        const int64_t q = (int64_t)1 << d;
+        *depth = d;
+        *Np = ceil_div(N, q) * q;
+        *Pp = ceil_div(P, q) * q;
+        *Mp = ceil_div(M, q) * q;
+    }
+    if (*depth > 10) return fail(MM_ERR_UNSUPPORTED, "Strassen depth %d exceeds 10", *depth);
+    int64_t launches = 1;
+    for (int i = 1; i < *depth; ++i) launches *= 7;
+    if (launches > 2401) return fail(MM_ERR_UNSUPPORTED, "Strassen depth %d needs %lld innermost launches (> 2401)",
+                                     *depth, (long long)launches);
+    return MM_OK;
+}
+
+size_t strassen_ws_bytes(int variant, int depth, int64_t Np, int64_t Pp, int64_t Mp) {
+    size_t total = 0;
+    for (int L = 0; L + 2 <= depth; ++L) total += node_bytes(variant, Np >> L, Pp >> L, Mp >> L);
+    return total;
+}
+
+int run_strassen(int variant, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                 int64_t ldb, double *C, int64_t ldc, int depth, int64_t Np, int64_t Pp, int64_t Mp, void *ws,
+                 cudaStream_t st) {
+    if (depth == 0) return run_naive(N, P, M, A, lda, B, ldb, C, ldc, st);
+    Arena arena{(char *)ws, 0};
+    return node(variant, depth, Np, Pp, Mp, View{A, lda, N, P}, View{B, ldb, P, M}, C, ldc, N, M, arena, st);
+}
+
+}  // namespace mm

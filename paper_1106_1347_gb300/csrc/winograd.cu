@@ -1,0 +1,251 @@
+// Sections "WinogradOriginal" and "WinogradScaled".
+//
+//  1. row pass over A: y_i = sum_{j<gamma} RN(A_i,2j A_i,2j+1) (0-based), each
+//     row summed in order by one lane after a shared-memory transpose of
+//     coalesced 32x32 tiles; the scaled form also sums |A_ij| in the same pass
+//     and folds the row maximum into ||A||_inf (NormInf fused into the y pass).
+//  2. column pass over B: z_k = sum_j RN(B_2j,k B_2j+1,k), one thread per
+//     column, coalesced across the warp.  The scaled form runs the NormInf
+//     kernel over B as well.
+//  3. main kernel: C_ik = (sum_j (A_i,2j + B_2j+1,k)(A_i,2j+1 + B_2j,k) - y'_i) - z'_k
+//     (+ RN(A_i,P-1 B_P-1,k) when P is odd).  For the scaled form every CTA
+//     derives Brent's lambda from the two device-resident norms (no host
+//     round trip), multiplies A by 2^lambda and B by 2^-lambda while staging
+//     tiles (MultiplyWithScalar by exact powers of two), and uses
+//     y' = 4^lambda y and z' = 4^-lambda z, which equal the terms of the
+//     scaled matrices bit for bit when nothing over- or underflows.
+// y and z are bit-identical to a sequential evaluation; the paired sum uses
+// one FMA per pair (2 DADD + 1 DFMA per pair per output, the FP64 pipe bound).
+#include "common.cuh"
+
+namespace {
+
+constexpr int kRows = 32;
+
+template <bool kNorm>
+__global__ void __launch_bounds__(32) a_terms_kernel(int64_t N, int64_t P, const double *__restrict__ A, int64_t lda,
+                                                     double *__restrict__ y, unsigned long long *norm_bits) {
+    __shared__ double tile[kRows][kRows + 1];
+    const int lane = threadIdx.x;
+    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    const int64_t nrows = min((int64_t)kRows, N - row0);
+    const int64_t gamma2 = (P / 2) * 2;  // columns that form pairs
+    double next[kRows];
+    auto fetch = [&](int64_t c0) {
+        const int64_t c = c0 + lane;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) next[r] = (r < nrows && c < P) ? A[(row0 + r) * lda + c] : 0.0;
+    };
+    double ys = 0.0, ns = 0.0;
+    fetch(0);
+    for (int64_t c0 = 0; c0 < P; c0 += kRows) {
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) tile[r][lane] = next[r];
+        __syncwarp();
+        if (c0 + kRows < P) fetch(c0 + kRows);
+        const int npair = (int)max((int64_t)0, min((int64_t)kRows, gamma2 - c0)) / 2;
+        for (int j = 0; j < npair; ++j) ys = __dadd_rn(ys, __dmul_rn(tile[lane][2 * j], tile[lane][2 * j + 1]));
+        if (kNorm) {
+            const int ncols = (int)min((int64_t)kRows, P - c0);
+            for (int j = 0; j < ncols; ++j) ns = __dadd_rn(ns, fabs(tile[lane][j]));
+        }
+        __syncwarp();
+    }
+    if (lane < nrows) {
+        y[row0 + lane] = ys;
+        if (kNorm) atomicMax(norm_bits, (unsigned long long)__double_as_longlong(ns));
+    }
+}
+
+__global__ void __launch_bounds__(128) b_terms_kernel(int64_t P, int64_t M, const double *__restrict__ B, int64_t ldb,
+                                                      double *__restrict__ z) {
+    const int64_t k = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (k >= M) return;
+    const int64_t gamma = P / 2;
+    double s = 0.0;
+    int64_t j = 0;
+    for (; j + 4 <= gamma; j += 4) {
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = B[(2 * j + q) * ldb + k];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s = __dadd_rn(s, __dmul_rn(v[2 * q], v[2 * q + 1]));
+    }
+    for (; j < gamma; ++j) s = __dadd_rn(s, __dmul_rn(B[(2 * j) * ldb + k], B[(2 * j + 1) * ldb + k]));
+    z[k] = s;
+}
+
+// Smallest lambda with 1/2 <= 4^lambda a / b <= 2, from frexp pairs (exact).
+__device__ int brent_lambda(double a, double b) {
+    if (!(a > 0.0) || !(b > 0.0) || isinf(a) || isinf(b)) return 0;
+    int ea, eb;
+    const double fa = frexp(a, &ea), fb = frexp(b, &eb);
+    int lam = (eb - ea - 1) / 2 - 2;
+    for (int it = 0; it < 8; ++it) {
+        const int ex = ea + 2 * lam + 1;
+        if (ex > eb || (ex == eb && fa >= fb)) break;
+        ++lam;
+    }
+    return lam;
+}
+
+constexpr int TM = 64, TN = 64, TK = 16;
+
+template <bool kScaled>
+__global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int64_t M, const double *__restrict__ A,
+                                                       int64_t lda, const double *__restrict__ B, int64_t ldb,
+                                                       double *__restrict__ C, int64_t ldc,
+                                                       const double *__restrict__ y, const double *__restrict__ z,
+                                                       const double *norms, int32_t *lambda_out) {
+    __shared__ double As[TM][TK + 1];
+    __shared__ double Bs[TK][TN];
+    __shared__ double s_scale[2];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t i0 = (int64_t)blockIdx.y * TM, j0 = (int64_t)blockIdx.x * TN;
+    const int64_t K2 = (P / 2) * 2;
+    if (tid == 0) {
+        double sa = 1.0, sb = 1.0;
+        if (kScaled) {
+            const int lam = brent_lambda(norms[0], norms[1]);
+            sa = ldexp(1.0, lam);
+            sb = ldexp(1.0, -lam);
+            if (lambda_out && blockIdx.x == 0 && blockIdx.y == 0) *lambda_out = lam;
+        }
+        s_scale[0] = sa;
+        s_scale[1] = sb;
+    }
+    __syncthreads();
+    const double sa = s_scale[0], sb = s_scale[1];
+    double acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+    double ra[4], rb[4];
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            const int64_t gi = i0 + (e >> 4), gk = k0 + (e & 15);
+            double av = (gi < N && gk < K2) ? A[gi * lda + gk] : 0.0;
+            const int64_t bk = k0 + (e >> 6), bj = j0 + (e & 63);
+            double bv = (bk < K2 && bj < M) ? B[bk * ldb + bj] : 0.0;
+            if (kScaled) {
+                av *= sa;
+                bv *= sb;
+            }
+            ra[q] = av;
+            rb[q] = bv;
+        }
+    };
+    if (K2 > 0) fetch(0);
+    for (int64_t k0 = 0; k0 < K2; k0 += TK) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            As[e >> 4][e & 15] = ra[q];
+            Bs[e >> 6][e & 63] = rb[q];
+        }
+        __syncthreads();
+        if (k0 + TK < K2) fetch(k0 + TK);
+        const int np = (int)min((int64_t)TK, K2 - k0) / 2;
+        for (int jj = 0; jj < np; ++jj) {
+            double ae[4], ao[4], be[4], bo[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                ae[r] = As[ty + 16 * r][2 * jj];
+                ao[r] = As[ty + 16 * r][2 * jj + 1];
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                be[c] = Bs[2 * jj][tx + 16 * c];
+                bo[c] = Bs[2 * jj + 1][tx + 16 * c];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const double s1 = __dadd_rn(ae[r], bo[c]);
+                    const double s2 = __dadd_rn(ao[r], be[c]);
+                    acc[r][c] = fma(s1, s2, acc[r][c]);
+                }
+        }
+    }
+    const bool odd = (P & 1) != 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t i = i0 + ty + 16 * r;
+        if (i >= N) continue;
+        double yi = y[i];
+        double alast = 0.0;
+        if (kScaled) yi = (yi * sa) * sa;
+        if (odd) alast = A[i * lda + (P - 1)] * sa;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t k = j0 + tx + 16 * c;
+            if (k >= M) continue;
+            double zk = z[k];
+            if (kScaled) zk = (zk * sb) * sb;
+            double v = __dsub_rn(__dsub_rn(acc[r][c], yi), zk);
+            if (odd) v = __dadd_rn(v, __dmul_rn(alast, B[(P - 1) * ldb + k] * sb));
+            C[i * ldc + k] = v;
+        }
+    }
+}
+
+}  // namespace
+
+namespace mm {
+
+size_t winograd_ws_bytes(int64_t N, int64_t P, int64_t M, bool scaled) {
+    (void)P;
+    if (N < 0 || M < 0) return 0;
+    size_t b = align_up((size_t)std::max<int64_t>(N, 1) * 8, 256) + align_up((size_t)std::max<int64_t>(M, 1) * 8, 256);
+    if (scaled) b += 256;
+    return b;
+}
+
+int run_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                 double *C, int64_t ldc, bool scaled, int32_t *lambda_out, void *ws, cudaStream_t st) {
+    char *w = (char *)ws;
+    double *y = (double *)w;
+    double *z = (double *)(w + align_up((size_t)std::max<int64_t>(N, 1) * 8, 256));
+    double *norms = scaled ? (double *)(w + align_up((size_t)std::max<int64_t>(N, 1) * 8, 256) +
+                                        align_up((size_t)std::max<int64_t>(M, 1) * 8, 256))
+                           : nullptr;
+    int rc;
+    if (scaled) {
+        cudaError_t e = cudaMemsetAsync(norms, 0, 2 * sizeof(double), st);
+        if (e != cudaSuccess) return cuda_fail(e, "mm_winograd_scaled");
+        rc = launch("winograd_a_terms_norm", st, [&] {
+            a_terms_kernel<true><<<(unsigned)ceil_div(N, kRows), 32, 0, st>>>(N, P, A, lda, y,
+                                                                             (unsigned long long *)norms);
+        });
+        if (rc) return rc;
+        if (P > 0) {
+            // ||B||_inf into norms[1] (NormInf over the rows of B).
+            rc = run_norm_inf(P, M, B, ldb, norms + 1, st);
+            if (rc) return rc;
+        }
+    } else {
+        rc = launch("winograd_a_terms", st, [&] {
+            a_terms_kernel<false><<<(unsigned)ceil_div(N, kRows), 32, 0, st>>>(N, P, A, lda, y, nullptr);
+        });
+        if (rc) return rc;
+    }
+    rc = launch("winograd_b_terms", st,
+                [&] { b_terms_kernel<<<(unsigned)ceil_div(M, 128), 128, 0, st>>>(P, M, B, ldb, z); });
+    if (rc) return rc;
+    dim3 grid((unsigned)ceil_div(M, TN), (unsigned)ceil_div(N, TM));
+    if (grid.y > 65535) return fail(MM_ERR_UNSUPPORTED, "mm_winograd: N too large for one launch");
+    if (scaled)
+        return launch("winograd_scaled_f64", st, [&] {
+            winograd_kernel<true><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, norms, lambda_out);
+        });
+    return launch("winograd_f64", st, [&] {
+        winograd_kernel<false><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, nullptr, nullptr);
+    });
+}
+
+}  // namespace mm

@@ -1,0 +1,261 @@
+"""GPU parity: every method through the C ABI against the CPU oracle, element by
+element, on seeded inputs.  Bar: bit-exact for integer-valued inputs (every
+method), for NormInf, Kahan, Winograd's y/z path ... and for the emulated
+product (its definition is exact integer arithmetic plus one rounding); within
+||C - C_ref||_inf / (||A||_inf ||B||_inf) <= 1e-14 for the FP64 methods whose
+GPU evaluation order differs from the oracle's (FMA/MMA blocking)."""
+import numpy as np
+import pytest
+
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-14
+
+
+@pytest.fixture(scope="module")
+def mm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1106_1347_gb300 import build
+
+    build.build()
+    import paper_1106_1347_gb300 as mm
+
+    mm.lib()
+    return mm
+
+
+def dev(x):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def pair(n, p, m, kind, tag):
+    if kind == "int":
+        return S.integers(n, p, S.stream_seed(0, 2 * tag)), S.integers(p, m, S.stream_seed(0, 2 * tag + 1))
+    if kind == "uni":
+        return S.uniform(n, p, S.stream_seed(0, 2 * tag)), S.uniform(p, m, S.stream_seed(0, 2 * tag + 1))
+    if kind == "log":
+        return S.loguniform(n, p, S.stream_seed(3, 2 * tag)), S.loguniform(p, m, S.stream_seed(3, 2 * tag + 1))
+    raise ValueError(kind)
+
+
+SHAPES = [(1, 1, 1), (3, 5, 2), (64, 64, 64), (65, 17, 33), (128, 129, 63), (256, 256, 256), (200, 333, 150)]
+
+
+# ----------------------------------------------------------------- NormInf
+
+@pytest.mark.parametrize("shape", [(1, 1), (31, 33), (64, 1000), (257, 129), (1000, 7)])
+def test_norm_inf_bit_exact(mm, orc, shape):
+    a = S.uniform(*shape, S.stream_seed(0, 900 + shape[0])) * 3.0
+    assert float(host(mm.norm_inf(dev(a)))) == orc.norm_inf(a)
+    g = np.array([[2.0 ** 53, 1.0, 1.0], [3.0, -4.0, 0.5]])
+    assert float(host(mm.norm_inf(dev(g)))) == orc.norm_inf(g)
+
+
+# ------------------------------------------------------------------ naive
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_naive_integer_bit_exact(mm, orc, shape):
+    a, b = pair(*shape, "int", 1)
+    assert np.array_equal(host(mm.naive(dev(a), dev(b))), orc.naiv_standard(a, b))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_naive_uniform_within_tolerance(mm, orc, shape):
+    a, b = pair(*shape, "uni", 2)
+    got = host(mm.naive(dev(a), dev(b)))
+    assert orc.rel_inf_error(got, orc.naiv_standard(a, b), a, b) <= TOL
+
+
+# ------------------------------------------------------------------ Kahan
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_kahan_bit_exact_on_reals(mm, orc, shape):
+    a, b = pair(*shape, "uni", 3)
+    assert np.array_equal(host(mm.kahan(dev(a), dev(b))), orc.naiv_kahan(a, b))
+
+
+def test_kahan_discriminator(mm):
+    a = np.array([[2.0 ** 53, 1.0, -(2.0 ** 53)]])
+    assert host(mm.kahan(dev(a), dev(np.ones((3, 1)))))[0, 0] == 1.0
+
+
+# --------------------------------------------------------------- Winograd
+
+@pytest.mark.parametrize("shape", SHAPES + [(33, 2047 % 97, 40)])
+def test_winograd_integer_bit_exact(mm, orc, shape):
+    a, b = pair(*shape, "int", 4)
+    assert np.array_equal(host(mm.winograd(dev(a), dev(b))), orc.winograd_original(a, b))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_winograd_uniform_within_tolerance(mm, orc, shape):
+    a, b = pair(*shape, "uni", 5)
+    got = host(mm.winograd(dev(a), dev(b)))
+    assert orc.rel_inf_error(got, orc.winograd_original(a, b), a, b) <= TOL
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_winograd_scaled_lambda_and_result(mm, orc, shape):
+    a, b = pair(*shape, "uni", 6)
+    b = b * 1024.0
+    c, lam = mm.winograd_scaled(dev(a), dev(b), return_lambda=True)
+    ref, lam_ref = orc.winograd_scaled(a, b)
+    assert int(host(lam)[0]) == lam_ref
+    assert orc.rel_inf_error(host(c), ref, a, b) <= TOL
+
+
+def test_winograd_scaled_paper_tie(mm, orc):
+    a = S.uniform(40, 40, 77)
+    c, lam = mm.winograd_scaled(dev(a), dev(8.0 * a), return_lambda=True)
+    assert int(host(lam)[0]) == 1
+    ai = S.integers(33, 21, 78)
+    bi = S.integers(21, 19, 79) * 64.0
+    assert np.array_equal(host(mm.winograd_scaled(dev(ai), dev(bi))), ai @ bi)
+
+
+# --------------------------------------------------------------- Strassen
+
+STRASSEN = [("strassen", "strassen_naiv"), ("strassen_winograd", "strassen_winograd")]
+
+
+@pytest.mark.parametrize("gpu_name,orc_name", STRASSEN)
+@pytest.mark.parametrize("shape", [(17, 33, 12), (100, 100, 100), (200, 200, 200), (129, 64, 77)])
+def test_strassen_paper_rule(mm, orc, gpu_name, orc_name, shape):
+    ai, bi = pair(*shape, "int", 7)
+    assert np.array_equal(host(getattr(mm, gpu_name)(dev(ai), dev(bi), cutoff=0)), ai @ bi)
+    a, b = pair(*shape, "uni", 8)
+    got = host(getattr(mm, gpu_name)(dev(a), dev(b), cutoff=0))
+    ref = getattr(orc, orc_name)(a, b)
+    assert orc.rel_inf_error(got, ref, a, b) <= TOL
+
+
+@pytest.mark.parametrize("gpu_name,orc_name", STRASSEN)
+@pytest.mark.parametrize("shape,cutoff", [((256, 256, 256), 128), ((256, 256, 256), 64), ((300, 257, 190), 80),
+                                          ((64, 512, 96), 130), ((1000, 600, 500), 300)])
+def test_strassen_cutoff_depths(mm, orc, gpu_name, orc_name, shape, cutoff):
+    n, p, m = shape
+    X = max(shape)
+    depth = 0
+    while -(-X // (1 << depth)) > cutoff:
+        depth += 1
+    q = 1 << depth
+    padded = tuple(-(-d // q) * q for d in shape)
+    ai, bi = pair(*shape, "int", 9)
+    assert np.array_equal(host(getattr(mm, gpu_name)(dev(ai), dev(bi), cutoff=cutoff)), ai @ bi)
+    a, b = pair(*shape, "uni", 10)
+    got = host(getattr(mm, gpu_name)(dev(a), dev(b), cutoff=cutoff))
+    ref = getattr(orc, orc_name)(a, b, depth=depth, padded=padded)
+    assert orc.rel_inf_error(got, ref, a, b) <= TOL
+
+
+@pytest.mark.parametrize("gpu_name", ["strassen", "strassen_winograd"])
+def test_strassen_tuned_default(mm, orc, gpu_name):
+    a, b = pair(512, 384, 448, "uni", 11)
+    got = host(getattr(mm, gpu_name)(dev(a), dev(b)))
+    assert orc.rel_inf_error(got, orc.dot2_product(a, b), a, b) <= TOL
+
+
+# ---------------------------------------------------------------- emulated
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (5, 3, 7), (128, 32, 64), (129, 33, 65), (200, 333, 150),
+                                   (256, 1100, 130)])
+@pytest.mark.parametrize("s", [8, 3])
+def test_emulated_bit_exact_vs_oracle(mm, orc, shape, s):
+    a, b = pair(*shape, "log", 12)
+    got = host(mm.emulated(dev(a), dev(b), nslices=s))
+    assert np.array_equal(got, orc.split_product(a, b, 7, s))
+
+
+@pytest.mark.parametrize("s", [1, 2, 5, 6, 7])
+def test_emulated_other_slice_counts(mm, orc, s):
+    a, b = pair(130, 200, 70, "uni", 13)
+    assert np.array_equal(host(mm.emulated(dev(a), dev(b), nslices=s)), orc.split_product(a, b, 7, s))
+
+
+def test_emulated_integers_exact(mm):
+    a, b = pair(150, 520, 90, "int", 14)
+    assert np.array_equal(host(mm.emulated(dev(a), dev(b), nslices=2)), a @ b)
+
+
+def test_emulated_tier_accuracy(mm, orc):
+    a, b = pair(192, 700, 160, "log", 15)
+    truth = orc.dot2_product(a, b)
+    got = host(mm.emulated(dev(a), dev(b), tier=1e-14))
+    assert orc.rel_inf_error(got, truth, a, b) <= TOL
+    got6 = host(mm.emulated(dev(a), dev(b), tier=1e-6))
+    assert orc.rel_inf_error(got6, truth, a, b) <= 1e-6
+
+
+def test_emulated_multi_chunk_exactness(mm, orc):
+    """P spans several exact K-chunks (512 for 8 slices) and a ragged K tail."""
+    a, b = pair(130, 1700, 66, "uni", 16)
+    assert np.array_equal(host(mm.emulated(dev(a), dev(b), nslices=8)), orc.split_product(a, b, 7, 8))
+
+
+def test_emulated_positive_worst_case_sums(mm, orc):
+    """All-positive operands make every digit sum grow linearly: the chunk drains
+    must keep the FP32 accumulation exact."""
+    a = np.abs(S.uniform(128, 1500, 171)) + 0.5
+    b = np.abs(S.uniform(1500, 64, 172)) + 0.5
+    assert np.array_equal(host(mm.emulated(dev(a), dev(b), nslices=8)), orc.split_product(a, b, 7, 8))
+
+
+# ------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("name", ["naive", "kahan", "winograd", "winograd_scaled", "strassen", "strassen_winograd",
+                                  "emulated"])
+def test_degenerate_shapes(mm, name):
+    import torch
+
+    fn = getattr(mm, name)
+    a = torch.zeros((4, 0), dtype=torch.float64, device="cuda")
+    b = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    out = torch.full((4, 3), 7.0, dtype=torch.float64, device="cuda")
+    fn(a, b, out=out)
+    assert torch.count_nonzero(out).item() == 0
+    a = torch.zeros((0, 5), dtype=torch.float64, device="cuda")
+    b = torch.ones((5, 3), dtype=torch.float64, device="cuda")
+    assert fn(a, b).shape == (0, 3)
+
+
+@pytest.mark.parametrize("name", ["naive", "kahan", "winograd", "strassen", "emulated"])
+def test_strided_views(mm, orc, name):
+    """Leading dimensions larger than the column count (sub-matrix views)."""
+    big_a = S.integers(90, 120, 181)
+    big_b = S.integers(110, 100, 182)
+    a, b = big_a[5:75, 7:100], big_b[3:96, 11:80]
+    ta, tb = dev(big_a)[5:75, 7:100], dev(big_b)[3:96, 11:80]
+    big_c = dev(np.zeros((80, 90)))
+    out = big_c[4:74, 9:78]
+    kw = {"nslices": 1} if name == "emulated" else {}
+    getattr(mm, name)(ta, tb, out=out, **kw)
+    got = host(big_c)
+    assert np.array_equal(got[4:74, 9:78], a @ b)
+    mask = np.ones_like(got, dtype=bool)
+    mask[4:74, 9:78] = False
+    assert np.all(got[mask] == 0.0)
+
+
+def test_argument_errors(mm):
+    import torch
+
+    a = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(mm.MMError):
+        mm.naive(a, a, out=a)  # C overlaps A
+    with pytest.raises(ValueError):
+        mm.naive(a, torch.zeros((5, 4), dtype=torch.float64, device="cuda"))
+
+
+def test_no_timeouts_raised(mm):
+    assert mm.device_status() == 0
