@@ -1,0 +1,365 @@
+"""Benchmark: FP64-accurate GEMM on one GB300 (or N independent replicas).
+
+One step = one FP64-accurate product C = A B, N = P = M = 8192, entries
++-2^E (1 + f) with E uniform in [-20, 19] (log-uniform magnitudes, random
+sign), through the library's split-precision path (mm_emulated, 8 BF16
+slices, tcgen05): split of A and B, slice products, exact recombination.
+The same line reports the plain FP64 product (mm_naive, FP64 tensor-core MMA)
+on the same inputs, the measured normwise error of both on sampled rows, the
+dominant kernel against its roofline, an end-to-end number through the C ABI
+with host buffers, and the CPU oracle timed on this machine's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 it runs under torchrun as N independent replicas (the product does
+not exchange data between GPUs), barriers and synchronises around the timed
+region and reports the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "split-precision vs plain FP64 GEMM TFLOP/s at rel ∞-err ≤1e-14; serve p50/p99 ms"
+N = P = M = 8192
+SLICES = 8
+WORKLOAD = "fp64-accurate GEMM 8192x8192x8192, log-uniform |a| in 2^-20..2^20 with random sign"
+DOMINANT = "emu_slice_gemm_tcgen05"
+PROFILE_FILE = os.path.join(ROOT, "profiles", "emu_slice_gemm_tcgen05_8192.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_1106_1347_gb300", "csrc", "emulated.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--n", type=int, default=8192, help="N = P = M (profiling runs use a smaller case)")
+    ap.add_argument("--quick", action="store_true", help="only the timed product (for profiler captures)")
+    args = ap.parse_args()
+    global N, P, M, WORKLOAD
+    if args.n != 8192:
+        N = P = M = args.n
+        WORKLOAD = WORKLOAD.replace("8192x8192x8192", f"{N}x{N}x{N}")
+    return args
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_tflops(a, b, seconds, threads):
+    """Times the CPU oracle's NaivStandard (the paper's plain FP64 product) on a
+    row sample of the workload, rows split across `threads` Python threads (the
+    ctypes call releases the GIL).  Returns (TFLOP/s, rows, threads, elapsed)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.naiv_standard(a[:1], b)
+    one_row = max(time.perf_counter() - t0, 1e-3)
+    rows = int(max(threads, min(a.shape[0], seconds * threads / one_row)))
+    rows -= rows % threads
+    rows = max(rows, threads)
+    blocks = np.array_split(np.arange(rows), threads)
+    def work(idx):
+        oracle.naiv_standard(a[idx[0]: idx[-1] + 1], b)
+    ths = [threading.Thread(target=work, args=(blk,)) for blk in blocks]
+    t0 = time.perf_counter()
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    el = time.perf_counter() - t0
+    return 2.0 * rows * b.shape[0] * b.shape[1] / el / 1e12, rows, threads, el
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def dominant_traffic(ntiles_scale=1.0):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    try:
+        prof = json.load(open(PROFILE_FILE))
+    except (OSError, ValueError):
+        return None
+    if prof.get("kernel_source_sha256_16") != source_hash(KERNEL_SRC):
+        return None
+    return prof.get("dram_bytes_per_launch_full_size")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def make_inputs():
+    import synthetic as S
+
+    a = S.loguniform(N, P, S.stream_seed(3, 0))
+    b = S.loguniform(P, M, S.stream_seed(3, 1))
+    return a, b
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    a, b = make_inputs()
+    cores = host_cores()
+    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_tflops(a, b, per_step / 4, cores)
+    vals, rows_used, t_total = [], 0, 0.0
+    for _ in range(args.steps):
+        v, rows, thr, el = cpu_oracle_tflops(a, b, per_step, cores)
+        vals.append(v)
+        rows_used = rows
+        t_total += el
+    value = statistics.median(vals)
+    sample = f"{rows_used} of {N} rows of C per step (all {P}x{M} of B), NaivStandard, {cores} threads over row blocks"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "P": P, "M": M, "oracle": "NaivStandard (plain C, sequential sums)"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def sampled_error(c_dev, a, b, norm_a, norm_b, rows):
+    """max over sampled rows i of sum_j |C_ij - T_ij| / (||A|| ||B||), T the
+    oracle's Dot2 product on those rows (a sample of the inf-norm's rows)."""
+    import numpy as np
+
+    import oracle
+
+    truth = oracle.dot2_product(a[rows], b)
+    got = c_dev[rows].cpu().numpy() if hasattr(c_dev, "cpu") else c_dev[rows]
+    return float(np.abs(got - truth).sum(axis=1).max() / (norm_a * norm_b))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1106_1347_gb300 as mm
+    from paper_1106_1347_gb300 import build as mmbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mmbuild.build()
+    a, b = make_inputs()
+    ta = torch.from_numpy(a).to(dev)
+    tb = torch.from_numpy(b).to(dev)
+    c = torch.empty((N, M), dtype=torch.float64, device=dev)
+    ws_bytes = mm.lib().mm_emulated_workspace_bytes(N, P, M, 0, SLICES, 1e-14)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lib = mm.lib()
+    import ctypes
+
+    def step(out=c):
+        rc = lib.mm_emulated(N, P, M, ctypes.c_void_p(ta.data_ptr()), P, ctypes.c_void_p(tb.data_ptr()), M,
+                             ctypes.c_void_p(out.data_ptr()), M, 0, SLICES, 1e-14, ctypes.c_void_p(ws.data_ptr()),
+                             ws_bytes, ctypes.c_void_p(stream.cuda_stream))
+        if rc != 0:
+            raise RuntimeError(lib.mm_last_error().decode())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk, mm.profile() as prof:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    flop = 2.0 * N * P * M
+    value = flop * args.steps * world / (ms * 1e-3) / 1e12
+
+    # Dominant kernel against its roofline (events bracket each launch on its stream).
+    launches, kms = prof.stats.get(DOMINANT, (0, 0.0))
+    pairs = SLICES * (SLICES + 1) // 2
+    pk, pk_kind = peaks()
+    tensor_flop_per_launch = pairs * flop
+    achieved = tensor_flop_per_launch / (kms / max(launches, 1) * 1e-3) / 1e12 if launches else None
+    peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": dominant_traffic(),
+                "kernel": DOMINANT, "peak_source": f"{pk_kind} bf16_tflops_sustained",
+                "algorithmic_unit": f"{pairs} slice pairs x 2NPM BF16 flops per launch"}
+    gpu_launches = sum(v[0] for v in prof.stats.values())
+    kernel_ms = {k: round(v[1] / max(v[0], 1), 4) for k, v in prof.stats.items()}
+
+    # Accuracy of this run (sampled rows) and the plain FP64 product on the same inputs.
+    out = {}
+    if rank == 0 and not args.quick:
+        norm_a = float(mm.norm_inf(ta).item())
+        norm_b = float(mm.norm_inf(tb).item())
+        rows = np.arange(0, N, N // 4)[:4]
+        err_emu = sampled_error(c, a, b, norm_a, norm_b, rows)
+        cn = torch.empty_like(c)
+        mm.naive(ta, tb, out=cn)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(2):
+            mm.naive(ta, tb, out=cn)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = f0.elapsed_time(f1) / 2
+        err_plain = sampled_error(cn, a, b, norm_a, norm_b, rows)
+        out["plain_fp64"] = {"value": flop / (plain_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms": plain_ms,
+                             "kernel": "gemm_f64_dmma (mma.sync m8n8k4 f64)", "rel_inf_err_sampled": err_plain}
+        out["accuracy"] = {"rel_inf_err_sampled": err_emu, "rows_sampled": [int(r) for r in rows],
+                           "target": 1e-14, "reference": "oracle Dot2 product on the sampled rows"}
+        del cn
+
+        # End to end through the C ABI with host buffers: H2D of A and B from pinned
+        # memory, the product, D2H of C, every step.
+        ha = torch.from_numpy(a).pin_memory()
+        hb = torch.from_numpy(b).pin_memory()
+        hc = torch.empty((N, M), dtype=torch.float64).pin_memory()
+        e2e_steps = max(3, min(10, args.steps))
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(e2e_steps):
+            ta.copy_(ha, non_blocking=True)
+            tb.copy_(hb, non_blocking=True)
+            step()
+            hc.copy_(c, non_blocking=True)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = g0.elapsed_time(g1) / e2e_steps
+        out["e2e"] = {"value": flop / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                      "h2d_bytes_per_step": int(a.nbytes + b.nbytes), "d2h_bytes_per_step": int(N * M * 8)}
+
+        cores = host_cores()
+        v, rows_used, thr, el = cpu_oracle_tflops(a, b, args.cpu_seconds, cores)
+        out["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": thr, "kind": "oracle",
+                               "sample": f"{rows_used} of {N} rows of C (NaivStandard, plain C), {el:.1f} s"}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "precision": "FP64-accurate: 8 BF16 slices, exact FP32 TMEM chunks, exact int64 recombination",
+        "config": {"workload": WORKLOAD, "N": N, "P": P, "M": M, "slices": SLICES, "beta": 7,
+                   "parallelism": "replicas" if world > 1 else "single", "l2": "inputs (1 GiB) larger than L2"},
+        "roofline": roofline, "kernel_ms_per_launch": kernel_ms, "gpu_launches": gpu_launches,
+        "clocks": clk.summary(),
+    }
+    line.update(out)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

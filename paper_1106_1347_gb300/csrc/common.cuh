@@ -197,17 +197,19 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 // Shared-memory matrix descriptor for tcgen05 (K-major operand, swizzled):
 // start address >> 4 in bits 0-13, leading byte offset >> 4 in 16-29 (unused
-// for swizzled K-major), stride byte offset >> 4 in 32-45, version 1 in bits
-// 46-47, base offset 0, layout type in bits 61-63 (4 = 64-byte swizzle).
-__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+// for swizzled K-major), stride byte offset >> 4 in 32-45 (distance between
+// 8-row groups), version 1 in bits 46-47, base offset 0, layout type in bits
+// 61-63 (4 = 64-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t row_bytes, uint32_t layout) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
     d |= (uint64_t)(16 >> 4) << 16;
-    d |= (uint64_t)(512 >> 4) << 32;  // 8 rows x 64 bytes between 8-row groups
+    d |= (uint64_t)((8 * row_bytes) >> 4) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)4 << 61;
+    d |= (uint64_t)layout << 61;
     return d;
 }
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) { return smem_desc_kmajor(saddr, 64, 4); }
 
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
 // and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in
