@@ -158,6 +158,28 @@ int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, c
 int mm_emulated_slices(int32_t kind, int32_t nslices, double tier);
 
 /*
+ * Allocation-free variant of mm_emulated (the paper has no counterpart; this
+ * is a deployment convenience).  For callers that cannot allocate a device
+ * workspace -- a host application that owns the device's whole memory pool,
+ * or a loop that must not allocate -- the scratch space lives in a fixed
+ * static device array of mm_emulated_noalloc_capacity() bytes (64 MiB) that
+ * every GPU loading the library holds until the process exits.  Same
+ * arguments and result as mm_emulated minus (ws, ws_bytes).
+ *   - Products whose mm_emulated_workspace_bytes exceeds the capacity return
+ *     MM_ERR_NOMEM (about N = P = M = 1400 with 8 slices); use mm_emulated.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Calls never allocate or free memory, but they all share the one array:
+ *     calls that overlap on the GPU (other streams, other threads on the same
+ *     device) race on it, so the caller must serialise them.
+ */
+int mm_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                        int64_t ldb, double *C, int64_t ldc, int32_t kind, int32_t nslices, double tier,
+                        void *stream);
+size_t mm_emulated_noalloc_capacity(void);
+
+/*
  * Kernel-level timing (measurement support).  While enabled, every kernel the
  * library launches on any stream is bracketed by CUDA events recorded on that
  * stream.  mm_profile_read synchronises those events and fills up to `cap`

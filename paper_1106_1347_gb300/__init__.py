@@ -14,7 +14,7 @@ import ctypes
 from ._native import KernelStat, MMError, check, lib
 
 __all__ = ["naive", "kahan", "winograd", "winograd_scaled", "strassen", "strassen_winograd", "norm_inf",
-           "emulated", "emulated_slices", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
+           "emulated", "emulated_noalloc", "emulated_slices", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
            "SLICE_FP8E4M3"]
 
 SLICE_BF16 = 0
@@ -151,6 +151,16 @@ def emulated(a, b, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
     ws = _ws(need, a.device)
     check("mm_emulated", lib().mm_emulated(*_gemm_args(a, b, c, n, p, m), kind, nslices, float(tier), _ptr(ws), need,
                                            _stream(a.device)))
+    return c
+
+
+def emulated_noalloc(a, b, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
+    """mm_emulated with its scratch in the library's fixed 64 MiB device array
+    instead of a workspace (for callers that cannot allocate device memory).
+    Calls sharing a device must not overlap on the GPU; see include/mm.h."""
+    a, b, c, n, p, m = _prep(a, b, out)
+    check("mm_emulated_noalloc", lib().mm_emulated_noalloc(*_gemm_args(a, b, c, n, p, m), kind, nslices, float(tier),
+                                                           _stream(a.device)))
     return c
 
 

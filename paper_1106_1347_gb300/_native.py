@@ -40,6 +40,8 @@ SIGNATURES = {
     "mm_emulated_workspace_bytes": (sz, [i64, i64, i64, i32, i32, dbl]),
     "mm_emulated": (ctypes.c_int, GEMM + [i32, i32, dbl, vp, sz, vp]),
     "mm_emulated_slices": (ctypes.c_int, [i32, i32, dbl]),
+    "mm_emulated_noalloc": (ctypes.c_int, GEMM + [i32, i32, dbl, vp]),
+    "mm_emulated_noalloc_capacity": (sz, []),
     "mm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mm_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelStat), i32]),
 }

@@ -287,6 +287,26 @@ int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, c
     return run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, ws, st);
 }
 
+int mm_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                        int64_t ldb, double *C, int64_t ldc, int32_t kind, int32_t nslices, double tier,
+                        void *stream) {
+    int rc = check_gemm_args("mm_emulated_noalloc", N, P, M, A, lda, B, ldb, C, ldc);
+    if (rc) return rc;
+    if (kind == MM_SLICE_FP8E4M3)
+        return fail(MM_ERR_UNSUPPORTED, "mm_emulated_noalloc: FP8-E4M3 slices are not built");
+    if (kind != MM_SLICE_BF16) return fail(MM_ERR_ARG, "mm_emulated_noalloc: unknown slice kind %d", kind);
+    if (nslices < 0 || nslices > 8) return fail(MM_ERR_ARG, "mm_emulated_noalloc: nslices must be 0..8");
+    if (nslices == 0 && !(tier > 0.0))
+        return fail(MM_ERR_ARG, "mm_emulated_noalloc: tier must be > 0 when nslices == 0");
+    const int s = emulated_slices(kind, nslices, tier);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N == 0 || M == 0) return MM_OK;
+    if (P == 0) return run_zero(N, M, C, ldc, st);
+    return run_emulated_noalloc(N, P, M, A, lda, B, ldb, C, ldc, s, st);
+}
+
+size_t mm_emulated_noalloc_capacity(void) { return emulated_noalloc_capacity(); }
+
 int mm_profile_enable(int on) {
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof_on = on != 0;

@@ -81,6 +81,9 @@ int emulated_slices(int32_t kind, int32_t nslices, double tier);
 size_t emulated_ws_bytes(int64_t N, int64_t P, int64_t M, int s);
 int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
                  double *C, int64_t ldc, int s, void *ws, cudaStream_t st);
+size_t emulated_noalloc_capacity();
+int run_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                         int64_t ldb, double *C, int64_t ldc, int s, cudaStream_t st);
 
 }  // namespace mm
 

@@ -531,3 +531,61 @@ int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
 }
 
 }  // namespace mm
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the emulated product.
+//
+// Some callers cannot allocate device memory for a workspace: for example a
+// host application that owns every byte of the device's memory through its
+// own pool and forbids other allocations, or a latency-critical loop in which
+// an allocation (and the synchronisation it can imply) is not acceptable.
+// For them the scratch space -- the row/column exponents, the column maxima
+// and the BF16 slices -- lives in this fixed device array instead of a
+// caller-supplied workspace.  Every GPU that loads the library holds these
+// 64 MiB until the process exits.  All calls share the array, so calls that
+// overlap on the GPU (different streams, or different host threads on the same
+// device) race on it and must be serialised by the caller.
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch on the current device, looked up once per
+// device (the first call on each device does this set-up).
+static int noalloc_scratch_ptr(void **out) {
+    static std::mutex mu;
+    static void *ptrs[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return mm::cuda_fail(e, "mm_emulated_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 64) return mm::fail(MM_ERR_UNSUPPORTED, "mm_emulated_noalloc: device index %d", dev);
+    std::lock_guard<std::mutex> g(mu);
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return mm::cuda_fail(e, "mm_emulated_noalloc: cudaGetSymbolAddress");
+        ptrs[dev] = p;
+    }
+    *out = ptrs[dev];
+    return MM_OK;
+}
+
+namespace mm {
+
+size_t emulated_noalloc_capacity() { return kNoAllocScratchBytes; }
+
+int run_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                         int64_t ldb, double *C, int64_t ldc, int s, cudaStream_t st) {
+    const size_t need = emulated_ws_bytes(N, P, M, s);
+    if (need > kNoAllocScratchBytes)
+        return fail(MM_ERR_NOMEM,
+                    "mm_emulated_noalloc: this product needs %zu bytes of scratch, more than the %zu-byte static "
+                    "array; call mm_emulated with a workspace instead",
+                    need, kNoAllocScratchBytes);
+    void *scratch = nullptr;
+    int rc = noalloc_scratch_ptr(&scratch);
+    if (rc) return rc;
+    // The only region that must start at zero (the column maxima) is cleared by
+    // run_emulated itself on every call; everything else is fully rewritten.
+    return run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, scratch, st);
+}
+
+}  // namespace mm
