@@ -180,6 +180,90 @@ int mm_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_
 size_t mm_emulated_noalloc_capacity(void);
 
 /*
+ * Grouped FP64-accurate products (spec batching; no counterpart in the
+ * paper): `count` independent products C_g = A_g B_g of uneven shapes, each
+ * with the mm_emulated definition and one common slice count, in one launch
+ * of each of the four kernels (split of A, column maxima and split of B, slice
+ * products).  Each problem obeys the mm_emulated argument rules; problems
+ * with N == 0 or M == 0 are skipped and P == 0 writes zeros.  The outputs must
+ * not overlap each other or any input.  Results are bit-identical to calling
+ * mm_emulated on each problem.  The host writes a table of the problems into
+ * the workspace with one host-to-device copy before the launches.
+ */
+typedef struct {
+    int64_t N, P, M;
+    const double *A;
+    int64_t lda;
+    const double *B;
+    int64_t ldb;
+    double *C;
+    int64_t ldc;
+} mm_problem;
+size_t mm_emulated_group_workspace_bytes(const mm_problem *probs, int32_t count, int32_t kind, int32_t nslices,
+                                         double tier);
+int mm_emulated_group(const mm_problem *probs, int32_t count, int32_t kind, int32_t nslices, double tier, void *ws,
+                      size_t ws_bytes, void *stream);
+
+/*
+ * Serving loop (spec serving; no counterpart in the paper).  A server
+ * owns a worker thread and K streams and serves requests C = A B with host
+ * operands and a requested accuracy tier:
+ *   - `arena` (device, caller-owned, arena_bytes) is the server's entire HBM
+ *     budget: per-stream batch tables, every admitted request's device copies
+ *     of A, B, C and every running batch's split workspace are carved from it;
+ *     the server allocates no device memory itself;
+ *   - requests are admitted in arrival order (later ones may pass one that does
+ *     not fit yet) once their A, B and C fit; a request that can never fit
+ *     completes with MM_ERR_NOMEM;
+ *   - continuous batching: whenever a stream is free, all admitted requests of
+ *     the oldest request's slice count (up to max_batch) run as one grouped
+ *     emulated launch (method 0), replayed from a CUDA graph cached per stream,
+ *     slice count and size bucket when use_graphs != 0; method 1 instead runs
+ *     one request at a time with mm_naive's FP64 kernel (a baseline);
+ *   - per request: host-to-device copies of A and B, the product, and the copy
+ *     of C back into the caller's host buffer, whose completion ends the
+ *     request's latency (measured from mm_server_submit).
+ * Host buffers must stay valid until the request completes; pinned host
+ * memory lets copies overlap.  Each result is bit-identical to mm_emulated on
+ * the same operands with the tier's slice count (or to mm_naive for method 1).
+ */
+typedef struct mm_server mm_server;
+typedef struct {
+    int64_t N, P, M;
+    const double *A; /* host, row-major, lda >= P */
+    int64_t lda;
+    const double *B; /* host, row-major, ldb >= M */
+    int64_t ldb;
+    double *C; /* host output, ldc >= M */
+    int64_t ldc;
+    double tier; /* requested ||C - AB||_inf / (||A||_inf ||B||_inf) (method 0) */
+    int64_t tag; /* caller's identifier, echoed in the completion */
+} mm_request;
+typedef struct {
+    int64_t tag;
+    int32_t status; /* MM_OK, MM_ERR_NOMEM (never fits), MM_ERR_TIMEOUT (cancelled), MM_ERR_CUDA */
+    int32_t slices; /* slice count used (0 for method 1) */
+    double queue_ms;   /* submit -> launch */
+    double latency_ms; /* submit -> C in the host buffer */
+} mm_completion;
+typedef struct {
+    int64_t submitted, completed, rejected, batches, graph_replays;
+    double p50_ms, p99_ms, mean_ms, max_ms;
+    double busy_s; /* first submit -> last completion */
+    double flops;  /* sum of 2NPM over completed requests */
+    int64_t peak_arena_bytes;
+} mm_server_stats_t;
+int mm_server_create(void *arena, size_t arena_bytes, int32_t max_batch, int32_t nstreams, int32_t use_graphs,
+                     int32_t method, mm_server **out);
+int mm_server_submit(mm_server *server, const mm_request *request); /* returns at once */
+int mm_server_poll(mm_server *server, mm_completion *out, int32_t cap); /* number of completions written */
+int mm_server_wait(mm_server *server, int64_t timeout_ms); /* MM_ERR_TIMEOUT if requests remain */
+int mm_server_stats(mm_server *server, mm_server_stats_t *out);
+/* Cancels requests that have not started (status MM_ERR_TIMEOUT), waits for
+ * running batches, frees the server.  The arena may be reused afterwards. */
+int mm_server_destroy(mm_server *server);
+
+/*
  * Kernel-level timing (measurement support).  While enabled, every kernel the
  * library launches on any stream is bracketed by CUDA events recorded on that
  * stream.  mm_profile_read synchronises those events and fills up to `cap`

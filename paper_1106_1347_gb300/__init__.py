@@ -14,7 +14,7 @@ import ctypes
 from ._native import KernelStat, MMError, check, lib
 
 __all__ = ["naive", "kahan", "winograd", "winograd_scaled", "strassen", "strassen_winograd", "norm_inf",
-           "emulated", "emulated_noalloc", "emulated_slices", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
+           "emulated", "emulated_group", "emulated_noalloc", "emulated_slices", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
            "SLICE_FP8E4M3"]
 
 SLICE_BF16 = 0
@@ -152,6 +152,30 @@ def emulated(a, b, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
     check("mm_emulated", lib().mm_emulated(*_gemm_args(a, b, c, n, p, m), kind, nslices, float(tier), _ptr(ws), need,
                                            _stream(a.device)))
     return c
+
+
+def emulated_group(pairs, nslices=0, tier=1e-14, kind=SLICE_BF16, outs=None):
+    """Grouped FP64-accurate products: [(A_g, B_g)] -> [C_g] in one launch per kernel."""
+    from ._native import Problem
+
+    torch = _torch()
+    prepared, results = [], []
+    for g, (a, b) in enumerate(pairs):
+        a, b, c, n, p, m = _prep(a, b, None if outs is None else outs[g])
+        prepared.append((a, b))
+        results.append(c)
+    if not prepared:
+        return []
+    arr = (Problem * len(prepared))()
+    for g, ((a, b), c) in enumerate(zip(prepared, results)):
+        arr[g] = Problem(a.shape[0], a.shape[1], b.shape[1], a.data_ptr(), _ld(a), b.data_ptr(), _ld(b),
+                         c.data_ptr(), _ld(c))
+    dev = prepared[0][0].device
+    need = lib().mm_emulated_group_workspace_bytes(arr, len(prepared), kind, nslices, tier)
+    ws = _ws(need, dev)
+    check("mm_emulated_group", lib().mm_emulated_group(arr, len(prepared), kind, nslices, float(tier), _ptr(ws), need,
+                                                       _stream(dev)))
+    return results
 
 
 def emulated_noalloc(a, b, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):

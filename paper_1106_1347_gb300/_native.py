@@ -17,6 +17,26 @@ i64, i32, dbl, vp, sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.
 GEMM = [i64, i64, i64, vp, i64, vp, i64, vp, i64]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("N", i64), ("P", i64), ("M", i64), ("A", vp), ("lda", i64), ("B", vp), ("ldb", i64), ("C", vp),
+                ("ldc", i64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("N", i64), ("P", i64), ("M", i64), ("A", vp), ("lda", i64), ("B", vp), ("ldb", i64), ("C", vp),
+                ("ldc", i64), ("tier", dbl), ("tag", i64)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", i64), ("status", i32), ("slices", i32), ("queue_ms", dbl), ("latency_ms", dbl)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", i64), ("completed", i64), ("rejected", i64), ("batches", i64), ("graph_replays", i64),
+                ("p50_ms", dbl), ("p99_ms", dbl), ("mean_ms", dbl), ("max_ms", dbl), ("busy_s", dbl),
+                ("flops", dbl), ("peak_arena_bytes", i64)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -42,6 +62,14 @@ SIGNATURES = {
     "mm_emulated_slices": (ctypes.c_int, [i32, i32, dbl]),
     "mm_emulated_noalloc": (ctypes.c_int, GEMM + [i32, i32, dbl, vp]),
     "mm_emulated_noalloc_capacity": (sz, []),
+    "mm_emulated_group_workspace_bytes": (sz, [ctypes.POINTER(Problem), i32, i32, i32, dbl]),
+    "mm_emulated_group": (ctypes.c_int, [ctypes.POINTER(Problem), i32, i32, i32, dbl, vp, sz, vp]),
+    "mm_server_create": (ctypes.c_int, [vp, sz, i32, i32, i32, i32, ctypes.POINTER(vp)]),
+    "mm_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(Request)]),
+    "mm_server_poll": (ctypes.c_int, [vp, ctypes.POINTER(Completion), i32]),
+    "mm_server_wait": (ctypes.c_int, [vp, i64]),
+    "mm_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
+    "mm_server_destroy": (ctypes.c_int, [vp]),
     "mm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mm_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelStat), i32]),
 }

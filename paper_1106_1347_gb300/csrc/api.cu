@@ -97,7 +97,14 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+namespace {
+thread_local bool t_prof_suspended = false;
+}
+
+void prof_suspend(bool on) { t_prof_suspended = on; }
+
 void prof_begin(const char *name, cudaStream_t stream) {
+    if (t_prof_suspended) return;
     std::lock_guard<std::mutex> g(g_prof_mu);
     if (!g_prof_on) return;
     ProfRec r{name, take_event(), take_event()};
@@ -107,6 +114,7 @@ void prof_begin(const char *name, cudaStream_t stream) {
 }
 
 void prof_end(cudaStream_t stream) {
+    if (t_prof_suspended) return;
     std::lock_guard<std::mutex> g(g_prof_mu);
     if (!g_prof_on || t_open < 0) return;
     cudaEventRecord(g_prof_recs[t_open].stop, stream);
@@ -306,6 +314,47 @@ int mm_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_
 }
 
 size_t mm_emulated_noalloc_capacity(void) { return emulated_noalloc_capacity(); }
+
+static int check_group(const char *fn, const mm_problem *probs, int32_t count, int32_t kind, int32_t nslices,
+                       double tier) {
+    if (count < 0 || (count > 0 && !probs)) return fail(MM_ERR_ARG, "%s: bad problem list", fn);
+    if (kind == MM_SLICE_FP8E4M3) return fail(MM_ERR_UNSUPPORTED, "%s: FP8-E4M3 slices are not built", fn);
+    if (kind != MM_SLICE_BF16) return fail(MM_ERR_ARG, "%s: unknown slice kind %d", fn, kind);
+    if (nslices < 0 || nslices > 8) return fail(MM_ERR_ARG, "%s: nslices must be 0..8", fn);
+    if (nslices == 0 && !(tier > 0.0)) return fail(MM_ERR_ARG, "%s: tier must be > 0 when nslices == 0", fn);
+    for (int32_t i = 0; i < count; ++i) {
+        const mm_problem &q = probs[i];
+        int rc = check_gemm_args(fn, q.N, q.P, q.M, q.A, q.lda, q.B, q.ldb, q.C, q.ldc);
+        if (rc) return fail(rc, "%s: problem %d: %s", fn, (int)i, mm_last_error());
+        if (q.P > (int64_t(1) << 20)) return fail(MM_ERR_UNSUPPORTED, "%s: problem %d has P > 2^20", fn, (int)i);
+    }
+    for (int32_t i = 0; i < count; ++i) {  // outputs must not overlap one another
+        const size_t bi = span_bytes(probs[i].N, probs[i].M, probs[i].ldc);
+        for (int32_t j = i + 1; j < count && bi; ++j)
+            if (ranges_overlap(probs[i].C, bi, probs[j].C, span_bytes(probs[j].N, probs[j].M, probs[j].ldc)))
+                return fail(MM_ERR_ARG, "%s: outputs of problems %d and %d overlap", fn, (int)i, (int)j);
+    }
+    return MM_OK;
+}
+
+size_t mm_emulated_group_workspace_bytes(const mm_problem *probs, int32_t count, int32_t kind, int32_t nslices,
+                                         double tier) {
+    const int s = emulated_slices(kind, nslices, tier);
+    if (s <= 0 || count <= 0 || !probs) return 0;
+    return emulated_group_ws_bytes(probs, count, s);
+}
+
+int mm_emulated_group(const mm_problem *probs, int32_t count, int32_t kind, int32_t nslices, double tier, void *ws,
+                      size_t ws_bytes, void *stream) {
+    int rc = check_group("mm_emulated_group", probs, count, kind, nslices, tier);
+    if (rc) return rc;
+    if (count == 0) return MM_OK;
+    const int s = emulated_slices(kind, nslices, tier);
+    const size_t need = emulated_group_ws_bytes(probs, count, s);
+    if (ws_bytes < need || !ws)
+        return fail(MM_ERR_WORKSPACE, "mm_emulated_group: workspace %zu bytes < %zu required", ws_bytes, need);
+    return run_emulated_group(probs, count, s, ws, (cudaStream_t)stream);
+}
 
 int mm_profile_enable(int on) {
     std::lock_guard<std::mutex> g(g_prof_mu);

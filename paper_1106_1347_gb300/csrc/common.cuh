@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "mm.h"
 
@@ -81,6 +82,25 @@ int emulated_slices(int32_t kind, int32_t nslices, double tier);
 size_t emulated_ws_bytes(int64_t N, int64_t P, int64_t M, int s);
 int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
                  double *C, int64_t ldc, int s, void *ws, cudaStream_t st);
+size_t emulated_group_ws_bytes(const mm_problem *probs, int count, int s);
+
+// Pieces of a grouped emulated launch, for runtimes that place the table part
+// (problem table, header, prefix arrays) and the data part (column maxima,
+// exponents, slices) themselves and replay the kernels from CUDA graphs.
+struct GroupLaunch {
+    const void *tab, *hdr;    // device table and header (table part)
+    const int64_t *begin[5];  // device prefix arrays
+    int64_t grid[5];          // CTAs per kernel; may be raised to upper bounds
+    int s;
+};
+size_t group_table_bytes(int count);
+size_t problem_data_bytes(const mm_problem &q, int s);
+size_t group_data_bytes(const mm_problem *probs, int count, int s);
+int group_build(const mm_problem *probs, int count, int s, void *table_dev, char *const *data,
+                std::vector<unsigned char> &image, GroupLaunch &gl);
+int group_kernels(const GroupLaunch &gl, cudaStream_t st);
+void prof_suspend(bool on);  // skip kernel timing while a stream is being captured
+int run_emulated_group(const mm_problem *probs, int count, int s, void *ws, cudaStream_t st);
 size_t emulated_noalloc_capacity();
 int run_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
                          int64_t ldb, double *C, int64_t ldc, int s, cudaStream_t st);

@@ -33,6 +33,7 @@
 #include <cuda_bf16.h>
 
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -102,21 +103,28 @@ __device__ __forceinline__ void balanced_digits(int64_t V, int s, int (&dig)[8])
     dig[0] = (int)V;
 }
 
-__global__ void __launch_bounds__(256) split_rows_kernel(int64_t N, int64_t P, const double *__restrict__ A,
-                                                         int64_t lda, int s, int64_t Nr, int64_t Pp,
-                                                         int32_t *__restrict__ ea,
-                                                         __nv_bfloat16 *__restrict__ slices) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * 8 + warp;
-    if (row >= N) return;
-    const double *a = A + row * lda;
+// Everything one split of A needs (one problem).
+struct SplitA {
+    int64_t N, P, lda, Nr, Pp;
+    const double *A;
+    int s;
+    int32_t *ea;
+    __nv_bfloat16 *slices;
+};
+
+// One warp per row of A: max |A_ik| by integer max on the bit patterns, then
+// the digits, written as BF16 slices [s][Nr][Pp].
+__device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int lane) {
+    const double *a = p.A + row * p.lda;
+    const int64_t P = p.P, Pp = p.Pp;
+    const int s = p.s;
     unsigned long long mx = 0;
     for (int64_t c = lane; c < P; c += 32) mx = umax64(mx, absbits(a[c]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         mx = umax64(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mx, o));
     const int e = frexp_exp_bits(mx);
-    if (lane == 0) ea[row] = e;
+    if (lane == 0) p.ea[row] = e;
     const int sh = kBeta * s - 1 - e;
     // Columns [P, Pp) are written as zero digits so every K-block read stays defined.
     for (int64_t c0 = 0; c0 < Pp; c0 += 64) {
@@ -127,7 +135,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(int64_t N, int64_t P, c
         const bool two = c + 1 < Pp;
         balanced_digits((two && c + 1 < P) ? round_scaled(a[c + 1], sh) : 0, s, d1);
         for (int t = 0; t < s; ++t) {
-            __nv_bfloat16 *dst = slices + ((int64_t)t * Nr + row) * Pp + c;
+            __nv_bfloat16 *dst = p.slices + ((int64_t)t * p.Nr + row) * Pp + c;
             if (two) {
                 *reinterpret_cast<__nv_bfloat162 *>(dst) = __floats2bfloat162_rn((float)d0[t], (float)d1[t]);
             } else {
@@ -137,37 +145,55 @@ __global__ void __launch_bounds__(256) split_rows_kernel(int64_t N, int64_t P, c
     }
 }
 
-__global__ void __launch_bounds__(128) col_max_kernel(int64_t P, int64_t M, const double *__restrict__ B,
-                                                      int64_t ldb, unsigned long long *__restrict__ colmax) {
-    const int64_t j = (int64_t)blockIdx.x * 128 + threadIdx.x;
-    if (j >= M) return;
-    const int64_t k0 = (int64_t)blockIdx.y * 256, k1 = min(P, k0 + 256);
+__global__ void __launch_bounds__(256) split_rows_kernel(const SplitA p) {
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row < p.N) split_row(p, row, threadIdx.x & 31);
+}
+
+// Everything the column split of B needs (one problem).
+struct SplitB {
+    int64_t P, M, ldb, Mr, Pp;
+    const double *B;
+    int s;
+    unsigned long long *colmax;  // zeroed before col_max runs
+    int32_t *fb;
+    __nv_bfloat16 *slices;
+};
+
+// Column maxima of rows [k0, k0 + 256) folded into colmax with atomicMax on the bits.
+__device__ __forceinline__ void col_max_part(const SplitB &p, int64_t j, int64_t k0) {
+    if (j >= p.M) return;
+    const int64_t k1 = min(p.P, k0 + 256);
     unsigned long long mx = 0;
-    for (int64_t k = k0; k < k1; ++k) mx = umax64(mx, absbits(B[k * ldb + j]));
-    if (mx) atomicMax(colmax + j, mx);
+    for (int64_t k = k0; k < k1; ++k) mx = umax64(mx, absbits(p.B[k * p.ldb + j]));
+    if (mx) atomicMax(p.colmax + j, mx);
+}
+
+__global__ void __launch_bounds__(128) col_max_kernel(const SplitB p) {
+    col_max_part(p, (int64_t)blockIdx.x * 128 + threadIdx.x, (int64_t)blockIdx.y * 256);
 }
 
 constexpr int SC_K = 32, SC_J = 64;
 
-__global__ void __launch_bounds__(256) split_cols_kernel(int64_t P, int64_t M, const double *__restrict__ B,
-                                                         int64_t ldb, int s, const unsigned long long *colmax,
-                                                         int64_t Mr, int64_t Pp, int32_t *__restrict__ fb,
-                                                         __nv_bfloat16 *__restrict__ slices) {
-    extern __shared__ __align__(16) __nv_bfloat16 sm[];  // [s][SC_J][SC_K + 2]
+// A 32 (k) x 64 (j) tile of B: digits, transposed through shared memory into
+// the K-major slices [s][Mr][Pp] (each slice row is one column of B).
+__device__ __forceinline__ void split_cols_tile(const SplitB &p, int64_t jt, int64_t kt, __nv_bfloat16 *sm) {
     constexpr int LD = SC_K + 2;
     const int tid = threadIdx.x;
-    const int64_t j0 = (int64_t)blockIdx.x * SC_J, k0 = (int64_t)blockIdx.y * SC_K;
+    const int64_t j0 = jt * SC_J, k0 = kt * SC_K;
+    const int64_t P = p.P, M = p.M, Pp = p.Pp;
+    const int s = p.s;
     const int jj = tid & 63;
     const int64_t j = j0 + jj;
-    const int f = (j < M) ? frexp_exp_bits(colmax[j]) : 0;
-    if (blockIdx.y == 0 && tid < 64 && j < M) fb[j] = f;
+    const int f = (j < M) ? frexp_exp_bits(p.colmax[j]) : 0;
+    if (kt == 0 && tid < 64 && j < M) p.fb[j] = f;
     const int sh = kBeta * s - 1 - f;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int kk = (tid >> 6) + 4 * r;
         const int64_t k = k0 + kk;
         int dig[8];
-        balanced_digits((k < P && j < M) ? round_scaled(B[k * ldb + j], sh) : 0, s, dig);
+        balanced_digits((k < P && j < M) ? round_scaled(p.B[k * p.ldb + j], sh) : 0, s, dig);
         for (int t = 0; t < s; ++t) sm[(t * SC_J + jj) * LD + kk] = __float2bfloat16_rn((float)dig[t]);
     }
     __syncthreads();
@@ -180,7 +206,7 @@ __global__ void __launch_bounds__(256) split_cols_kernel(int64_t P, int64_t M, c
             const int64_t gj = j0 + jr, gk = k0 + kp;
             if (gj >= M || gk >= Pp) continue;  // [P, Pp) receives zero digits
             const __nv_bfloat16 *src = sm + (t * SC_J + jr) * LD + kp;
-            __nv_bfloat16 *dst = slices + ((int64_t)t * Mr + gj) * Pp + gk;
+            __nv_bfloat16 *dst = p.slices + ((int64_t)t * p.Mr + gj) * Pp + gk;
             if (gk + 1 < Pp) {
                 __nv_bfloat162 v;
                 v.x = src[0];
@@ -191,6 +217,11 @@ __global__ void __launch_bounds__(256) split_cols_kernel(int64_t P, int64_t M, c
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(256) split_cols_kernel(const SplitB p) {
+    extern __shared__ __align__(16) __nv_bfloat16 sm[];  // [s][SC_J][SC_K + 2]
+    split_cols_tile(p, blockIdx.x, blockIdx.y, sm);
 }
 
 struct EmuParams {
@@ -228,9 +259,11 @@ __device__ __forceinline__ double int128_to_double(int64_t hi, uint64_t lo) {
     return neg ? -r : r;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                      const EmuParams p) {
+// One 128 x 64 output tile (tm, tn) of one problem; called by every thread of
+// the CTA.  tmA / tmB are the problem's slice tensor maps (kernel parameters
+// or entries of a grouped launch's table in global memory).
+__device__ __forceinline__ void slice_tile(const CUtensorMap *tmA, const CUtensorMap *tmB, const EmuParams &p,
+                                           int tm, int tn) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bars[2 * 8 + 3];
     __shared__ uint32_t tmem_slot;
@@ -241,11 +274,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *full = bars, *empty = bars + 8, *acc_full = bars + 16, *acc_empty = bars + 17, *mma_done = bars + 18;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // Grouped rasterisation: runs of 8 tile-rows share B slices in L2.
-    const int id = blockIdx.x, per_group = 8 * p.tiles_n;
-    const int group = id / per_group, first_m = group * 8;
-    const int gsize = min(p.tiles_m - first_m, 8);
-    const int tm = first_m + (id % per_group) % gsize, tn = (id % per_group) / gsize;
     const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BN;
     const int nkb = (int)((p.P + BKE - 1) / BKE);
     const int nchunks = (nkb + p.chunk_blocks - 1) / p.chunk_blocks;
@@ -271,8 +299,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            mmdev::prefetch_tmap(&tmA);
-            mmdev::prefetch_tmap(&tmB);
+            mmdev::prefetch_tmap(tmA);
+            mmdev::prefetch_tmap(tmB);
             int issued = 0;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int st = kb % S, use = kb / S;
@@ -282,8 +310,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 uint8_t *sa = smem + (size_t)st * stage_bytes;
                 mmdev::mbar_arrive_expect_tx(&full[st], stage_bytes);
-                mmdev::tma_load_3d(sa, &tmA, &full[st], kb * BKE, (int32_t)m0, 0);
-                mmdev::tma_load_3d(sa + a_bytes, &tmB, &full[st], kb * BKE, (int32_t)n0, 0);
+                mmdev::tma_load_3d(sa, tmA, &full[st], kb * BKE, (int32_t)m0, 0);
+                mmdev::tma_load_3d(sa + a_bytes, tmB, &full[st], kb * BKE, (int32_t)n0, 0);
                 issued = kb + 1;
             }
             // Wait (bounded) for the last load into each stage, so no copy is in flight at exit.
@@ -406,6 +434,114 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// Tile of CTA `id` in a tiles_m x tiles_n grid, in runs of 8 tile-rows so that
+// consecutive CTAs share B slices in L2.
+__device__ __forceinline__ void tile_of(int64_t id, int tiles_m, int tiles_n, int &tm, int &tn) {
+    const int64_t per_group = 8 * (int64_t)tiles_n;
+    const int64_t group = id / per_group, first_m = group * 8;
+    const int gsize = (int)min((int64_t)tiles_m - first_m, (int64_t)8);
+    tm = (int)(first_m + (id % per_group) % gsize);
+    tn = (int)((id % per_group) / gsize);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const EmuParams p) {
+    int tm, tn;
+    tile_of(blockIdx.x, p.tiles_m, p.tiles_n, tm, tn);
+    slice_tile(&tmA, &tmB, p, tm, tn);
+}
+
+// ------------------------------------------------------------ grouped launch
+//
+// Many products with one slice count in one launch per kernel.  The host
+// writes a table of EmuProblem entries, four prefix arrays (per kernel, the
+// first CTA of each problem) and a header with the totals into the workspace;
+// each CTA finds its problem by binary search over the prefix array.  Grids
+// may exceed the totals (the serving loop captures a launch once per size
+// bucket in a CUDA graph); surplus CTAs return before touching anything.
+struct __align__(64) EmuProblem {
+    CUtensorMap tmA, tmB;
+    EmuParams prm;
+    SplitA spa;
+    SplitB spb;
+};
+
+struct GroupHeader {
+    int64_t count;
+    int64_t units[5];  // split_rows, col_max, split_cols, slice_gemm, zero_colmax CTAs
+};
+
+enum { U_ROWS = 0, U_COLMAX = 1, U_SPLITCOLS = 2, U_TILES = 3, U_ZERO = 4 };
+
+// Largest g in [0, count) with begin[g] <= unit.
+__device__ __forceinline__ int find_problem(const int64_t *begin, int64_t count, int64_t unit) {
+    int64_t lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= unit)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return (int)lo;
+}
+
+__global__ void __launch_bounds__(256) group_zero_colmax_kernel(const EmuProblem *tab, const int64_t *begin,
+                                                                const GroupHeader *hdr) {
+    const int64_t u = blockIdx.x;
+    if (u >= hdr->units[U_ZERO]) return;
+    const int g = find_problem(begin, hdr->count, u);
+    const SplitB &p = tab[g].spb;
+    const int64_t j = (u - begin[g]) * 256 + threadIdx.x;
+    if (j < p.M) p.colmax[j] = 0ull;
+}
+
+__global__ void __launch_bounds__(256) group_split_rows_kernel(const EmuProblem *tab, const int64_t *begin,
+                                                               const GroupHeader *hdr) {
+    const int64_t u = blockIdx.x;
+    if (u >= hdr->units[U_ROWS]) return;
+    const int g = find_problem(begin, hdr->count, u);
+    const SplitA &p = tab[g].spa;
+    const int64_t row = (u - begin[g]) * 8 + (threadIdx.x >> 5);
+    if (row < p.N) split_row(p, row, threadIdx.x & 31);
+}
+
+__global__ void __launch_bounds__(128) group_col_max_kernel(const EmuProblem *tab, const int64_t *begin,
+                                                            const GroupHeader *hdr) {
+    const int64_t u = blockIdx.x;
+    if (u >= hdr->units[U_COLMAX]) return;
+    const int g = find_problem(begin, hdr->count, u);
+    const SplitB &p = tab[g].spb;
+    const int64_t local = u - begin[g], nj = (p.M + 127) / 128;
+    col_max_part(p, (local % nj) * 128 + threadIdx.x, (local / nj) * 256);
+}
+
+__global__ void __launch_bounds__(256) group_split_cols_kernel(const EmuProblem *tab, const int64_t *begin,
+                                                               const GroupHeader *hdr) {
+    extern __shared__ __align__(16) __nv_bfloat16 sm[];
+    const int64_t u = blockIdx.x;
+    if (u >= hdr->units[U_SPLITCOLS]) return;
+    const int g = find_problem(begin, hdr->count, u);
+    const SplitB &p = tab[g].spb;
+    const int64_t local = u - begin[g], nj = (p.M + SC_J - 1) / SC_J;
+    split_cols_tile(p, local % nj, local / nj, sm);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) group_slice_gemm_kernel(const EmuProblem *tab, const int64_t *begin,
+                                                                       const GroupHeader *hdr) {
+    const int64_t u = blockIdx.x;
+    if (u >= hdr->units[U_TILES]) return;
+    const int g = find_problem(begin, hdr->count, u);
+    const EmuProblem &e = tab[g];
+    const EmuParams prm = e.prm;
+    int tm, tn;
+    tile_of(u - begin[g], prm.tiles_m, prm.tiles_n, tm, tn);
+    slice_tile(&e.tmA, &e.tmB, prm, tm, tn);
+}
+
+cudaError_t slice_smem_attributes();
+
 struct Layout {
     int s;
     int64_t Nr, Mr, Pp;
@@ -478,19 +614,20 @@ int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
     int rc;
     cudaError_t e = cudaMemsetAsync(colmax, 0, (size_t)M * 8, st);
     if (e != cudaSuccess) return cuda_fail(e, "mm_emulated");
-    rc = launch("emu_split_rows", st, [&] {
-        split_rows_kernel<<<(unsigned)ceil_div(N, 8), 256, 0, st>>>(N, P, A, lda, s, L.Nr, L.Pp, ea, sa);
-    });
+    const SplitA spa{N, P, lda, L.Nr, L.Pp, A, s, ea, sa};
+    const SplitB spb{P, M, ldb, L.Mr, L.Pp, B, s, colmax, fb, sb};
+    rc = launch("emu_split_rows", st,
+                [&] { split_rows_kernel<<<(unsigned)ceil_div(N, 8), 256, 0, st>>>(spa); });
     if (rc) return rc;
     rc = launch("emu_col_max", st, [&] {
         dim3 g((unsigned)ceil_div(M, 128), (unsigned)ceil_div(P, 256));
-        col_max_kernel<<<g, 128, 0, st>>>(P, M, B, ldb, colmax);
+        col_max_kernel<<<g, 128, 0, st>>>(spb);
     });
     if (rc) return rc;
     rc = launch("emu_split_cols", st, [&] {
         dim3 g((unsigned)ceil_div(M, SC_J), (unsigned)ceil_div(L.Pp, SC_K));
         const size_t sm = (size_t)s * SC_J * (SC_K + 2) * sizeof(__nv_bfloat16);
-        split_cols_kernel<<<g, 256, sm, st>>>(P, M, B, ldb, s, colmax, L.Mr, L.Pp, fb, sb);
+        split_cols_kernel<<<g, 256, sm, st>>>(spb);
     });
     if (rc) return rc;
 
@@ -518,16 +655,231 @@ int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
     prm.ldc = ldc;
     prm.status = device_status_ptr();
     const size_t smem = (size_t)prm.stages * stage_bytes + 1024;
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        kSmemLimit - 1024);
-    });
+    const cudaError_t attr_err = slice_smem_attributes();
     if (attr_err != cudaSuccess) return cuda_fail(attr_err, "mm_emulated: shared memory attribute");
     const int64_t tiles = (int64_t)prm.tiles_m * prm.tiles_n;
     return launch("emu_slice_gemm_tcgen05", st,
                   [&] { slice_gemm_kernel<<<(unsigned)tiles, kThreads, smem, st>>>(tmA, tmB, prm); });
+}
+
+}  // namespace mm
+
+// ------------------------------------------------------- grouped host side
+
+namespace {
+
+size_t slices_bytes(int64_t rows_padded, int64_t Pp, int s) {
+    return mm::align_up((size_t)s * rows_padded * Pp * 2, 1024);
+}
+
+// Per-launch constants shared by every problem of a slice count s.
+void fill_common(EmuParams &prm, int s) {
+    const uint32_t stage_bytes = (uint32_t)s * (BM + BN) * BKE * 2;
+    prm.s = s;
+    prm.stages = std::min(4, (int)((kSmemLimit - 2048) / stage_bytes));
+    prm.chunk_blocks = std::max(1, (int)((1 << 24) / ((int64_t)s * 4096) / BKE));
+    prm.hsplit = (s + 1) / 2;
+    int cols = 32;
+    while (cols < s * BN) cols <<= 1;
+    prm.tmem_cols = cols;
+}
+
+size_t slice_smem_bytes(int s) {
+    const uint32_t stage_bytes = (uint32_t)s * (BM + BN) * BKE * 2;
+    const int stages = std::min(4, (int)((kSmemLimit - 2048) / stage_bytes));
+    return (size_t)stages * stage_bytes + 1024;
+}
+
+cudaError_t slice_smem_attributes() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = cudaFuncSetAttribute(slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit - 1024);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(group_slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSmemLimit - 1024);
+    });
+    return err;
+}
+
+}  // namespace
+
+namespace mm {
+
+// A grouped launch's memory: a table part (problem table, header, prefix
+// arrays), and per problem a data region [column maxima | e | f | A slices |
+// B slices].  mm_emulated_group places the data regions right after the
+// table; the serving loop keeps each request's region with its operands.
+struct GroupLayout {
+    size_t off_table, off_hdr, off_begin[5], table_bytes;
+};
+
+static GroupLayout group_layout(int count) {
+    GroupLayout g{};
+    size_t o = 0;
+    g.off_table = o;
+    o += align_up((size_t)count * sizeof(EmuProblem), 256);
+    g.off_hdr = o;
+    o += align_up(sizeof(GroupHeader), 256);
+    for (int k = 0; k < 5; ++k) {
+        g.off_begin[k] = o;
+        o += align_up((size_t)(count + 1) * 8, 256);
+    }
+    g.table_bytes = align_up(o, 1024);
+    return g;
+}
+
+size_t group_table_bytes(int count) { return group_layout(count).table_bytes; }
+
+size_t problem_data_bytes(const mm_problem &q, int s) {
+    const Layout L = layout(q.N, q.P, q.M, s);
+    return align_up((size_t)L.Mr * 8, 1024) + align_up((size_t)L.Nr * 4, 1024) + align_up((size_t)L.Mr * 4, 1024) +
+           slices_bytes(L.Nr, L.Pp, s) + slices_bytes(L.Mr, L.Pp, s);
+}
+
+size_t group_data_bytes(const mm_problem *probs, int count, int s) {
+    size_t d = 0;
+    for (int i = 0; i < count; ++i) d += problem_data_bytes(probs[i], s);
+    return d;
+}
+
+size_t emulated_group_ws_bytes(const mm_problem *probs, int count, int s) {
+    if (count <= 0) return 0;
+    return group_table_bytes(count) + group_data_bytes(probs, count, s);
+}
+
+// The five kernels of a grouped launch (no memset or copy: capturable).
+int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
+    cudaError_t e = slice_smem_attributes();
+    if (e != cudaSuccess) return cuda_fail(e, "grouped emulated product: shared memory attribute");
+    int rc = MM_OK;
+    if (gl.grid[U_ZERO] > 0)
+        rc = launch("emu_group_zero_colmax", st, [&] {
+            group_zero_colmax_kernel<<<(unsigned)gl.grid[U_ZERO], 256, 0, st>>>(
+                (const EmuProblem *)gl.tab, gl.begin[U_ZERO], (const GroupHeader *)gl.hdr);
+        });
+    if (rc) return rc;
+    if (gl.grid[U_ROWS] > 0)
+        rc = launch("emu_group_split_rows", st, [&] {
+            group_split_rows_kernel<<<(unsigned)gl.grid[U_ROWS], 256, 0, st>>>((const EmuProblem *)gl.tab,
+                                                                                 gl.begin[U_ROWS],
+                                                                                 (const GroupHeader *)gl.hdr);
+        });
+    if (rc) return rc;
+    if (gl.grid[U_COLMAX] > 0)
+        rc = launch("emu_group_col_max", st, [&] {
+            group_col_max_kernel<<<(unsigned)gl.grid[U_COLMAX], 128, 0, st>>>((const EmuProblem *)gl.tab,
+                                                                                gl.begin[U_COLMAX],
+                                                                                (const GroupHeader *)gl.hdr);
+        });
+    if (rc) return rc;
+    if (gl.grid[U_SPLITCOLS] > 0)
+        rc = launch("emu_group_split_cols", st, [&] {
+            const size_t sm = (size_t)gl.s * SC_J * (SC_K + 2) * sizeof(__nv_bfloat16);
+            group_split_cols_kernel<<<(unsigned)gl.grid[U_SPLITCOLS], 256, sm, st>>>(
+                (const EmuProblem *)gl.tab, gl.begin[U_SPLITCOLS], (const GroupHeader *)gl.hdr);
+        });
+    if (rc) return rc;
+    if (gl.grid[U_TILES] > 0)
+        rc = launch("emu_group_slice_gemm_tcgen05", st, [&] {
+            group_slice_gemm_kernel<<<(unsigned)gl.grid[U_TILES], kThreads, slice_smem_bytes(gl.s), st>>>(
+                (const EmuProblem *)gl.tab, gl.begin[U_TILES], (const GroupHeader *)gl.hdr);
+        });
+    return rc;
+}
+
+// Builds the host image of the table part for the problems (all N, P, M >= 1)
+// -- to be copied to `table_dev` -- and the launch description.  data[i] is
+// problem i's data region of problem_data_bytes(probs[i], s) bytes.
+int group_build(const mm_problem *probs, int count, int s, void *table_dev, char *const *data,
+                std::vector<unsigned char> &image, GroupLaunch &gl) {
+    const GroupLayout G = group_layout(count);
+    char *t = (char *)table_dev;
+    image.assign(G.table_bytes, 0);
+    EmuProblem *tab = (EmuProblem *)(image.data() + G.off_table);
+    GroupHeader *hdr = (GroupHeader *)(image.data() + G.off_hdr);
+    int64_t *begin[5];
+    for (int k = 0; k < 5; ++k) begin[k] = (int64_t *)(image.data() + G.off_begin[k]);
+    int64_t units[5] = {0, 0, 0, 0, 0};
+    int *status = device_status_ptr();
+    for (int i = 0; i < count; ++i) {
+        const mm_problem &q = probs[i];
+        const Layout L = layout(q.N, q.P, q.M, s);
+        EmuProblem &e = tab[i];
+        char *w = data[i];
+        unsigned long long *cm = (unsigned long long *)w;
+        w += align_up((size_t)L.Mr * 8, 1024);
+        int32_t *ea = (int32_t *)w;
+        w += align_up((size_t)L.Nr * 4, 1024);
+        int32_t *fb = (int32_t *)w;
+        w += align_up((size_t)L.Mr * 4, 1024);
+        __nv_bfloat16 *sa = (__nv_bfloat16 *)w;
+        w += slices_bytes(L.Nr, L.Pp, s);
+        __nv_bfloat16 *sb = (__nv_bfloat16 *)w;
+        e.spa = SplitA{q.N, q.P, q.lda, L.Nr, L.Pp, q.A, s, ea, sa};
+        e.spb = SplitB{q.P, q.M, q.ldb, L.Mr, L.Pp, q.B, s, cm, fb, sb};
+        fill_common(e.prm, s);
+        e.prm.N = q.N;
+        e.prm.P = q.P;
+        e.prm.M = q.M;
+        e.prm.tiles_m = (int)ceil_div(q.N, BM);
+        e.prm.tiles_n = (int)ceil_div(q.M, BN);
+        e.prm.ea = ea;
+        e.prm.fb = fb;
+        e.prm.C = q.C;
+        e.prm.ldc = q.ldc;
+        e.prm.status = status;
+        int rc = encode_slices(&e.tmA, sa, L.Nr, L.Pp, s, BM);
+        if (!rc) rc = encode_slices(&e.tmB, sb, L.Mr, L.Pp, s, BN);
+        if (rc) return rc;
+        for (int k = 0; k < 5; ++k) begin[k][i] = units[k];
+        units[U_ROWS] += ceil_div(q.N, 8);
+        units[U_COLMAX] += ceil_div(q.M, 128) * ceil_div(q.P, 256);
+        units[U_SPLITCOLS] += ceil_div(q.M, SC_J) * ceil_div(L.Pp, SC_K);
+        units[U_TILES] += (int64_t)e.prm.tiles_m * e.prm.tiles_n;
+        units[U_ZERO] += ceil_div(q.M, 256);
+    }
+    hdr->count = count;
+    for (int k = 0; k < 5; ++k) {
+        begin[k][count] = units[k];
+        hdr->units[k] = units[k];
+        gl.grid[k] = units[k];
+        gl.begin[k] = (const int64_t *)(t + G.off_begin[k]);
+    }
+    gl.tab = t + G.off_table;
+    gl.hdr = t + G.off_hdr;
+    gl.s = s;
+    return MM_OK;
+}
+
+int run_emulated_group(const mm_problem *probs, int count, int s, void *ws, cudaStream_t st) {
+    std::vector<mm_problem> live;
+    live.reserve(count);
+    for (int i = 0; i < count; ++i) {
+        const mm_problem &q = probs[i];
+        if (q.N == 0 || q.M == 0) continue;
+        if (q.P == 0) {
+            int rc = run_zero(q.N, q.M, q.C, q.ldc, st);
+            if (rc) return rc;
+            continue;
+        }
+        live.push_back(q);
+    }
+    if (live.empty()) return MM_OK;
+    std::vector<unsigned char> image;
+    GroupLaunch gl{};
+    std::vector<char *> data(live.size());
+    char *d = (char *)ws + group_table_bytes((int)live.size());
+    for (size_t i = 0; i < live.size(); ++i) {
+        data[i] = d;
+        d += problem_data_bytes(live[i], s);
+    }
+    int rc = group_build(live.data(), (int)live.size(), s, ws, data.data(), image, gl);
+    if (rc) return rc;
+    // Pageable source: the copy is staged before cudaMemcpyAsync returns, so `image` may go.
+    cudaError_t e = cudaMemcpyAsync((void *)gl.tab, image.data(), image.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "grouped emulated product: table upload");
+    return group_kernels(gl, st);
 }
 
 }  // namespace mm

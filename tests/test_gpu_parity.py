@@ -211,6 +211,40 @@ def test_emulated_positive_worst_case_sums(mm, orc):
     assert np.array_equal(host(mm.emulated(dev(a), dev(b), nslices=8)), orc.split_product(a, b, 7, 8))
 
 
+# ---------------------------------------------------------- grouped launch
+
+def test_emulated_group_matches_single_calls(mm, orc):
+    import torch
+
+    rng = np.random.default_rng(5)
+    shapes = [(1, 1, 1), (37, 65, 129), (128, 64, 64), (300, 40, 17), (5, 1000, 3), (200, 333, 150), (64, 0, 9),
+              (0, 5, 5), (129, 513, 250)]
+    pairs, hostpairs = [], []
+    for i, (n, p, m) in enumerate(shapes):
+        a = S.loguniform(n, p, S.stream_seed(6, 2 * i)) if n * p else np.zeros((n, p))
+        b = S.loguniform(p, m, S.stream_seed(6, 2 * i + 1)) if p * m else np.zeros((p, m))
+        hostpairs.append((a, b))
+        pairs.append((dev(a), dev(b)))
+    for s in (8, 3):
+        outs = mm.emulated_group(pairs, nslices=s)
+        for (a, b), (ta, tb), c in zip(hostpairs, pairs, outs):
+            single = host(mm.emulated(ta, tb, nslices=s))
+            assert np.array_equal(host(c), single)
+            if a.size and b.size and a.shape[0] <= 200:
+                assert np.array_equal(single, orc.split_product(a, b, 7, s))
+
+
+def test_emulated_group_rejects_overlapping_outputs(mm):
+    import torch
+    from paper_1106_1347_gb300._native import Problem
+
+    a = torch.ones((8, 8), dtype=torch.float64, device="cuda")
+    c = torch.zeros((16, 8), dtype=torch.float64, device="cuda")
+    arr = (Problem * 2)(Problem(8, 8, 8, a.data_ptr(), 8, a.data_ptr(), 8, c.data_ptr(), 8),
+                        Problem(8, 8, 8, a.data_ptr(), 8, a.data_ptr(), 8, c[4:].data_ptr(), 8))
+    assert mm.lib().mm_emulated_group(arr, 2, 0, 3, 1e-6, None, 0, None) == -1
+
+
 # ------------------------------------------------------------ edge cases
 
 @pytest.mark.parametrize("name", ["naive", "kahan", "winograd", "winograd_scaled", "strassen", "strassen_winograd",
