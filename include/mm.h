@@ -115,7 +115,9 @@ int mm_winograd_scaled(int64_t N, int64_t P, int64_t M, const double *A, int64_t
  *                embed in Y x Y with Y = (floor(X/2^k) + 1) 2^k, recurse k levels;
  *   cutoff  > 0: the smallest depth at which every padded dimension / 2^depth
  *                is <= cutoff, each dimension padded to a multiple of 2^depth;
- *   cutoff == -1: depth chosen by the library's tuned table.
+ *   cutoff == -1: the depth mm_tune_strassen recorded for this shape bucket,
+ *                else one level per doubling of max(N, P, M) above 1024 (at
+ *                most 3); each dimension padded to a multiple of 2^depth.
  * Padding is virtual (out-of-range elements read as zero).  The innermost
  * level forms the operand sums (Plus/Minus) while staging tiles and adds
  * +-H_i into the C quadrants in the paper's left-to-right order in its
@@ -130,6 +132,27 @@ size_t mm_strassen_winograd_workspace_bytes(int64_t N, int64_t P, int64_t M, int
 int mm_strassen_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
                          int64_t ldb, double *C, int64_t ldc, int32_t cutoff, void *ws, size_t ws_bytes,
                          void *stream);
+
+/*
+ * Autotuner for the Strassen depth used by cutoff == -1 (north-star
+ * autotuning; the paper fixes the depth by its padding rule).
+ * mm_tune_strassen times the recursion at depths 0..3 (each dimension padded
+ * to a multiple of 2^depth) on the given operands, writing C each time, and
+ * records the fastest depth for (variant, floor(log2 max(N, P, M))); it
+ * synchronises `stream`.  variant: 0 = StrassenNaiv, 1 = StrassenWinograd.
+ * ws must hold mm_tune_strassen_workspace_bytes(N, P, M) bytes (depths whose
+ * workspace does not fit are skipped).  The table persists with
+ * mm_tune_save / mm_tune_load (text, one entry per line); if MM_TUNE_CACHE is
+ * set, that file is loaded at first use.  mm_tune_load returns the number of
+ * entries read.
+ */
+size_t mm_tune_strassen_workspace_bytes(int64_t N, int64_t P, int64_t M);
+int mm_tune_strassen(int32_t variant, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                     int64_t ldb, double *C, int64_t ldc, void *ws, size_t ws_bytes, void *stream,
+                     int32_t *best_depth, double *best_ms);
+int mm_tune_save(const char *path);
+int mm_tune_load(const char *path);
+int mm_tune_clear(void);
 
 /*
  * FP64-accurate product emulated from slices (not in the paper; its
@@ -259,6 +282,8 @@ int mm_server_submit(mm_server *server, const mm_request *request); /* returns a
 int mm_server_poll(mm_server *server, mm_completion *out, int32_t cap); /* number of completions written */
 int mm_server_wait(mm_server *server, int64_t timeout_ms); /* MM_ERR_TIMEOUT if requests remain */
 int mm_server_stats(mm_server *server, mm_server_stats_t *out);
+/* Text of the first failure the server hit ("" if none); valid until destroy. */
+const char *mm_server_error(mm_server *server);
 /* Cancels requests that have not started (status MM_ERR_TIMEOUT), waits for
  * running batches, frees the server.  The arena may be reused afterwards. */
 int mm_server_destroy(mm_server *server);

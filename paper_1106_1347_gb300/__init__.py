@@ -13,7 +13,7 @@ import ctypes
 
 from ._native import KernelStat, MMError, check, lib
 
-__all__ = ["naive", "kahan", "winograd", "winograd_scaled", "strassen", "strassen_winograd", "norm_inf",
+__all__ = ["naive", "kahan", "winograd", "winograd_scaled", "strassen", "strassen_winograd", "tune_strassen", "norm_inf",
            "emulated", "emulated_group", "emulated_noalloc", "emulated_slices", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
            "SLICE_FP8E4M3"]
 
@@ -129,6 +129,18 @@ def strassen(a, b, cutoff=-1, out=None):
 def strassen_winograd(a, b, cutoff=-1, out=None):
     """Section "StrassenWinograd"."""
     return _strassen("mm_strassen_winograd", a, b, cutoff, out)
+
+
+def tune_strassen(a, b, variant=0):
+    """Times Strassen depths 0..3 on (A, B), records the fastest for this shape
+    bucket (used by cutoff=-1) and returns (depth, ms)."""
+    a, b, c, n, p, m = _prep(a, b, None)
+    need = lib().mm_tune_strassen_workspace_bytes(n, p, m)
+    ws = _ws(need, a.device)
+    depth, ms = ctypes.c_int32(-1), ctypes.c_double(0.0)
+    check("mm_tune_strassen", lib().mm_tune_strassen(int(variant), *_gemm_args(a, b, c, n, p, m), _ptr(ws), need,
+                                                     _stream(a.device), ctypes.byref(depth), ctypes.byref(ms)))
+    return int(depth.value), float(ms.value)
 
 
 def norm_inf(a):

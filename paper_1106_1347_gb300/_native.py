@@ -69,7 +69,13 @@ SIGNATURES = {
     "mm_server_poll": (ctypes.c_int, [vp, ctypes.POINTER(Completion), i32]),
     "mm_server_wait": (ctypes.c_int, [vp, i64]),
     "mm_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
+    "mm_server_error": (ctypes.c_char_p, [vp]),
     "mm_server_destroy": (ctypes.c_int, [vp]),
+    "mm_tune_strassen_workspace_bytes": (sz, [i64, i64, i64]),
+    "mm_tune_strassen": (ctypes.c_int, [i32] + GEMM + [vp, sz, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
+    "mm_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "mm_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "mm_tune_clear": (ctypes.c_int, []),
     "mm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mm_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelStat), i32]),
 }

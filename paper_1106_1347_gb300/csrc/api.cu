@@ -225,7 +225,7 @@ static size_t strassen_ws_query(int variant, int64_t N, int64_t P, int64_t M, in
     int depth;
     int64_t Np, Pp, Mp;
     if (N <= 0 || P <= 0 || M <= 0) return 0;
-    if (strassen_plan(N, P, M, cutoff, &depth, &Np, &Pp, &Mp) != MM_OK) return 0;
+    if (strassen_plan(variant, N, P, M, cutoff, &depth, &Np, &Pp, &Mp) != MM_OK) return 0;
     return strassen_ws_bytes(variant, depth, Np, Pp, Mp);
 }
 
@@ -247,7 +247,7 @@ static int strassen_common(const char *fn, int variant, int64_t N, int64_t P, in
     if (P == 0) return run_zero(N, M, C, ldc, st);
     int depth;
     int64_t Np, Pp, Mp;
-    rc = strassen_plan(N, P, M, cutoff, &depth, &Np, &Pp, &Mp);
+    rc = strassen_plan(variant, N, P, M, cutoff, &depth, &Np, &Pp, &Mp);
     if (rc) return rc;
     size_t need = strassen_ws_bytes(variant, depth, Np, Pp, Mp);
     if (ws_bytes < need || (need && !ws))

@@ -72,8 +72,9 @@ int run_kahan(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, con
 size_t winograd_ws_bytes(int64_t N, int64_t P, int64_t M, bool scaled);
 int run_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
                  double *C, int64_t ldc, bool scaled, int32_t *lambda_out, void *ws, cudaStream_t st);
-int strassen_plan(int64_t N, int64_t P, int64_t M, int32_t cutoff, int *depth, int64_t *Np, int64_t *Pp,
-                  int64_t *Mp);
+int strassen_plan(int variant, int64_t N, int64_t P, int64_t M, int32_t cutoff, int *depth, int64_t *Np,
+                  int64_t *Pp, int64_t *Mp);
+bool tuned_strassen_depth(int variant, int64_t N, int64_t P, int64_t M, int *depth);
 size_t strassen_ws_bytes(int variant, int depth, int64_t Np, int64_t Pp, int64_t Mp);
 int run_strassen(int variant, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
                  int64_t ldb, double *C, int64_t ldc, int depth, int64_t Np, int64_t Pp, int64_t Mp, void *ws,
@@ -96,7 +97,7 @@ struct GroupLaunch {
 size_t group_table_bytes(int count);
 size_t problem_data_bytes(const mm_problem &q, int s);
 size_t group_data_bytes(const mm_problem *probs, int count, int s);
-int group_build(const mm_problem *probs, int count, int s, void *table_dev, char *const *data,
+int group_build(const mm_problem *probs, int count, int capacity, int s, void *table_dev, char *const *data,
                 std::vector<unsigned char> &image, GroupLaunch &gl);
 int group_kernels(const GroupLaunch &gl, cudaStream_t st);
 void prof_suspend(bool on);  // skip kernel timing while a stream is being captured
@@ -165,6 +166,11 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
             "r"(smem_u32(dst)),
         "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
         : "memory");
+}
+// Makes a tensor map that lives in global memory, and was written through the
+// generic proxy (host copy or device store), visible to the TMA unit.
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
 }
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");

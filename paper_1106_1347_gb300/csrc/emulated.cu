@@ -263,7 +263,7 @@ __device__ __forceinline__ double int128_to_double(int64_t hi, uint64_t lo) {
 // the CTA.  tmA / tmB are the problem's slice tensor maps (kernel parameters
 // or entries of a grouped launch's table in global memory).
 __device__ __forceinline__ void slice_tile(const CUtensorMap *tmA, const CUtensorMap *tmB, const EmuParams &p,
-                                           int tm, int tn) {
+                                           int tm, int tn, bool maps_in_global) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bars[2 * 8 + 3];
     __shared__ uint32_t tmem_slot;
@@ -299,6 +299,10 @@ __device__ __forceinline__ void slice_tile(const CUtensorMap *tmA, const CUtenso
 
     if (warp == 0) {
         if (lane == 0) {
+            if (maps_in_global) {  // the grouped table is rewritten in place between launches
+                mmdev::tmap_acquire(tmA);
+                mmdev::tmap_acquire(tmB);
+            }
             mmdev::prefetch_tmap(tmA);
             mmdev::prefetch_tmap(tmB);
             int issued = 0;
@@ -449,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                       const EmuParams p) {
     int tm, tn;
     tile_of(blockIdx.x, p.tiles_m, p.tiles_n, tm, tn);
-    slice_tile(&tmA, &tmB, p, tm, tn);
+    slice_tile(&tmA, &tmB, p, tm, tn, false);
 }
 
 // ------------------------------------------------------------ grouped launch
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1) group_slice_gemm_kernel(const Emu
     const EmuParams prm = e.prm;
     int tm, tn;
     tile_of(u - begin[g], prm.tiles_m, prm.tiles_n, tm, tn);
-    slice_tile(&e.tmA, &e.tmB, prm, tm, tn);
+    slice_tile(&e.tmA, &e.tmB, prm, tm, tn, true);
 }
 
 cudaError_t slice_smem_attributes();
@@ -710,6 +714,9 @@ namespace mm {
 // arrays), and per problem a data region [column maxima | e | f | A slices |
 // B slices].  mm_emulated_group places the data regions right after the
 // table; the serving loop keeps each request's region with its operands.
+// The table part is laid out for a fixed capacity (>= the problem count) so
+// that its header and prefix arrays sit at the same addresses for every
+// batch: a CUDA graph captured for one batch is replayed for others.
 struct GroupLayout {
     size_t off_table, off_hdr, off_begin[5], table_bytes;
 };
@@ -790,10 +797,12 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
 
 // Builds the host image of the table part for the problems (all N, P, M >= 1)
 // -- to be copied to `table_dev` -- and the launch description.  data[i] is
-// problem i's data region of problem_data_bytes(probs[i], s) bytes.
-int group_build(const mm_problem *probs, int count, int s, void *table_dev, char *const *data,
+// problem i's data region of problem_data_bytes(probs[i], s) bytes; the table
+// is laid out for `capacity` problems (>= count).
+int group_build(const mm_problem *probs, int count, int capacity, int s, void *table_dev, char *const *data,
                 std::vector<unsigned char> &image, GroupLaunch &gl) {
-    const GroupLayout G = group_layout(count);
+    if (capacity < count) return fail(MM_ERR_ARG, "grouped launch: %d problems exceed capacity %d", count, capacity);
+    const GroupLayout G = group_layout(capacity);
     char *t = (char *)table_dev;
     image.assign(G.table_bytes, 0);
     EmuProblem *tab = (EmuProblem *)(image.data() + G.off_table);
@@ -874,7 +883,7 @@ int run_emulated_group(const mm_problem *probs, int count, int s, void *ws, cuda
         data[i] = d;
         d += problem_data_bytes(live[i], s);
     }
-    int rc = group_build(live.data(), (int)live.size(), s, ws, data.data(), image, gl);
+    int rc = group_build(live.data(), (int)live.size(), (int)live.size(), s, ws, data.data(), image, gl);
     if (rc) return rc;
     // Pageable source: the copy is staged before cudaMemcpyAsync returns, so `image` may go.
     cudaError_t e = cudaMemcpyAsync((void *)gl.tab, image.data(), image.size(), cudaMemcpyHostToDevice, st);

@@ -23,10 +23,12 @@
 // elementwise kernel; only the innermost level is fused.
 //
 // Tiling: 64x64 output tile, K-step 16, 4 warps each owning 32x32 (4x4 MMA
-// tiles of 8x8x4).  The kernel is bound by the FP64 MMA pipe (~4.2 TFLOP/s
-// measured on GB300 against ~1.0 for DFMA), so operand tiles are staged with
-// plain coalesced loads into padded, bank-conflict-free shared memory (the
-// expression evaluation happens in those loads), prefetched one K-step ahead.
+// tiles of 8x8x4).  The kernel is bound by the FP64 pipe: on GB300 the
+// m8n8k4 f64 MMA and DFMA both measure ~1.06 TFLOP/s, and the MMA needs 16x
+// fewer instructions.  At that rate the loads do not matter, so operand tiles
+// are staged with plain coalesced loads into padded, bank-conflict-free shared
+// memory (the expression evaluation happens in those loads), prefetched one
+// K-step ahead.
 #include <vector>
 
 #include "common.cuh"
@@ -495,8 +497,8 @@ int run_naive(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, con
 }
 
 // Depth and padded sizes of the recursion (see mm_strassen in mm.h).
-int strassen_plan(int64_t N, int64_t P, int64_t M, int32_t cutoff, int *depth, int64_t *Np, int64_t *Pp,
-                  int64_t *Mp) {
+int strassen_plan(int variant, int64_t N, int64_t P, int64_t M, int32_t cutoff, int *depth, int64_t *Np,
+                  int64_t *Pp, int64_t *Mp) {
     const int64_t X = std::max(N, std::max(P, M));
     int d = 0;
     if (cutoff == 0) {  // the paper's rule, square embedding
@@ -509,7 +511,8 @@ int strassen_plan(int64_t N, int64_t P, int64_t M, int32_t cutoff, int *depth, i
     } else {
         if (cutoff > 0) {
             while (ceil_div(X, (int64_t)1 << d) > cutoff) ++d;
-        } else {  // tuned: one level per doubling above 1024
+        } else if (!tuned_strassen_depth(variant, N, P, M, &d)) {
+            // untuned default: one level per doubling above 1024, at most 3
             for (int64_t t = X; t >= 2048 && d < 3; t >>= 1) ++d;
         }
         const int64_t q = (int64_t)1 << d;

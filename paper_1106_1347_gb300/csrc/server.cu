@@ -27,6 +27,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <tuple>
 #include <vector>
@@ -163,6 +164,15 @@ struct mm_server {
     bool have_first = false;
     Clock::time_point first_arrival, last_done;
     int fatal = MM_OK;
+    std::string fatal_msg;
+
+    void set_fatal(int rc) {  // keeps the first failure's status and message
+        std::lock_guard<std::mutex> g(res_mu);
+        if (fatal == MM_OK) {
+            fatal = rc;
+            fatal_msg = mm_last_error();
+        }
+    }
 
     void finish(Req *q, int status, Clock::time_point now) {
         mm_completion c{};
@@ -196,10 +206,7 @@ struct mm_server {
             }
             const Clock::time_point now = Clock::now();
             const int st = (e == cudaSuccess) ? MM_OK : MM_ERR_CUDA;
-            if (e != cudaSuccess) {
-                std::lock_guard<std::mutex> g(res_mu);
-                fatal = MM_ERR_CUDA;
-            }
+            if (e != cudaSuccess) set_fatal(mm::cuda_fail(e, "server: batch completion"));
             for (Req *q : b.reqs) {
                 arena.release(q->block, q->block_bytes);
                 finish(q, st, now);
@@ -247,8 +254,7 @@ struct mm_server {
                 probs.push_back(mm_problem{q->r.N, q->r.P, q->r.M, q->dA, q->r.P, q->dB, q->r.M, q->dC, q->r.M});
                 data.push_back(q->block + operand_bytes(q->r));
             }
-            if (mm::group_table_bytes((int)probs.size()) > sl.table_cap)
-                return mm::fail(MM_ERR_NOMEM, "server: batch table exceeds its slot");
+            if ((int)probs.size() > max_batch) return mm::fail(MM_ERR_NOMEM, "server: batch exceeds max_batch");
         }
         auto give_back = [&](int rc) {
             cudaStreamSynchronize(st);  // nothing of this batch may still touch its memory
@@ -270,7 +276,8 @@ struct mm_server {
         } else {
             std::vector<unsigned char> image;
             mm::GroupLaunch gl{};
-            rc = mm::group_build(probs.data(), (int)probs.size(), s, sl.table_dev, data.data(), image, gl);
+            rc = mm::group_build(probs.data(), (int)probs.size(), max_batch, s, sl.table_dev, data.data(), image,
+                                 gl);
             if (rc) return give_back(rc);
             std::memcpy(sl.staging, image.data(), image.size());
             cudaError_t e = cudaMemcpyAsync(sl.table_dev, sl.staging, image.size(), cudaMemcpyHostToDevice, st);
@@ -344,10 +351,7 @@ struct mm_server {
             if (rc == MM_OK) {
                 any = true;
             } else {
-                {
-                    std::lock_guard<std::mutex> g(res_mu);
-                    fatal = rc;
-                }
+                set_fatal(rc);
                 const Clock::time_point now = Clock::now();
                 for (Req *q : take) {
                     arena.release(q->block, q->block_bytes);
@@ -514,6 +518,12 @@ int mm_server_stats(mm_server *s, mm_server_stats_t *out) {
     }
     *out = st;
     return MM_OK;
+}
+
+const char *mm_server_error(mm_server *s) {
+    if (!s) return "";
+    std::lock_guard<std::mutex> g(s->res_mu);
+    return s->fatal_msg.c_str();
 }
 
 int mm_server_destroy(mm_server *s) {

@@ -87,6 +87,10 @@ class Server:
     def wait(self, timeout_s: float = 600.0) -> int:
         return int(self._L.mm_server_wait(self._h, int(timeout_s * 1000)))
 
+    def error(self) -> str:
+        msg = self._L.mm_server_error(self._h)
+        return msg.decode() if msg else ""
+
     def stats(self) -> dict:
         st = Stats()
         check("mm_server_stats", self._L.mm_server_stats(self._h, ctypes.byref(st)))
@@ -133,4 +137,6 @@ def replay(server: Server, trace, a_pool, b_pool, c_pool, time_scale: float = 1.
         server.submit(a_pool[:n, :p], b_pool[:p, :m], c, tier=req["tier"], tag=req["id"])
     rc = server.wait()
     comps = server.poll(len(trace) + 16)
+    if rc != 0:
+        raise RuntimeError(f"serving failed with status {rc}: {server.error()}")
     return server.stats(), comps, rc

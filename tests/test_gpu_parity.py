@@ -293,3 +293,26 @@ def test_argument_errors(mm):
 
 def test_no_timeouts_raised(mm):
     assert mm.device_status() == 0
+
+
+# -------------------------------------------------------------- autotuner
+
+def test_tune_strassen_records_and_persists(mm, orc, tmp_path):
+    import ctypes
+
+    L = mm.lib()
+    L.mm_tune_clear()
+    a, b = pair(600, 520, 560, "uni", 21)
+    depth, ms = mm.tune_strassen(dev(a), dev(b), variant=0)
+    assert 0 <= depth <= 3 and ms > 0
+    q = 1 << depth
+    want = 0 if depth <= 1 else L.mm_strassen_workspace_bytes(600, 520, 560, max(1, -(-600 // q)))
+    assert L.mm_strassen_workspace_bytes(600, 520, 560, -1) == want
+    got = host(mm.strassen(dev(a), dev(b), cutoff=-1))
+    assert orc.rel_inf_error(got, orc.dot2_product(a, b), a, b) <= TOL
+    path = str(tmp_path / "tune.txt").encode()
+    assert L.mm_tune_save(path) == 0
+    L.mm_tune_clear()
+    assert L.mm_tune_load(path) == 1
+    assert L.mm_strassen_workspace_bytes(600, 520, 560, -1) == want
+    L.mm_tune_clear()

@@ -118,3 +118,19 @@ def test_fp64_baseline_mode(srv):
         assert s.wait(120) == 0
     for a, b, c in cases:
         assert np.array_equal(c.numpy(), mm.naive(a.cuda(), b.cuda()).cpu().numpy())
+
+
+def test_graph_replay_across_batch_sizes(srv):
+    """Batches of 3 and then 4 requests of one shape have the same size bucket,
+    so the second replays the first one's CUDA graph with a different problem
+    count; results must still equal the single-call path."""
+    mm, serving = srv
+    with serving.Server(1 << 30, max_batch=16, nstreams=1, use_graphs=True) as s:
+        for count, base in ((3, 200), (4, 210), (3, 220)):
+            cases = [_case(base + i, 64, 64, 64) for i in range(count)]
+            for i, (a, b, c) in enumerate(cases):
+                s.submit(a, b, c, tier=1e-14, tag=base + i)
+            assert s.wait(60) == 0, s.error()
+            for a, b, c in cases:
+                assert np.array_equal(c.numpy(), mm.emulated(a.cuda(), b.cuda(), tier=1e-14).cpu().numpy())
+        assert s.stats()["graph_replays"] >= 1
