@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--serve-baseline-requests", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--variants-n", type=int, default=4096, help="size of the per-method FP64 timings (0: skip)")
+    ap.add_argument("--fp64-only", action="store_true", help="only the per-method FP64 timings (profiling runs)")
     args = ap.parse_args()
     global N, P, M, WORKLOAD
     if args.n != 8192:
@@ -268,6 +270,51 @@ def serve_bench(dev, requests, budget_gb, baseline_requests):
     }
 
 
+FP64_PEAK_TFLOPS = 1.056  # DFMA and mma.sync f64 on GB300, measured by the library's own probe
+
+
+def variants_bench(dev, n):
+    """Each FP64 method at n^3 (uniform [-1, 1] inputs): TFLOP/s as 2n^3/t and
+    the FP64-pipe work it issues against the measured FP64 peak."""
+    import torch
+
+    import paper_1106_1347_gb300 as mm
+    import synthetic as S
+
+    a = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 0))).to(dev)
+    b = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 1))).to(dev)
+    out = {}
+    # FP64-pipe operations (an FMA, DADD or DMUL each, or 1/256 of an m8n8k4 MMA)
+    # issued per reported flop (2n^3 per product): naive 1 FMA per 2 flop; Kahan
+    # 1 DMUL + 4 DADD per k; Winograd 2 DADD + 1 FMA per pair of k.
+    pipe = {"naive": 0.5, "kahan": 2.5, "winograd": 0.75, "winograd_scaled": 0.75}
+    peak_ops = FP64_PEAK_TFLOPS / 2.0  # FP64-pipe ops per second (1e12)
+    runs = {
+        "naive": lambda: mm.naive(a, b),
+        "kahan": lambda: mm.kahan(a, b),
+        "winograd": lambda: mm.winograd(a, b),
+        "winograd_scaled": lambda: mm.winograd_scaled(a, b),
+        "strassen": lambda: mm.strassen(a, b),
+        "strassen_winograd": lambda: mm.strassen_winograd(a, b),
+    }
+    for name, fn in runs.items():
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        tf = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+        entry = {"ms": ms, "tflops": tf}
+        if name in pipe:  # fraction of the FP64 pipe kept busy
+            entry["fp64_pipe_frac"] = tf * pipe[name] / peak_ops
+        out[name] = entry
+    return {"n": n, "inputs": "uniform [-1, 1]", "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+            "fp64_peak_source": "own probe: DFMA and mma.sync m8n8k4 f64 both ~1.06 TFLOP/s", "methods": out}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -378,6 +425,8 @@ def run_ours(args):
         out["e2e"] = {"value": flop / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                       "h2d_bytes_per_step": int(a.nbytes + b.nbytes), "d2h_bytes_per_step": int(N * M * 8)}
 
+        if args.variants_n > 0:
+            out["fp64_methods"] = variants_bench(dev, args.variants_n)
         if not args.no_serve:
             del ha, hb, hc
             out["serving"] = serve_bench(dev, args.serve_requests, args.serve_budget_gb,
@@ -408,6 +457,14 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.fp64_only:
+        import torch
+
+        from paper_1106_1347_gb300 import build as mmbuild
+
+        mmbuild.build()
+        print(json.dumps(variants_bench(torch.device("cuda", 0), args.variants_n)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

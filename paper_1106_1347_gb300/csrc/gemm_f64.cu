@@ -22,8 +22,8 @@
 // caller's workspace, like the paper's Aux matrices, and combine them with an
 // elementwise kernel; only the innermost level is fused.
 //
-// Tiling: 64x64 output tile, K-step 16, 4 warps each owning 32x32 (4x4 MMA
-// tiles of 8x8x4).  The kernel is bound by the FP64 pipe: on GB300 the
+// Tiling: 64x64 output tile (32x32 when that leaves SMs idle), K-step 16,
+// 4 warps each owning a quarter as 8x8x4 MMA tiles.  The kernel is bound by the FP64 pipe: on GB300 the
 // m8n8k4 f64 MMA and DFMA both measure ~1.06 TFLOP/s, and the MMA needs 16x
 // fewer instructions.  At that rate the loads do not matter, so operand tiles
 // are staged with plain coalesced loads into padded, bank-conflict-free shared
@@ -35,15 +35,23 @@
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BK = 16;
 constexpr int AST = BK + 4;  // A tile row stride (doubles): conflict-free fragment reads
-constexpr int BST = BN + 4;  // B tile row stride
 
-enum : uint8_t { T11 = 0, T12 = 1, T21 = 2, T22 = 3, OP_ADD = 8, OP_SUB = 9 };
+enum : uint8_t { T11 = 0, T12 = 1, T21 = 2, T22 = 3 };
 
+// An operand sum as one of the seven tree shapes the paper's schedules use,
+// with op[i] = +1 (Plus) or -1 (Minus); each node is rounded as the paper's
+// Plus/Minus matrices are:
+//   S1: t0                        S2: t0 o0 t1
+//   S3: t0 o0 (t1 o1 t2)          S4: (t0 o0 t1) o1 t2
+//   S5: t0 o0 (t1 o1 (t2 o2 t3))  S6: t0 o0 ((t1 o1 t2) o2 t3)
+//   S7: ((t0 o0 t1) o1 t2) o2 t3
+// Fixed shapes keep the evaluation in registers (no indexed stack).
 struct Expr {
-    uint8_t code[8];
-    uint8_t len;
+    uint8_t shape;
+    uint8_t term[4];
+    int8_t op[3];
 };
 struct Target {
     uint8_t quad;
@@ -72,30 +80,37 @@ __device__ __forceinline__ double view_at(const View &v, int64_t r, int64_t c) {
     return (r < v.rows && c < v.cols) ? v.p[r * v.ld + c] : 0.0;
 }
 
-// Postfix evaluation of an operand element; quadrant (qr, qc) of term t sits
-// at row offset (t >> 1) * rstep and column offset (t & 1) * cstep.
+__device__ __forceinline__ double pm(double x, int8_t op, double y) {
+    return op > 0 ? __dadd_rn(x, y) : __dsub_rn(x, y);
+}
+
+// Evaluates the shape on already loaded terms v[0..3].
+__device__ __forceinline__ double eval_shape(const Expr &e, const double (&v)[4]) {
+    switch (e.shape) {
+        case 1: return v[0];
+        case 2: return pm(v[0], e.op[0], v[1]);
+        case 3: return pm(v[0], e.op[0], pm(v[1], e.op[1], v[2]));
+        case 4: return pm(pm(v[0], e.op[0], v[1]), e.op[1], v[2]);
+        case 5: return pm(v[0], e.op[0], pm(v[1], e.op[1], pm(v[2], e.op[2], v[3])));
+        case 6: return pm(v[0], e.op[0], pm(pm(v[1], e.op[1], v[2]), e.op[2], v[3]));
+        default: return pm(pm(pm(v[0], e.op[0], v[1]), e.op[1], v[2]), e.op[2], v[3]);
+    }
+}
+
+__device__ __forceinline__ int expr_terms(const Expr &e) {
+    return e.shape == 1 ? 1 : e.shape == 2 ? 2 : (e.shape == 3 || e.shape == 4) ? 3 : 4;
+}
+
+// Operand element (r, c) of the expression over quadrants of v; quadrant t
+// sits at row offset (t >> 1) * rstep and column offset (t & 1) * cstep.
 __device__ __forceinline__ double eval_expr(const Expr &e, const View &v, int64_t r, int64_t c, int64_t rstep,
                                             int64_t cstep) {
-    if (e.len == 1) return view_at(v, r + (e.code[0] >> 1) * rstep, c + (e.code[0] & 1) * cstep);
-    double st[4];
-    int sp = 0;
+    double x[4] = {0.0, 0.0, 0.0, 0.0};
+    const int nt = expr_terms(e);
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        if (t < e.len) {
-            const uint8_t op = e.code[t];
-            if (op < 4) {
-                const double x = view_at(v, r + (op >> 1) * rstep, c + (op & 1) * cstep);
-                st[sp] = x;
-                ++sp;
-            } else {
-                const double y = st[sp - 1], x = st[sp - 2];
-                sp -= 2;
-                st[sp] = (op == OP_ADD) ? __dadd_rn(x, y) : __dsub_rn(x, y);
-                ++sp;
-            }
-        }
-    }
-    return st[0];
+    for (int t = 0; t < 4; ++t)
+        if (t < nt) x[t] = view_at(v, r + (e.term[t] >> 1) * rstep, c + (e.term[t] & 1) * cstep);
+    return eval_shape(e, x);
 }
 
 __device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
@@ -104,8 +119,13 @@ __device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
                  : "d"(a), "d"(b));
 }
 
-template <bool kSingle>
+// BM x BN output tile per CTA of 4 warps (2 x 2), each warp owning
+// (BM/2) x (BN/2) as MI x NI MMA tiles of 8 x 8.  64 x 64 for large grids,
+// 32 x 32 when the 64 x 64 grid would leave SMs idle.
+template <bool kSingle, int BM, int BN>
 __global__ void __launch_bounds__(128) level_kernel(const __grid_constant__ LevelArgs args) {
+    constexpr int BST = BN + 4;  // B tile row stride
+    constexpr int MI = BM / 16, NI = BN / 16, RA = BM * BK / 128, RB = BK * BN / 128;
     __shared__ __align__(16) double As[BM][AST];
     __shared__ __align__(16) double Bs[BK][BST];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -116,15 +136,15 @@ __global__ void __launch_bounds__(128) level_kernel(const __grid_constant__ Leve
 
     for (int pi = 0; pi < args.nprod; ++pi) {
         const Product &pr = args.prod[pi];
-        double acc[4][4][2];
+        double acc[MI][NI][2];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < MI; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
-        double ra[8], rb[8];
+            for (int b = 0; b < NI; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+        double ra[RA], rb[RB];
         auto fetch = [&](int64_t k0) {
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < RA; ++r) {
                 const int e = tid + 128 * r;
                 const int64_t gi = i0 + (e >> 4), gk = k0 + (e & 15);
                 double v = 0.0;
@@ -137,9 +157,9 @@ __global__ void __launch_bounds__(128) level_kernel(const __grid_constant__ Leve
                 ra[r] = v;
             }
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < RB; ++r) {
                 const int e = tid + 128 * r;
-                const int64_t gk = k0 + (e >> 6), gj = j0 + (e & 63);
+                const int64_t gk = k0 + e / BN, gj = j0 + e % BN;
                 double v = 0.0;
                 if (gk < p && gj < m) {
                     if (kSingle)
@@ -154,24 +174,28 @@ __global__ void __launch_bounds__(128) level_kernel(const __grid_constant__ Leve
         for (int64_t k0 = 0; k0 < p; k0 += BK) {
             __syncthreads();
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < RA; ++r) {
                 const int e = tid + 128 * r;
                 As[e >> 4][e & 15] = ra[r];
-                Bs[e >> 6][e & 63] = rb[r];
+            }
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const int e = tid + 128 * r;
+                Bs[e / BN][e % BN] = rb[r];
             }
             __syncthreads();
             if (k0 + BK < p) fetch(k0 + BK);
 #pragma unroll
             for (int kk = 0; kk < BK; kk += 4) {
-                double af[4], bf[4];
+                double af[MI], bf[NI];
 #pragma unroll
-                for (int mi = 0; mi < 4; ++mi) af[mi] = As[wm * 32 + mi * 8 + g][kk + t4];
+                for (int mi = 0; mi < MI; ++mi) af[mi] = As[wm * (BM / 2) + mi * 8 + g][kk + t4];
 #pragma unroll
-                for (int ni = 0; ni < 4; ++ni) bf[ni] = Bs[kk + t4][wn * 32 + ni * 8 + g];
+                for (int ni = 0; ni < NI; ++ni) bf[ni] = Bs[kk + t4][wn * (BN / 2) + ni * 8 + g];
 #pragma unroll
-                for (int mi = 0; mi < 4; ++mi)
+                for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
-                    for (int ni = 0; ni < 4; ++ni) dmma_8x8x4(acc[mi][ni], af[mi], bf[ni]);
+                    for (int ni = 0; ni < NI; ++ni) dmma_8x8x4(acc[mi][ni], af[mi], bf[ni]);
             }
         }
         // Epilogue: fold +-H into each target quadrant (vectorised when aligned).
@@ -180,13 +204,13 @@ __global__ void __launch_bounds__(128) level_kernel(const __grid_constant__ Leve
             const int64_t roff = (tg.quad >> 1) * n, coff = (tg.quad & 1) * m;
             const double sgn = (double)tg.sign;
 #pragma unroll
-            for (int mi = 0; mi < 4; ++mi) {
-                const int64_t row = i0 + wm * 32 + mi * 8 + g;
+            for (int mi = 0; mi < MI; ++mi) {
+                const int64_t row = i0 + wm * (BM / 2) + mi * 8 + g;
                 const int64_t crow = row + roff;
                 if (row >= n || crow >= args.crows) continue;
 #pragma unroll
-                for (int ni = 0; ni < 4; ++ni) {
-                    const int64_t col = j0 + wn * 32 + ni * 8 + 2 * t4;
+                for (int ni = 0; ni < NI; ++ni) {
+                    const int64_t col = j0 + wn * (BN / 2) + ni * 8 + 2 * t4;
                     const int64_t ccol = col + coff;
                     double *dst = args.C + crow * args.ldc + ccol;
                     const double v0 = sgn * acc[mi][ni][0], v1 = sgn * acc[mi][ni][1];
@@ -224,66 +248,93 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Co
     const int64_t j = (int64_t)blockIdx.x * 64 + (threadIdx.x & 63);
     const int64_t i = (int64_t)blockIdx.y * 4 + (threadIdx.x >> 6);
     if (i >= a.rows || j >= a.cols) return;
-    double st[4];
-    int sp = 0;
+    double x[4] = {0.0, 0.0, 0.0, 0.0};
+    const int nt = expr_terms(a.e);
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        if (t < a.e.len) {
-            const uint8_t op = a.e.code[t];
-            if (op < 4) {
-                st[sp] = view_at(a.term[op], i, j);
-                ++sp;
-            } else {
-                const double y = st[sp - 1], x = st[sp - 2];
-                sp -= 2;
-                st[sp] = (op == OP_ADD) ? __dadd_rn(x, y) : __dsub_rn(x, y);
-                ++sp;
-            }
-        }
-    }
-    a.out[i * a.ldo + j] = st[0];
+    for (int t = 0; t < 4; ++t)
+        if (t < nt) x[t] = view_at(a.term[a.e.term[t]], i, j);
+    a.out[i * a.ldo + j] = eval_shape(a.e, x);
 }
 
-Expr ex(std::initializer_list<uint8_t> c) {
-    Expr e{};
-    e.len = 0;
-    for (uint8_t x : c) e.code[e.len++] = x;
-    return e;
+constexpr int8_t P_ = 1, M_ = -1;  // Plus, Minus
+Expr E1(uint8_t t0) { return Expr{1, {t0, 0, 0, 0}, {0, 0, 0}}; }
+Expr E2(uint8_t t0, int8_t o0, uint8_t t1) { return Expr{2, {t0, t1, 0, 0}, {o0, 0, 0}}; }
+Expr E3(uint8_t t0, int8_t o0, uint8_t t1, int8_t o1, uint8_t t2) {  // t0 o0 (t1 o1 t2)
+    return Expr{3, {t0, t1, t2, 0}, {o0, o1, 0}};
+}
+Expr E4(uint8_t t0, int8_t o0, uint8_t t1, int8_t o1, uint8_t t2) {  // (t0 o0 t1) o1 t2
+    return Expr{4, {t0, t1, t2, 0}, {o0, o1, 0}};
+}
+Expr E5(uint8_t t0, int8_t o0, uint8_t t1, int8_t o1, uint8_t t2, int8_t o2, uint8_t t3) {
+    return Expr{5, {t0, t1, t2, t3}, {o0, o1, o2}};  // t0 o0 (t1 o1 (t2 o2 t3))
+}
+Expr E6(uint8_t t0, int8_t o0, uint8_t t1, int8_t o1, uint8_t t2, int8_t o2, uint8_t t3) {
+    return Expr{6, {t0, t1, t2, t3}, {o0, o1, o2}};  // t0 o0 ((t1 o1 t2) o2 t3)
+}
+Expr E7(uint8_t t0, int8_t o0, uint8_t t1, int8_t o1, uint8_t t2, int8_t o2, uint8_t t3) {
+    return Expr{7, {t0, t1, t2, t3}, {o0, o1, o2}};  // ((t0 o0 t1) o1 t2) o2 t3
 }
 Target tgt(uint8_t q, int s, bool first) { return Target{q, (int8_t)s, (uint8_t)(first ? 1 : 0)}; }
 
 // One recursion level of section "StrassenNaiv", in the order H1 H3 H2 H4 H5 H6 H7.
 void strassen_products(Product (&pr)[7]) {
-    pr[0] = Product{ex({T11, T22, OP_ADD}), ex({T11, T22, OP_ADD}), 2, {tgt(T11, 1, true), tgt(T22, 1, true)}};
-    pr[1] = Product{ex({T11}), ex({T12, T22, OP_SUB}), 2, {tgt(T12, 1, true), tgt(T22, 1, false)}};
-    pr[2] = Product{ex({T21, T22, OP_ADD}), ex({T11}), 2, {tgt(T21, 1, true), tgt(T22, -1, false)}};
-    pr[3] = Product{ex({T22}), ex({T21, T11, OP_SUB}), 2, {tgt(T11, 1, false), tgt(T21, 1, false)}};
-    pr[4] = Product{ex({T11, T12, OP_ADD}), ex({T22}), 2, {tgt(T11, -1, false), tgt(T12, 1, false)}};
-    pr[5] = Product{ex({T21, T11, OP_SUB}), ex({T11, T12, OP_ADD}), 1, {tgt(T22, 1, false)}};
-    pr[6] = Product{ex({T12, T22, OP_SUB}), ex({T21, T22, OP_ADD}), 1, {tgt(T11, 1, false)}};
+    pr[0] = Product{E2(T11, P_, T22), E2(T11, P_, T22), 2, {tgt(T11, 1, true), tgt(T22, 1, true)}};
+    pr[1] = Product{E1(T11), E2(T12, M_, T22), 2, {tgt(T12, 1, true), tgt(T22, 1, false)}};
+    pr[2] = Product{E2(T21, P_, T22), E1(T11), 2, {tgt(T21, 1, true), tgt(T22, -1, false)}};
+    pr[3] = Product{E1(T22), E2(T21, M_, T11), 2, {tgt(T11, 1, false), tgt(T21, 1, false)}};
+    pr[4] = Product{E2(T11, P_, T12), E1(T22), 2, {tgt(T11, -1, false), tgt(T12, 1, false)}};
+    pr[5] = Product{E2(T21, M_, T11), E2(T11, P_, T12), 1, {tgt(T22, 1, false)}};
+    pr[6] = Product{E2(T12, M_, T22), E2(T21, P_, T22), 1, {tgt(T11, 1, false)}};
 }
 
 // One recursion level of section "StrassenWinograd", H1..H7, with
 // A1 = A11-A21, A2 = A22-A1, B1 = B22-B12, B2 = B1+B11 written out per use.
 void strassen_winograd_products(Product (&pr)[7]) {
-    pr[0] = Product{ex({T11}), ex({T11}), 4,
+    pr[0] = Product{E1(T11), E1(T11), 4,
                     {tgt(T11, 1, true), tgt(T12, 1, true), tgt(T21, 1, true), tgt(T22, 1, true)}};
-    pr[1] = Product{ex({T12}), ex({T21}), 1, {tgt(T11, 1, false)}};
-    pr[2] = Product{ex({T22, T11, T21, OP_SUB, OP_SUB}), ex({T22, T12, OP_SUB, T11, OP_ADD}), 3,
+    pr[1] = Product{E1(T12), E1(T21), 1, {tgt(T11, 1, false)}};
+    // A2 = A22 - (A11 - A21), B2 = (B22 - B12) + B11
+    pr[2] = Product{E3(T22, M_, T11, M_, T21), E4(T22, M_, T12, P_, T11), 3,
                     {tgt(T12, 1, false), tgt(T21, 1, false), tgt(T22, 1, false)}};
-    pr[3] = Product{ex({T21, T22, OP_ADD}), ex({T12, T11, OP_SUB}), 2, {tgt(T12, 1, false), tgt(T22, 1, false)}};
-    pr[4] = Product{ex({T11, T21, OP_SUB}), ex({T22, T12, OP_SUB}), 2, {tgt(T21, 1, false), tgt(T22, 1, false)}};
-    pr[5] = Product{ex({T12, T22, T11, T21, OP_SUB, OP_SUB, OP_SUB}), ex({T22}), 1, {tgt(T12, 1, false)}};
-    pr[6] = Product{ex({T22}), ex({T21, T22, T12, OP_SUB, T11, OP_ADD, OP_SUB}), 1, {tgt(T21, 1, false)}};
+    pr[3] = Product{E2(T21, P_, T22), E2(T12, M_, T11), 2, {tgt(T12, 1, false), tgt(T22, 1, false)}};
+    pr[4] = Product{E2(T11, M_, T21), E2(T22, M_, T12), 2, {tgt(T21, 1, false), tgt(T22, 1, false)}};
+    // A12 - A2 = A12 - (A22 - (A11 - A21))
+    pr[5] = Product{E5(T12, M_, T22, M_, T11, M_, T21), E1(T22), 1, {tgt(T12, 1, false)}};
+    // B21 - B2 = B21 - ((B22 - B12) + B11)
+    pr[6] = Product{E1(T22), E6(T21, M_, T22, M_, T12, P_, T11), 1, {tgt(T21, 1, false)}};
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
 }
 
 int launch_level(const LevelArgs &a, bool single, cudaStream_t st) {
-    dim3 grid((unsigned)mm::ceil_div(a.m, BN), (unsigned)mm::ceil_div(a.n, BM));
-    if (grid.x == 0 || grid.y == 0) return MM_OK;
+    if (a.m <= 0 || a.n <= 0) return MM_OK;
+    // 64 x 64 tiles when they give at least four CTAs per SM, else 32 x 32.
+    const bool big = mm::ceil_div(a.m, 64) * mm::ceil_div(a.n, 64) >= 4 * sm_count();
+    const int tile = big ? 64 : 32;
+    dim3 grid((unsigned)mm::ceil_div(a.m, tile), (unsigned)mm::ceil_div(a.n, tile));
     if (grid.y > 65535) return mm::fail(MM_ERR_UNSUPPORTED, "product too tall for one launch");
     if (single)
-        return mm::launch("gemm_f64_dmma", st, [&] { level_kernel<true><<<grid, 128, 0, st>>>(a); });
-    return mm::launch("strassen_level_dmma", st, [&] { level_kernel<false><<<grid, 128, 0, st>>>(a); });
+        return mm::launch("gemm_f64_dmma", st, [&] {
+            if (big)
+                level_kernel<true, 64, 64><<<grid, 128, 0, st>>>(a);
+            else
+                level_kernel<true, 32, 32><<<grid, 128, 0, st>>>(a);
+        });
+    return mm::launch("strassen_level_dmma", st, [&] {
+        if (big)
+            level_kernel<false, 64, 64><<<grid, 128, 0, st>>>(a);
+        else
+            level_kernel<false, 32, 32><<<grid, 128, 0, st>>>(a);
+    });
 }
 
 int launch_combine(const CombineArgs &a, cudaStream_t st) {
@@ -385,48 +436,48 @@ int node(int variant, int depth, int64_t n, int64_t p, int64_t m, const View &A,
         if (rc == MM_OK) rc = launch_combine(c, st);
     };
     if (variant == 0) {
-        child(mat_a(ex({T11, T22, OP_ADD})), mat_b(ex({T11, T22, OP_ADD})), H[1]);
-        child(mat_a(ex({T21, T22, OP_ADD})), qb(T11), H[2]);
-        child(qa(T11), mat_b(ex({T12, T22, OP_SUB})), H[3]);
-        child(qa(T22), mat_b(ex({T21, T11, OP_SUB})), H[4]);
-        child(mat_a(ex({T11, T12, OP_ADD})), qb(T22), H[5]);
+        child(mat_a(E2(T11, P_, T22)), mat_b(E2(T11, P_, T22)), H[1]);
+        child(mat_a(E2(T21, P_, T22)), qb(T11), H[2]);
+        child(qa(T11), mat_b(E2(T12, M_, T22)), H[3]);
+        child(qa(T22), mat_b(E2(T21, M_, T11)), H[4]);
+        child(mat_a(E2(T11, P_, T12)), qb(T22), H[5]);
         {
-            View sa = mat_a(ex({T21, T11, OP_SUB}));
-            View tb = mat_b(ex({T11, T12, OP_ADD}));
+            View sa = mat_a(E2(T21, M_, T11));
+            View tb = mat_b(E2(T11, P_, T12));
             child(sa, tb, H[6]);
         }
         {
-            View sa = mat_a(ex({T12, T22, OP_SUB}));
-            View tb = mat_b(ex({T21, T22, OP_ADD}));
+            View sa = mat_a(E2(T12, M_, T22));
+            View tb = mat_b(E2(T21, P_, T22));
             child(sa, tb, H[7]);
         }
         // C11 = ((H1+H4)-H5)+H7, C12 = H3+H5, C21 = H2+H4, C22 = ((H1+H3)-H2)+H6
-        combine_into(T11, {1, 4, 5, 7}, ex({0, 1, OP_ADD, 2, OP_SUB, 3, OP_ADD}));
-        combine_into(T12, {3, 5}, ex({0, 1, OP_ADD}));
-        combine_into(T21, {2, 4}, ex({0, 1, OP_ADD}));
-        combine_into(T22, {1, 3, 2, 6}, ex({0, 1, OP_ADD, 2, OP_SUB, 3, OP_ADD}));
+        combine_into(T11, {1, 4, 5, 7}, E7(0, P_, 1, M_, 2, P_, 3));
+        combine_into(T12, {3, 5}, E2(0, P_, 1));
+        combine_into(T21, {2, 4}, E2(0, P_, 1));
+        combine_into(T22, {1, 3, 2, 6}, E7(0, P_, 1, M_, 2, P_, 3));
     } else {
         double *A1 = arena.take(hn * hp), *A2 = arena.take(hn * hp);
         double *B1 = arena.take(hp * hm), *B2 = arena.take(hp * hm);
         // A1 = A11 - A21, A2 = A22 - A1, B1 = B22 - B12, B2 = B1 + B11
-        if (rc == MM_OK) rc = materialize(ex({T11, T21, OP_SUB}), A, hn, hp, A1, st);
+        if (rc == MM_OK) rc = materialize(E2(T11, M_, T21), A, hn, hp, A1, st);
         if (rc == MM_OK) {
             CombineArgs c{};
             c.term[0] = qa(T22);
             c.term[1] = dense(A1, hn, hp);
-            c.e = ex({0, 1, OP_SUB});
+            c.e = E2(0, M_, 1);
             c.out = A2;
             c.ldo = hp;
             c.rows = hn;
             c.cols = hp;
             rc = launch_combine(c, st);
         }
-        if (rc == MM_OK) rc = materialize(ex({T22, T12, OP_SUB}), B, hp, hm, B1, st);
+        if (rc == MM_OK) rc = materialize(E2(T22, M_, T12), B, hp, hm, B1, st);
         if (rc == MM_OK) {
             CombineArgs c{};
             c.term[0] = dense(B1, hp, hm);
             c.term[1] = qb(T11);
-            c.e = ex({0, 1, OP_ADD});
+            c.e = E2(0, P_, 1);
             c.out = B2;
             c.ldo = hm;
             c.rows = hp;
@@ -437,8 +488,8 @@ int node(int variant, int depth, int64_t n, int64_t p, int64_t m, const View &A,
         child(qa(T12), qb(T21), H[2]);
         child(dense(A2, hn, hp), dense(B2, hp, hm), H[3]);
         {
-            View sa = mat_a(ex({T21, T22, OP_ADD}));
-            View tb = mat_b(ex({T12, T11, OP_SUB}));
+            View sa = mat_a(E2(T21, P_, T22));
+            View tb = mat_b(E2(T12, M_, T11));
             child(sa, tb, H[4]);
         }
         child(dense(A1, hn, hp), dense(B1, hp, hm), H[5]);
@@ -446,7 +497,7 @@ int node(int variant, int depth, int64_t n, int64_t p, int64_t m, const View &A,
             CombineArgs c{};
             c.term[0] = qa(T12);
             c.term[1] = dense(A2, hn, hp);
-            c.e = ex({0, 1, OP_SUB});
+            c.e = E2(0, M_, 1);
             c.out = S;
             c.ldo = hp;
             c.rows = hn;
@@ -458,7 +509,7 @@ int node(int variant, int depth, int64_t n, int64_t p, int64_t m, const View &A,
             CombineArgs c{};
             c.term[0] = qb(T21);
             c.term[1] = dense(B2, hp, hm);
-            c.e = ex({0, 1, OP_SUB});
+            c.e = E2(0, M_, 1);
             c.out = T;
             c.ldo = hm;
             c.rows = hp;
@@ -467,10 +518,10 @@ int node(int variant, int depth, int64_t n, int64_t p, int64_t m, const View &A,
         }
         child(qa(T22), dense(T, hp, hm), H[7]);
         // C11 = H1+H2, C12 = ((H1+H3)+H4)+H6, C21 = ((H1+H3)+H5)+H7, C22 = ((H1+H3)+H4)+H5
-        combine_into(T11, {1, 2}, ex({0, 1, OP_ADD}));
-        combine_into(T12, {1, 3, 4, 6}, ex({0, 1, OP_ADD, 2, OP_ADD, 3, OP_ADD}));
-        combine_into(T21, {1, 3, 5, 7}, ex({0, 1, OP_ADD, 2, OP_ADD, 3, OP_ADD}));
-        combine_into(T22, {1, 3, 4, 5}, ex({0, 1, OP_ADD, 2, OP_ADD, 3, OP_ADD}));
+        combine_into(T11, {1, 2}, E2(0, P_, 1));
+        combine_into(T12, {1, 3, 4, 6}, E7(0, P_, 1, P_, 2, P_, 3));
+        combine_into(T21, {1, 3, 5, 7}, E7(0, P_, 1, P_, 2, P_, 3));
+        combine_into(T22, {1, 3, 4, 5}, E7(0, P_, 1, P_, 2, P_, 3));
     }
     return rc;
 }
@@ -492,7 +543,7 @@ int run_naive(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, con
     a.p = P;
     a.m = M;
     a.nprod = 1;
-    a.prod[0] = Product{ex({T11}), ex({T11}), 1, {tgt(T11, 1, true)}};
+    a.prod[0] = Product{E1(T11), E1(T11), 1, {tgt(T11, 1, true)}};
     return launch_level(a, true, st);
 }
 
