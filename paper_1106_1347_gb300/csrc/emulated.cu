@@ -21,7 +21,8 @@
 //   slice_gemm  -- 128x64 output tile per CTA.  Warp 0 issues TMA loads of all
 //                  s slices of a 32-wide K-block of A and B (3-D boxes,
 //                  64-byte swizzle) into a ring of shared-memory stages; warp 1
-//                  issues tcgen05.mma kind::f16 for every pair with
+//                  (one elected lane, warp-uniform operands) issues
+//                  tcgen05.mma kind::f16 for every pair with
 //                  sigma + tau = d into TMEM accumulator d (s x 64 FP32
 //                  columns); eight epilogue warps drain the accumulators every
 //                  K-chunk Kc, chosen so every partial sum is an integer below
@@ -323,47 +324,48 @@ __device__ __forceinline__ void slice_tile(const CUtensorMap *tmA, const CUtenso
                 (void)mmdev::mbar_wait(&full[kb % S], (uint32_t)((kb / S) & 1));
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            const uint32_t idesc = mmdev::idesc_bf16_f32(BM, BN);
-            bool ok = true;
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                const int st = kb % S, use = kb / S;
-                const int kin = kb % p.chunk_blocks, chunk = kb / p.chunk_blocks;
-                if (kin == 0 && chunk > 0) {
-                    if (!mmdev::mbar_wait(acc_empty, (uint32_t)((chunk - 1) & 1))) {
-                        raise_status(p.status, mm::kStatusTimeoutMma);
-                        ok = false;
-                        break;
-                    }
-                    mmdev::tc_fence_after();
-                }
-                if (!mmdev::mbar_wait(&full[st], (uint32_t)(use & 1))) {
-                    raise_status(p.status, mm::kStatusTimeoutMma);
-                    ok = false;
-                    break;
-                }
+        // The whole warp runs the issue loop; each MMA and commit is issued by one
+        // elected lane.  Descriptors are the stage's base descriptors plus
+        // compile-time offsets (the start-address field cannot carry: shared
+        // addresses stay below 2^18).
+        const uint32_t idesc = mmdev::idesc_bf16_f32(BM, BN);
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb % S, use = kb / S;
+            const int kin = kb % p.chunk_blocks, chunk = kb / p.chunk_blocks;
+            if (kin == 0 && chunk > 0) {
+                ok = __all_sync(0xffffffffu, mmdev::mbar_wait(acc_empty, (uint32_t)((chunk - 1) & 1)));
+                if (!ok) break;
                 mmdev::tc_fence_after();
-                const uint32_t a_base = mmdev::smem_u32(smem + (size_t)st * stage_bytes);
-                const uint32_t b_base = a_base + a_bytes;
-                for (int d = 0; d < s; ++d) {
+            }
+            ok = __all_sync(0xffffffffu, mmdev::mbar_wait(&full[st], (uint32_t)(use & 1)));
+            if (!ok) break;
+            mmdev::tc_fence_after();
+            const uint32_t a_base = mmdev::smem_u32(smem + (size_t)st * stage_bytes);
+            const uint64_t da = mmdev::smem_desc_sw64(a_base), db = mmdev::smem_desc_sw64(a_base + a_bytes);
+            const uint32_t first = kin == 0 ? 0u : 1u;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                if (d < s) {
+#pragma unroll
                     for (int sg = 0; sg <= d; ++sg) {
-                        const int tu = d - sg;
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
-                            const uint64_t ad = mmdev::smem_desc_sw64(a_base + (uint32_t)sg * (BM * BKE * 2) + kk * 32);
-                            const uint64_t bd = mmdev::smem_desc_sw64(b_base + (uint32_t)tu * (BN * BKE * 2) + kk * 32);
-                            const uint32_t accum = (kin == 0 && sg == 0 && kk == 0) ? 0u : 1u;
-                            mmdev::mma_bf16(tmem + (uint32_t)(d * BN), ad, bd, idesc, accum);
+                            const uint64_t ad = da + (uint64_t)((sg * (BM * BKE * 2) + kk * 32) >> 4);
+                            const uint64_t bd = db + (uint64_t)(((d - sg) * (BN * BKE * 2) + kk * 32) >> 4);
+                            mmdev::mma_bf16_elect(tmem + (uint32_t)(d * BN), ad, bd, idesc,
+                                                  (sg == 0 && kk == 0) ? first : 1u);
                         }
                     }
                 }
-                mmdev::mma_commit(&empty[st]);
-                if (kin == p.chunk_blocks - 1 || kb == nkb - 1) mmdev::mma_commit(acc_full);
             }
-            // Every MMA issued above has completed once mma_done flips.
-            mmdev::mma_commit(mma_done);
-            (void)mmdev::mbar_wait(mma_done, 0);
+            mmdev::mma_commit_elect(&empty[st]);
+            if (kin == p.chunk_blocks - 1 || kb == nkb - 1) mmdev::mma_commit_elect(acc_full);
         }
+        if (!ok && lane == 0) raise_status(p.status, mm::kStatusTimeoutMma);
+        // Every MMA issued above has completed once mma_done flips.
+        mmdev::mma_commit_elect(mma_done);
+        (void)mmdev::mbar_wait(mma_done, 0);
     } else {
         const int q = warp & 3, h = (warp - 2) >> 2;
         const int64_t row = m0 + 32 * q + lane;

@@ -198,8 +198,8 @@ def test_emulated_tier_accuracy(mm, orc):
 
 
 def test_emulated_multi_chunk_exactness(mm, orc):
-    """P spans several exact K-chunks (512 for 8 slices) and a ragged K tail."""
-    a, b = pair(130, 1700, 66, "uni", 16)
+    """P spans several exact K-chunks of every diagonal (512 to 4096 K for 8 slices) and a ragged K tail."""
+    a, b = pair(130, 9000, 66, "uni", 16)
     assert np.array_equal(host(mm.emulated(dev(a), dev(b), nslices=8)), orc.split_product(a, b, 7, 8))
 
 
@@ -209,6 +209,24 @@ def test_emulated_positive_worst_case_sums(mm, orc):
     a = np.abs(S.uniform(128, 1500, 171)) + 0.5
     b = np.abs(S.uniform(1500, 64, 172)) + 0.5
     assert np.array_equal(host(mm.emulated(dev(a), dev(b), nslices=8)), orc.split_product(a, b, 7, 8))
+
+
+def test_emulated_extreme_digit_sums(mm, orc):
+    """Every digit of x = -(63 2^49 + 64 (2^42 + 2^35 + ... + 1)) 2^-55 is -64
+    except the top one (-63), the largest magnitudes the balanced split allows,
+    so every diagonal's per-k product sum sits within 128 of (d + 1) 2^12.  With
+    rows of alternating sign and P beyond the longest exact chunk (4096 K for
+    diagonal 0), each accumulator runs through whole chunks at the edge of
+    FP32's exact integer range, positive and negative."""
+    v = 63 * 2 ** 49 + 64 * sum(2 ** (7 * t) for t in range(7))
+    x = -float(v) * 2.0 ** -55
+    assert x * 2.0 ** 55 == -v  # exactly representable
+    n, p, m = 130, 4500, 70
+    sign = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)[:, None]
+    a = np.full((n, p), x) * sign
+    b = np.full((p, m), x)
+    got = host(mm.emulated(dev(a), dev(b), nslices=8))
+    assert np.array_equal(got, orc.split_product(a, b, 7, 8))
 
 
 # ---------------------------------------------------------- grouped launch
