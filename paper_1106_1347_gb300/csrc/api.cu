@@ -1,5 +1,6 @@
 // libmm C ABI: argument checking, status reporting, kernel timing and dispatch
 // to the per-method launchers.  See include/mm.h for the contract.
+#include <atomic>
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -17,6 +18,19 @@
 static __device__ int g_device_status;
 
 namespace mm {
+
+int sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
 
 static thread_local std::string t_err;
 

@@ -22,6 +22,8 @@ int cuda_fail(cudaError_t e, const char *what);
 
 // Device status word the kernels raise when a bounded wait gives up.
 int *device_status_ptr();
+// Streaming multiprocessors of the current device (cached per device).
+int sm_count();
 
 constexpr int kStatusTimeoutTma = 1;
 constexpr int kStatusTimeoutMma = 2;

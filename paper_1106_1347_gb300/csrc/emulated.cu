@@ -260,24 +260,45 @@ __device__ __forceinline__ double int128_to_double(int64_t hi, uint64_t lo) {
     return neg ? -r : r;
 }
 
-// One 128 x 64 output tile (tm, tn) of one problem; called by every thread of
-// the CTA.  tmA / tmB are the problem's slice tensor maps (kernel parameters
-// or entries of a grouped launch's table in global memory).
-__device__ __forceinline__ void slice_tile(const CUtensorMap *tmA, const CUtensorMap *tmB, const EmuParams &p,
-                                           int tm, int tn, bool maps_in_global) {
+// Tile of CTA `id` in a tiles_m x tiles_n grid, in runs of 8 tile-rows so that
+// consecutive CTAs share B slices in L2.
+__device__ __forceinline__ void tile_of(int64_t id, int tiles_m, int tiles_n, int &tm, int &tn) {
+    const int64_t per_group = 8 * (int64_t)tiles_n;
+    const int64_t group = id / per_group, first_m = group * 8;
+    const int gsize = (int)min((int64_t)tiles_m - first_m, (int64_t)8);
+    tm = (int)(first_m + (id % per_group) % gsize);
+    tn = (int)((id % per_group) / gsize);
+}
+
+// One output tile of one problem: its slice tensor maps (kernel parameters or
+// entries of a grouped launch's table in global memory), parameters and place.
+struct TileJob {
+    const CUtensorMap *tmA, *tmB;
+    EmuParams p;
+    int tm, tn;
+};
+
+// Persistent slice product: CTA b takes tiles b, b + gridDim.x, ... of the
+// launch (Tiles::get resolves one).  The TMA warp, the MMA warp and the
+// epilogue warps walk the same tile sequence; stage and accumulator barrier
+// phases run on across tiles, so the loads of the next tile start while the
+// last chunk of the current one is in the tensor pipe, and its MMAs start as
+// soon as the epilogue has read the accumulators out -- the final rounding and
+// the stores of C overlap them.  `c` holds the launch-wide constants (slice
+// count, stages, chunk, TMEM columns).
+template <class Tiles>
+__device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, const EmuParams &c,
+                                            bool maps_in_global) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bars[2 * 8 + 3];
     __shared__ uint32_t tmem_slot;
+    if ((int64_t)blockIdx.x >= total) return;  // whole CTA, before any barrier
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int s = p.s, S = p.stages;
+    const int s = c.s, S = c.stages, CB = c.chunk_blocks;
     const uint32_t a_bytes = (uint32_t)s * BM * BKE * 2, b_bytes = (uint32_t)s * BN * BKE * 2;
     const uint32_t stage_bytes = a_bytes + b_bytes;
     uint64_t *full = bars, *empty = bars + 8, *acc_full = bars + 16, *acc_empty = bars + 17, *mma_done = bars + 18;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BN;
-    const int nkb = (int)((p.P + BKE - 1) / BKE);
-    const int nchunks = (nkb + p.chunk_blocks - 1) / p.chunk_blocks;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
@@ -290,7 +311,7 @@ __device__ __forceinline__ void slice_tile(const CUtensorMap *tmA, const CUtenso
         mmdev::fence_mbar_init();
     }
     if (warp == 1) {
-        mmdev::tmem_alloc(&tmem_slot, (uint32_t)p.tmem_cols);
+        mmdev::tmem_alloc(&tmem_slot, (uint32_t)c.tmem_cols);
         mmdev::tmem_relinquish();
     }
     mmdev::tc_fence_before();
@@ -300,28 +321,35 @@ __device__ __forceinline__ void slice_tile(const CUtensorMap *tmA, const CUtenso
 
     if (warp == 0) {
         if (lane == 0) {
-            if (maps_in_global) {  // the grouped table is rewritten in place between launches
-                mmdev::tmap_acquire(tmA);
-                mmdev::tmap_acquire(tmB);
-            }
-            mmdev::prefetch_tmap(tmA);
-            mmdev::prefetch_tmap(tmB);
-            int issued = 0;
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int st = kb % S, use = kb / S;
-                if (use > 0 && !mmdev::mbar_wait(&empty[st], (uint32_t)((use - 1) & 1))) {
-                    raise_status(p.status, mm::kStatusTimeoutTma);
-                    break;
+            uint32_t it = 0;  // K-blocks loaded so far, over all tiles of this CTA
+            bool ok = true;
+            for (int64_t id = blockIdx.x; id < total && ok; id += gridDim.x) {
+                TileJob j;
+                tiles.get(id, j);
+                if (maps_in_global) {  // the grouped table is rewritten in place between launches
+                    mmdev::tmap_acquire(j.tmA);
+                    mmdev::tmap_acquire(j.tmB);
                 }
-                uint8_t *sa = smem + (size_t)st * stage_bytes;
-                mmdev::mbar_arrive_expect_tx(&full[st], stage_bytes);
-                mmdev::tma_load_3d(sa, tmA, &full[st], kb * BKE, (int32_t)m0, 0);
-                mmdev::tma_load_3d(sa + a_bytes, tmB, &full[st], kb * BKE, (int32_t)n0, 0);
-                issued = kb + 1;
+                mmdev::prefetch_tmap(j.tmA);
+                mmdev::prefetch_tmap(j.tmB);
+                const int nkb = (int)((j.p.P + BKE - 1) / BKE);
+                const int32_t m0 = j.tm * BM, n0 = j.tn * BN;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const uint32_t st = it % S, use = it / S;
+                    if (use > 0 && !mmdev::mbar_wait(&empty[st], (use - 1) & 1u)) {
+                        raise_status(c.status, mm::kStatusTimeoutTma);
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *sa = smem + (size_t)st * stage_bytes;
+                    mmdev::mbar_arrive_expect_tx(&full[st], stage_bytes);
+                    mmdev::tma_load_3d(sa, j.tmA, &full[st], kb * BKE, m0, 0);
+                    mmdev::tma_load_3d(sa + a_bytes, j.tmB, &full[st], kb * BKE, n0, 0);
+                }
             }
             // Wait (bounded) for the last load into each stage, so no copy is in flight at exit.
-            for (int kb = max(0, issued - S); kb < issued; ++kb)
-                (void)mmdev::mbar_wait(&full[kb % S], (uint32_t)((kb / S) & 1));
+            for (uint32_t k = it > (uint32_t)S ? it - S : 0u; k < it; ++k)
+                (void)mmdev::mbar_wait(&full[k % S], (k / S) & 1u);
         }
     } else if (warp == 1) {
         // The whole warp runs the issue loop; each MMA and commit is issued by one
@@ -329,103 +357,128 @@ __device__ __forceinline__ void slice_tile(const CUtensorMap *tmA, const CUtenso
         // compile-time offsets (the start-address field cannot carry: shared
         // addresses stay below 2^18).
         const uint32_t idesc = mmdev::idesc_bf16_f32(BM, BN);
+        uint32_t it = 0, ev = 0;  // K-blocks consumed and chunks handed to the epilogue, over all tiles
         bool ok = true;
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int st = kb % S, use = kb / S;
-            const int kin = kb % p.chunk_blocks, chunk = kb / p.chunk_blocks;
-            if (kin == 0 && chunk > 0) {
-                ok = __all_sync(0xffffffffu, mmdev::mbar_wait(acc_empty, (uint32_t)((chunk - 1) & 1)));
+        for (int64_t id = blockIdx.x; id < total && ok; id += gridDim.x) {
+            TileJob j;
+            tiles.get(id, j);
+            const int nkb = (int)((j.p.P + BKE - 1) / BKE);
+            int kin = 0;  // K-block within the current exact chunk
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+                const uint32_t st = it % S, use = it / S;
+                if (kin == 0 && ev > 0) {  // the accumulators must have been read out
+                    ok = __all_sync(0xffffffffu, mmdev::mbar_wait(acc_empty, (ev - 1) & 1u));
+                    if (!ok) break;
+                    mmdev::tc_fence_after();
+                }
+                ok = __all_sync(0xffffffffu, mmdev::mbar_wait(&full[st], use & 1u));
                 if (!ok) break;
                 mmdev::tc_fence_after();
-            }
-            ok = __all_sync(0xffffffffu, mmdev::mbar_wait(&full[st], (uint32_t)(use & 1)));
-            if (!ok) break;
-            mmdev::tc_fence_after();
-            const uint32_t a_base = mmdev::smem_u32(smem + (size_t)st * stage_bytes);
-            const uint64_t da = mmdev::smem_desc_sw64(a_base), db = mmdev::smem_desc_sw64(a_base + a_bytes);
-            const uint32_t first = kin == 0 ? 0u : 1u;
+                const uint32_t a_base = mmdev::smem_u32(smem + (size_t)st * stage_bytes);
+                const uint64_t da = mmdev::smem_desc_sw64(a_base), db = mmdev::smem_desc_sw64(a_base + a_bytes);
+                const uint32_t first = kin == 0 ? 0u : 1u;
 #pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                if (d < s) {
+                for (int d = 0; d < 8; ++d) {
+                    if (d < s) {
 #pragma unroll
-                    for (int sg = 0; sg <= d; ++sg) {
+                        for (int sg = 0; sg <= d; ++sg) {
 #pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
-                            const uint64_t ad = da + (uint64_t)((sg * (BM * BKE * 2) + kk * 32) >> 4);
-                            const uint64_t bd = db + (uint64_t)(((d - sg) * (BN * BKE * 2) + kk * 32) >> 4);
-                            mmdev::mma_bf16_elect(tmem + (uint32_t)(d * BN), ad, bd, idesc,
-                                                  (sg == 0 && kk == 0) ? first : 1u);
+                            for (int kk = 0; kk < 2; ++kk) {
+                                const uint64_t ad = da + (uint64_t)((sg * (BM * BKE * 2) + kk * 32) >> 4);
+                                const uint64_t bd = db + (uint64_t)(((d - sg) * (BN * BKE * 2) + kk * 32) >> 4);
+                                mmdev::mma_bf16_elect(tmem + (uint32_t)(d * BN), ad, bd, idesc,
+                                                      (sg == 0 && kk == 0) ? first : 1u);
+                            }
                         }
                     }
                 }
+                mmdev::mma_commit_elect(&empty[st]);
+                if (++kin == CB || kb == nkb - 1) {
+                    mmdev::mma_commit_elect(acc_full);
+                    ++ev;
+                    kin = 0;
+                }
             }
-            mmdev::mma_commit_elect(&empty[st]);
-            if (kin == p.chunk_blocks - 1 || kb == nkb - 1) mmdev::mma_commit_elect(acc_full);
         }
-        if (!ok && lane == 0) raise_status(p.status, mm::kStatusTimeoutMma);
+        if (!ok && lane == 0) raise_status(c.status, mm::kStatusTimeoutMma);
         // Every MMA issued above has completed once mma_done flips.
         mmdev::mma_commit_elect(mma_done);
         (void)mmdev::mbar_wait(mma_done, 0);
     } else {
         const int q = warp & 3, h = (warp - 2) >> 2;
-        const int64_t row = m0 + 32 * q + lane;
-        int64_t whi[32], wlo[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) whi[j] = wlo[j] = 0;
         const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h);
+        uint32_t ev = 0;
         bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            if (!mmdev::mbar_wait(acc_full, (uint32_t)(c & 1))) {
-                raise_status(p.status, mm::kStatusTimeoutEpi);
-                ok = false;
-                break;
+        const int hsplit = c.hsplit;
+        for (int64_t id = blockIdx.x; id < total && ok; id += gridDim.x) {
+            int nchunks;
+            {
+                TileJob j;
+                tiles.get(id, j);
+                nchunks = ((int)((j.p.P + BKE - 1) / BKE) + CB - 1) / CB;
             }
-            mmdev::tc_fence_after();
-            for (int d = 0; d < s; ++d) {
-                uint32_t v[32];
-                mmdev::tmem_ld_32x32b_x32(tbase + (uint32_t)(d * BN), v);
-                mmdev::tmem_wait_ld();
-                if (d < p.hsplit) {
-                    const int sh = kBeta * (p.hsplit - 1 - d);
+            int64_t whi[32], wlo[32];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) whi[j] += (int64_t)__float2int_rn(__uint_as_float(v[j])) << sh;
-                } else {
-                    const int sh = kBeta * (s - 1 - d);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) wlo[j] += (int64_t)__float2int_rn(__uint_as_float(v[j])) << sh;
+            for (int k = 0; k < 32; ++k) whi[k] = wlo[k] = 0;
+            for (int ch = 0; ch < nchunks; ++ch, ++ev) {
+                if (!mmdev::mbar_wait(acc_full, ev & 1u)) {
+                    raise_status(c.status, mm::kStatusTimeoutEpi);
+                    ok = false;
+                    break;
                 }
+                mmdev::tc_fence_after();
+                for (int d = 0; d < s; ++d) {
+                    uint32_t v[32];
+                    mmdev::tmem_ld_32x32b_x32(tbase + (uint32_t)(d * BN), v);
+                    mmdev::tmem_wait_ld();
+                    if (d < hsplit) {
+                        const int sh = kBeta * (hsplit - 1 - d);
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) whi[k] += (int64_t)__float2int_rn(__uint_as_float(v[k])) << sh;
+                    } else {
+                        const int sh = kBeta * (s - 1 - d);
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) wlo[k] += (int64_t)__float2int_rn(__uint_as_float(v[k])) << sh;
+                    }
+                }
+                mmdev::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mmdev::mbar_arrive(acc_empty);
             }
-            mmdev::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mmdev::mbar_arrive(acc_empty);
-        }
-        if (ok && row < p.N) {
-            const int e = p.ea[row];
-            const int sh2 = kBeta * (s - p.hsplit);
-            double *crow = p.C + row * p.ldc;
+            // The accumulators are free again: round and store while the next tile's MMAs
+            // run (the tile is resolved again so its parameters need no registers above).
+            TileJob j;
+            tiles.get(id, j);
+            const EmuParams &p = j.p;
+            const int64_t row = (int64_t)j.tm * BM + 32 * q + lane, n0 = (int64_t)j.tn * BN;
+            if (ok && row < p.N) {
+                const int e = p.ea[row];
+                const int sh2 = kBeta * (s - hsplit);
+                double *crow = p.C + row * p.ldc;
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-                double out[2];
+                for (int k = 0; k < 32; k += 2) {
+                    double out[2];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int64_t col = n0 + 32 * h + j + u;
-                    const int64_t wh = whi[j + u], wl = wlo[j + u];
-                    // W = wh * 2^sh2 + wl as a signed 128-bit integer.
-                    uint64_t lo = sh2 ? ((uint64_t)wh << sh2) : (uint64_t)wh;
-                    int64_t hi = sh2 ? (wh >> (64 - sh2)) : (wh >> 63);
-                    const uint64_t lo2 = lo + (uint64_t)wl;
-                    hi += (wl >> 63) + (lo2 < lo ? 1 : 0);
-                    lo = lo2;
-                    const int f = (col < p.M) ? p.fb[col] : 0;
-                    out[u] = ldexp(int128_to_double(hi, lo), e + f + 2 - kBeta * (s + 1));
-                }
-                const int64_t col = n0 + 32 * h + j;
-                double *dst = crow + col;
-                if (col + 1 < p.M && (((uintptr_t)dst & 15) == 0)) {
-                    *reinterpret_cast<double2 *>(dst) = make_double2(out[0], out[1]);
-                } else {
-                    if (col < p.M) dst[0] = out[0];
-                    if (col + 1 < p.M) dst[1] = out[1];
+                    for (int u = 0; u < 2; ++u) {
+                        const int64_t col = n0 + 32 * h + k + u;
+                        const int64_t wh = whi[k + u], wl = wlo[k + u];
+                        // W = wh * 2^sh2 + wl as a signed 128-bit integer.
+                        uint64_t lo = sh2 ? ((uint64_t)wh << sh2) : (uint64_t)wh;
+                        int64_t hi = sh2 ? (wh >> (64 - sh2)) : (wh >> 63);
+                        const uint64_t lo2 = lo + (uint64_t)wl;
+                        hi += (wl >> 63) + (lo2 < lo ? 1 : 0);
+                        lo = lo2;
+                        const int f = (col < p.M) ? p.fb[col] : 0;
+                        out[u] = ldexp(int128_to_double(hi, lo), e + f + 2 - kBeta * (s + 1));
+                    }
+                    const int64_t col = n0 + 32 * h + k;
+                    double *dst = crow + col;
+                    if (col + 1 < p.M && (((uintptr_t)dst & 15) == 0)) {
+                        *reinterpret_cast<double2 *>(dst) = make_double2(out[0], out[1]);
+                    } else {
+                        if (col < p.M) dst[0] = out[0];
+                        if (col + 1 < p.M) dst[1] = out[1];
+                    }
                 }
             }
         }
@@ -436,26 +489,26 @@ __device__ __forceinline__ void slice_tile(const CUtensorMap *tmA, const CUtenso
     if (warp == 1) {
         __syncwarp();
         mmdev::tc_fence_after();
-        mmdev::tmem_dealloc(tmem, (uint32_t)p.tmem_cols);
+        mmdev::tmem_dealloc(tmem, (uint32_t)c.tmem_cols);
     }
 }
 
-// Tile of CTA `id` in a tiles_m x tiles_n grid, in runs of 8 tile-rows so that
-// consecutive CTAs share B slices in L2.
-__device__ __forceinline__ void tile_of(int64_t id, int tiles_m, int tiles_n, int &tm, int &tn) {
-    const int64_t per_group = 8 * (int64_t)tiles_n;
-    const int64_t group = id / per_group, first_m = group * 8;
-    const int gsize = (int)min((int64_t)tiles_m - first_m, (int64_t)8);
-    tm = (int)(first_m + (id % per_group) % gsize);
-    tn = (int)((id % per_group) / gsize);
-}
+struct SingleTiles {
+    const CUtensorMap *tmA, *tmB;
+    const EmuParams *p;
+    __device__ __forceinline__ void get(int64_t id, TileJob &j) const {
+        j.tmA = tmA;
+        j.tmB = tmB;
+        j.p = *p;
+        tile_of(id, p->tiles_m, p->tiles_n, j.tm, j.tn);
+    }
+};
 
 __global__ void __launch_bounds__(kThreads, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const EmuParams p) {
-    int tm, tn;
-    tile_of(blockIdx.x, p.tiles_m, p.tiles_n, tm, tn);
-    slice_tile(&tmA, &tmB, p, tm, tn, false);
+    const SingleTiles tiles{&tmA, &tmB, &p};
+    slice_tiles(tiles, (int64_t)p.tiles_m * p.tiles_n, p, false);
 }
 
 // ------------------------------------------------------------ grouped launch
@@ -534,16 +587,27 @@ __global__ void __launch_bounds__(256) group_split_cols_kernel(const EmuProblem 
     split_cols_tile(p, local % nj, local / nj, sm);
 }
 
+struct GroupTiles {
+    const EmuProblem *tab;
+    const int64_t *begin;
+    int64_t count;
+    __device__ __forceinline__ void get(int64_t id, TileJob &j) const {
+        const int g = find_problem(begin, count, id);
+        const EmuProblem &e = tab[g];
+        j.tmA = &e.tmA;
+        j.tmB = &e.tmB;
+        j.p = e.prm;
+        tile_of(id - begin[g], j.p.tiles_m, j.p.tiles_n, j.tm, j.tn);
+    }
+};
+
 __global__ void __launch_bounds__(kThreads, 1) group_slice_gemm_kernel(const EmuProblem *tab, const int64_t *begin,
                                                                        const GroupHeader *hdr) {
-    const int64_t u = blockIdx.x;
-    if (u >= hdr->units[U_TILES]) return;
-    const int g = find_problem(begin, hdr->count, u);
-    const EmuProblem &e = tab[g];
-    const EmuParams prm = e.prm;
-    int tm, tn;
-    tile_of(u - begin[g], prm.tiles_m, prm.tiles_n, tm, tn);
-    slice_tile(&e.tmA, &e.tmB, prm, tm, tn, true);
+    const int64_t total = hdr->units[U_TILES];
+    if (total <= 0) return;
+    const GroupTiles tiles{tab, begin, hdr->count};
+    const EmuParams c = tab[0].prm;  // one slice count per launch: the constants are the same for every problem
+    slice_tiles(tiles, total, c, true);
 }
 
 cudaError_t slice_smem_attributes();
@@ -664,8 +728,9 @@ int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
     const cudaError_t attr_err = slice_smem_attributes();
     if (attr_err != cudaSuccess) return cuda_fail(attr_err, "mm_emulated: shared memory attribute");
     const int64_t tiles = (int64_t)prm.tiles_m * prm.tiles_n;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, sm_count());  // persistent: one CTA per SM
     return launch("emu_slice_gemm_tcgen05", st,
-                  [&] { slice_gemm_kernel<<<(unsigned)tiles, kThreads, smem, st>>>(tmA, tmB, prm); });
+                  [&] { slice_gemm_kernel<<<grid, kThreads, smem, st>>>(tmA, tmB, prm); });
 }
 
 }  // namespace mm
@@ -791,7 +856,8 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
     if (rc) return rc;
     if (gl.grid[U_TILES] > 0)
         rc = launch("emu_group_slice_gemm_tcgen05", st, [&] {
-            group_slice_gemm_kernel<<<(unsigned)gl.grid[U_TILES], kThreads, slice_smem_bytes(gl.s), st>>>(
+            group_slice_gemm_kernel<<<(unsigned)std::min<int64_t>(gl.grid[U_TILES], sm_count()), kThreads,
+                                      slice_smem_bytes(gl.s), st>>>(
                 (const EmuProblem *)gl.tab, gl.begin[U_TILES], (const GroupHeader *)gl.hdr);
         });
     return rc;

@@ -304,21 +304,10 @@ void strassen_winograd_products(Product (&pr)[7]) {
     pr[6] = Product{E1(T22), E6(T21, M_, T22, M_, T12, P_, T11), 1, {tgt(T21, 1, false)}};
 }
 
-int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 152;
-    }
-    return n;
-}
-
 int launch_level(const LevelArgs &a, bool single, cudaStream_t st) {
     if (a.m <= 0 || a.n <= 0) return MM_OK;
     // 64 x 64 tiles when they give at least four CTAs per SM, else 32 x 32.
-    const bool big = mm::ceil_div(a.m, 64) * mm::ceil_div(a.n, 64) >= 4 * sm_count();
+    const bool big = mm::ceil_div(a.m, 64) * mm::ceil_div(a.n, 64) >= 4 * mm::sm_count();
     const int tile = big ? 64 : 32;
     dim3 grid((unsigned)mm::ceil_div(a.m, tile), (unsigned)mm::ceil_div(a.n, tile));
     if (grid.y > 65535) return mm::fail(MM_ERR_UNSUPPORTED, "product too tall for one launch");
