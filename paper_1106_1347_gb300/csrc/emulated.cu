@@ -270,6 +270,32 @@ __device__ __forceinline__ void tile_of(int64_t id, int tiles_m, int tiles_n, in
     tn = (int)((id % per_group) / gsize);
 }
 
+// Accumulator d holds d + 1 slice pairs, so its exact length is
+// L_d = 2^12 / (BKE (d + 1)) K-blocks, a whole number r_d = floor(L_d / CB) of
+// chunks of CB = L_(s-1) K-blocks: at each chunk end only the accumulators
+// whose r_d chunks are complete are read out (plus all of them at the tile's
+// last chunk), which cuts the TMEM traffic of the drains by a third for 8
+// slices.  The countdowns live in one register, 4 bits per diagonal.
+__device__ __forceinline__ uint32_t drain_periods(int CB) {
+    uint32_t R = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) R |= (uint32_t)(max(1, (4096 / BKE / (d + 1)) / CB) - 1) << (4 * d);
+    return R;
+}
+// Diagonals due at this chunk end; advances the countdowns.
+__device__ __forceinline__ uint32_t drain_due(uint32_t &cnt, uint32_t R, bool last) {
+    uint32_t due = 0, nc = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const uint32_t v = (cnt >> (4 * d)) & 15u;
+        const bool z = last || v == 0;
+        due |= (uint32_t)z << d;
+        nc |= (z ? (R >> (4 * d)) & 15u : v - 1) << (4 * d);
+    }
+    cnt = nc;
+    return due;
+}
+
 // One output tile of one problem: its slice tensor maps (kernel parameters or
 // entries of a grouped launch's table in global memory), parameters and place.
 struct TileJob {
@@ -357,13 +383,15 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
         // compile-time offsets (the start-address field cannot carry: shared
         // addresses stay below 2^18).
         const uint32_t idesc = mmdev::idesc_bf16_f32(BM, BN);
+        const uint32_t R = drain_periods(CB);
         uint32_t it = 0, ev = 0;  // K-blocks consumed and chunks handed to the epilogue, over all tiles
         bool ok = true;
         for (int64_t id = blockIdx.x; id < total && ok; id += gridDim.x) {
             TileJob j;
             tiles.get(id, j);
             const int nkb = (int)((j.p.P + BKE - 1) / BKE);
-            int kin = 0;  // K-block within the current exact chunk
+            int kin = 0;                // K-block within the current exact chunk
+            uint32_t cnt = R, fresh = 0xffu;  // accumulators that start over at the next chunk
             for (int kb = 0; kb < nkb; ++kb, ++it) {
                 const uint32_t st = it % S, use = it / S;
                 if (kin == 0 && ev > 0) {  // the accumulators must have been read out
@@ -376,9 +404,9 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                 mmdev::tc_fence_after();
                 const uint32_t a_base = mmdev::smem_u32(smem + (size_t)st * stage_bytes);
                 const uint64_t da = mmdev::smem_desc_sw64(a_base), db = mmdev::smem_desc_sw64(a_base + a_bytes);
-                const uint32_t first = kin == 0 ? 0u : 1u;
 #pragma unroll
                 for (int d = 0; d < 8; ++d) {
+                    const uint32_t first = (kin == 0 && ((fresh >> d) & 1u)) ? 0u : 1u;
                     if (d < s) {
 #pragma unroll
                         for (int sg = 0; sg <= d; ++sg) {
@@ -395,6 +423,7 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                 mmdev::mma_commit_elect(&empty[st]);
                 if (++kin == CB || kb == nkb - 1) {
                     mmdev::mma_commit_elect(acc_full);
+                    fresh = drain_due(cnt, R, kb == nkb - 1);
                     ++ev;
                     kin = 0;
                 }
@@ -410,6 +439,7 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
         uint32_t ev = 0;
         bool ok = true;
         const int hsplit = c.hsplit;
+        const uint32_t R = drain_periods(CB);
         for (int64_t id = blockIdx.x; id < total && ok; id += gridDim.x) {
             int nchunks;
             {
@@ -420,6 +450,7 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
             int64_t whi[32], wlo[32];
 #pragma unroll
             for (int k = 0; k < 32; ++k) whi[k] = wlo[k] = 0;
+            uint32_t cnt = R;
             for (int ch = 0; ch < nchunks; ++ch, ++ev) {
                 if (!mmdev::mbar_wait(acc_full, ev & 1u)) {
                     raise_status(c.status, mm::kStatusTimeoutEpi);
@@ -427,7 +458,9 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                     break;
                 }
                 mmdev::tc_fence_after();
+                const uint32_t due = drain_due(cnt, R, ch == nchunks - 1);
                 for (int d = 0; d < s; ++d) {
+                    if (!((due >> d) & 1u)) continue;
                     uint32_t v[32];
                     mmdev::tmem_ld_32x32b_x32(tbase + (uint32_t)(d * BN), v);
                     mmdev::tmem_wait_ld();
