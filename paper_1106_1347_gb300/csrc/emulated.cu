@@ -18,17 +18,18 @@
 //                  (K-major, coalesced).
 //   col_max / split_cols -- per-column maxima of B, then digits transposed
 //                  through shared memory into slices [s][M][P] (K-major).
-//   slice_gemm  -- 128x64 output tile per CTA.  Warp 0 issues TMA loads of all
-//                  s slices of a 32-wide K-block of A and B (3-D boxes,
-//                  64-byte swizzle) into a ring of shared-memory stages; warp 1
-//                  (one elected lane, warp-uniform operands) issues
-//                  tcgen05.mma kind::f16 for every pair with
-//                  sigma + tau = d into TMEM accumulator d (s x 64 FP32
-//                  columns); eight epilogue warps drain the accumulators every
-//                  K-chunk Kc, chosen so every partial sum is an integer below
-//                  2^24 and FP32 accumulation is exact, into two int64
-//                  registers per output, and at the end round the exact
-//                  128-bit integer once to double and apply 2^(e_i + f_j ...).
+//   slice_gemm  -- persistent, one CTA per SM looping over 128x64 output
+//                  tiles.  Warp 0 issues TMA loads of all s slices of a
+//                  32-wide K-block of A and B (3-D boxes, 64-byte swizzle)
+//                  into a ring of shared-memory stages; warp 1 (one elected
+//                  lane, warp-uniform operands) issues tcgen05.mma kind::f16
+//                  for every pair with sigma + tau = d into TMEM accumulator d
+//                  (s x 64 FP32 columns); eight epilogue warps read each
+//                  accumulator out before its partial sums could leave the
+//                  integers FP32 holds exactly (|x| <= 2^24), into two int64
+//                  registers per output, and at the tile's end round the
+//                  exact 128-bit integer once to double and apply
+//                  2^(e_i + f_j ...) while the next tile's MMAs run.
 // Every mbarrier wait is bounded; on timeout the kernel raises the device
 // status word, waits (bounded) for its own copies and MMAs, frees TMEM and exits.
 #include <cuda_bf16.h>
