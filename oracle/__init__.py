@@ -53,6 +53,8 @@ def _load():
             lib.oracle_winograd_terms.argtypes = [i64, i64, i64, dp, i64, dp, i64, dp, dp]
             lib.oracle_winograd_scaled.argtypes = gemm
             lib.oracle_winograd_scaled.restype = ctypes.c_int
+            lib.oracle_winograd_rowcol_scaled.argtypes = gemm + [ip, ip]
+            lib.oracle_winograd_rowcol_scaled.restype = None
             lib.oracle_brent_lambda.argtypes = [ctypes.c_double, ctypes.c_double]
             lib.oracle_brent_lambda.restype = ctypes.c_int
             lib.oracle_strassen_paper_rule.argtypes = [i64, i64, i64, ctypes.POINTER(ctypes.c_int),
@@ -140,6 +142,21 @@ def winograd_scaled(a, b):
     """Returns (C, lambda)."""
     c, lam = _gemm("oracle_winograd_scaled", a, b)
     return c, int(lam)
+
+
+def winograd_rowcol_scaled(a, b):
+    """Returns (C, e, f): Winograd's form with each row of A scaled by 2^-e_i and
+    each column of B by 2^-f_k, the result scaled back by 2^(e_i + f_k)."""
+    a, b = _f64(a), _f64(b)
+    n, p = a.shape
+    m = b.shape[1]
+    c = np.zeros((n, m))
+    e = np.zeros(max(n, 1), dtype=np.int32)
+    f = np.zeros(max(m, 1), dtype=np.int32)
+    ipt = ctypes.POINTER(ctypes.c_int32)
+    _load().oracle_winograd_rowcol_scaled(n, p, m, _ptr(a), _ld(a), _ptr(b), _ld(b), _ptr(c), _ld(c),
+                                          e.ctypes.data_as(ipt), f.ctypes.data_as(ipt))
+    return c, e[:n], f[:m]
 
 
 def strassen_paper_rule(n: int, p: int, m: int):

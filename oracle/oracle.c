@@ -25,6 +25,10 @@
  *    Y = m 2^k; sums of several terms are evaluated left to right.
  *  - Kahan: the paper's update is used as printed and the final err is not
  *    folded back into the sum.
+ *  - Per-row/column scaled Winograd (not in the paper; its scaling taken from
+ *    one pair of norms to every row of A and column of B): e_i and f_k are the
+ *    frexp exponents of the row and column maxima, so every scaled row and
+ *    column has its largest magnitude in [1/2, 1).
  */
 #include <math.h>
 #include <stdint.h>
@@ -195,6 +199,53 @@ int oracle_winograd_scaled(int64_t N, int64_t P, int64_t M, const double *A, int
     free(As);
     free(Bs);
     return lam;
+}
+
+/* Per-row/column power-of-two scaling of Winograd's form: the exact scaling of
+ * section "WinogradScaled" (MultiplyWithScalar by 2^lambda and 2^-lambda, Eq.
+ * for lambda) taken from one global pair of norms down to each row of A and
+ * each column of B.  e_i is the frexp exponent of max_j |A_ij| and f_k that of
+ * max_j |B_jk| (0 for a zero row or column), so every row of A' = 2^-e_i A_i,:
+ * and every column of B' = 2^-f_k B_:,k has its largest entry in [1/2, 1) and
+ * each paired sum (A'_i,2j-1 + B'_2j,k) adds terms of like size.  Then
+ * C_ik = 2^(e_i + f_k) C'_ik with C' = WinogradOriginal(A', B').  All scalings
+ * are by ldexp, exact unless a scaled entry leaves the normal range.
+ * e (N entries) and f (M entries) receive the exponents when not NULL. */
+void oracle_winograd_rowcol_scaled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                                   int64_t ldb, double *C, int64_t ldc, int *e, int *f) {
+    int *ea = (int *)malloc(sizeof(int) * (size_t)imax(N, 1));
+    int *fb = (int *)malloc(sizeof(int) * (size_t)imax(M, 1));
+    double *As = (double *)malloc(sizeof(double) * (size_t)imax(N * P, 1));
+    double *Bs = (double *)malloc(sizeof(double) * (size_t)imax(P * M, 1));
+    double *Cs = (double *)malloc(sizeof(double) * (size_t)imax(N * M, 1));
+    for (int64_t i = 0; i < N; ++i) {
+        double mx = 0.0;
+        for (int64_t j = 0; j < P; ++j) mx = fmax(mx, fabs(AT(A, lda, i, j)));
+        int ex = 0;
+        if (mx > 0.0) (void)frexp(mx, &ex);
+        ea[i] = ex;
+        for (int64_t j = 0; j < P; ++j) AT(As, P, i, j) = ldexp(AT(A, lda, i, j), -ex);
+    }
+    for (int64_t k = 0; k < M; ++k) {
+        double mx = 0.0;
+        for (int64_t j = 0; j < P; ++j) mx = fmax(mx, fabs(AT(B, ldb, j, k)));
+        int ex = 0;
+        if (mx > 0.0) (void)frexp(mx, &ex);
+        fb[k] = ex;
+        for (int64_t j = 0; j < P; ++j) AT(Bs, M, j, k) = ldexp(AT(B, ldb, j, k), -ex);
+    }
+    oracle_winograd_original(N, P, M, As, P, Bs, M, Cs, M);
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t k = 0; k < M; ++k) AT(C, ldc, i, k) = ldexp(AT(Cs, M, i, k), ea[i] + fb[k]);
+    if (e)
+        for (int64_t i = 0; i < N; ++i) e[i] = ea[i];
+    if (f)
+        for (int64_t k = 0; k < M; ++k) f[k] = fb[k];
+    free(ea);
+    free(fb);
+    free(As);
+    free(Bs);
+    free(Cs);
 }
 
 /* --------------------------------------------------------------- Strassen */

@@ -16,8 +16,8 @@ import synthetic as S
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_pins.json")))
 U = 2.0 ** -53
 
-GEMMS = ["naiv_standard", "naiv_kahan", "winograd_original", "winograd_scaled", "strassen_naiv",
-         "strassen_winograd", "dot2_product"]
+GEMMS = ["naiv_standard", "naiv_kahan", "winograd_original", "winograd_scaled", "winograd_rowcol_scaled",
+         "strassen_naiv", "strassen_winograd", "dot2_product"]
 
 
 def run(orc, name, a, b, **kw):
@@ -188,8 +188,8 @@ def test_kahan_error_bound_and_gain(orc):
     assert abs(Fraction(float(k)) - exact) <= U * exact  # within half an ulp of 1
 
 
-@pytest.mark.parametrize("name", ["naiv_standard", "winograd_original", "winograd_scaled", "strassen_naiv",
-                                  "strassen_winograd"])
+@pytest.mark.parametrize("name", ["naiv_standard", "winograd_original", "winograd_scaled", "winograd_rowcol_scaled",
+                                  "strassen_naiv", "strassen_winograd"])
 def test_real_inputs_near_exact(orc, name):
     """Random reals: normwise error against the exact product stays far below 1e-14."""
     a = S.uniform(12, 29, 51)
@@ -304,3 +304,64 @@ def test_split_product_error_tiers(orc, beta, s, tol):
     b = S.loguniform(40, 20, 122)
     truth = orc.dot2_product(a, b)
     assert orc.rel_inf_error(orc.split_product(a, b, beta, s), truth, a, b) <= tol
+
+
+# ------------------------------------------- per-row/column scaled Winograd
+
+def test_rowcol_exponents_follow_the_definition(orc):
+    """e_i: 2^(e_i - 1) <= max_j |A_ij| < 2^e_i, 0 for a zero row; likewise f_k
+    over the columns of B."""
+    a = S.badly_scaled(24, S.stream_seed(2, 10), S.stream_seed(2, 11))[0][:, :17].copy()
+    b = S.badly_scaled(24, S.stream_seed(2, 12), S.stream_seed(2, 13))[1][:17, :].copy()
+    a[5, :] = 0.0
+    b[:, 7] = 0.0
+    _, e, f = orc.winograd_rowcol_scaled(a, b)
+    for mx, ex in list(zip(np.abs(a).max(axis=1), e)) + list(zip(np.abs(b).max(axis=0), f)):
+        if mx == 0.0:
+            assert ex == 0
+        else:
+            assert np.ldexp(1.0, int(ex) - 1) <= mx < np.ldexp(1.0, int(ex))
+
+
+def test_rowcol_power_of_two_invariance(orc):
+    """Scaling row i of A by 2^r_i and column k of B by 2^c_k (exact) leaves A'
+    and B' unchanged, so the result is the old one times 2^(r_i + c_k), bit for
+    bit; a scale-back with a wrong exponent fails this."""
+    a = S.uniform(13, 21, 91)
+    b = S.uniform(21, 9, 92)
+    rng = np.random.default_rng(11)
+    r = rng.integers(-40, 41, size=13)
+    c = rng.integers(-40, 41, size=9)
+    c0 = orc.winograd_rowcol_scaled(a, b)[0]
+    c1 = orc.winograd_rowcol_scaled(np.ldexp(a, r[:, None]), np.ldexp(b, c[None, :]))[0]
+    assert np.array_equal(c1, np.ldexp(c0, r[:, None] + c[None, :]))
+
+
+def test_rowcol_reduces_to_original_when_balanced(orc):
+    """Every row maximum of A and column maximum of B in [1/2, 1): all exponents
+    are 0 and the method is WinogradOriginal itself."""
+    a = S.uniform(10, 15, 93) * 0.7
+    b = S.uniform(15, 8, 94) * 0.7
+    a[:, 3] = 0.75
+    b[4, :] = -0.75
+    c, e, f = orc.winograd_rowcol_scaled(a, b)
+    assert not e.any() and not f.any()
+    assert np.array_equal(c, orc.winograd_original(a, b))
+
+
+def test_rowcol_elementwise_bound_on_badly_scaled(orc):
+    """After scaling, |A'|, |B'| < 1: each paired factor is below 2 in magnitude,
+    each product below 4, the paired sum below 4 gamma and y', z' below gamma,
+    so a standard rounding-error count gives
+    |C' - T'|_ik <= 8 gamma (gamma + 5) u (gamma = P/2, u = 2^-53), and the
+    exact scale-back makes it |C - T|_ik <= 8 gamma (gamma + 5) u 2^(e_i + f_k)
+    -- an elementwise form of the bound of section 'WinogradScaled'.  Plain
+    Winograd breaks it on rows times 10^u and columns times 10^v."""
+    n = 64
+    a, b = S.badly_scaled(n, S.stream_seed(2, 14), S.stream_seed(2, 15))
+    truth = orc.dot2_product(a, b)
+    c, e, f = orc.winograd_rowcol_scaled(a, b)
+    gamma = n // 2
+    bound = 8 * gamma * (gamma + 5) * U * np.ldexp(1.0, e[:, None] + f[None, :])
+    assert (np.abs(c - truth) <= bound).all()
+    assert not (np.abs(orc.winograd_original(a, b) - truth) <= bound).all()
