@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--serve-baseline-requests", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the slice sweep, the 4096x16384x4096 shape and the badly scaled errors")
     ap.add_argument("--variants-n", type=int, default=4096, help="size of the per-method FP64 timings (0: skip)")
     ap.add_argument("--fp64-only", action="store_true", help="only the per-method FP64 timings (profiling runs)")
     args = ap.parse_args()
@@ -214,19 +216,112 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def sampled_error(c_dev, a, b, norm_a, norm_b, rows):
+def sampled_error(c_dev, a, b, norm_a, norm_b, rows, truth=None):
     """max over sampled rows i of sum_j |C_ij - T_ij| / (||A|| ||B||), T the
     oracle's Dot2 product on those rows (a sample of the inf-norm's rows)."""
     import numpy as np
 
     import oracle
 
-    truth = oracle.dot2_product(a[rows], b)
+    if truth is None:
+        truth = oracle.dot2_product(a[rows], b)
     got = c_dev[rows].cpu().numpy() if hasattr(c_dev, "cpu") else c_dev[rows]
     return float(np.abs(got - truth).sum(axis=1).max() / (norm_a * norm_b))
 
 
-def serve_bench(dev, requests, budget_gb, baseline_requests):
+def timed(fn, reps):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def slice_sweep(ta, tb, a, b, norm_a, norm_b, rows, truth):
+    """The emulated product at the bench shape for every BF16 slice count 3..8:
+    FP64-equivalent TFLOP/s (2NPM / t) and the sampled normwise error."""
+    import torch
+
+    import paper_1106_1347_gb300 as mm
+
+    n, p, m = a.shape[0], a.shape[1], b.shape[1]
+    c = torch.empty((n, m), dtype=torch.float64, device=ta.device)
+    out = {}
+    for s in range(3, 9):
+        ms = timed(lambda: mm.emulated(ta, tb, nslices=s, out=c), 3)
+        out[str(s)] = {"ms": ms, "tflops": 2.0 * n * p * m / (ms * 1e-3) / 1e12,
+                       "slice_pairs": s * (s + 1) // 2,
+                       "rel_inf_err_sampled": sampled_error(c, a, b, norm_a, norm_b, rows, truth)}
+    return out
+
+
+def tall_inner_shape(dev):
+    """N = M = 4096, P = 16384, log-uniform entries, 8 slices."""
+    import numpy as np
+    import torch
+
+    import paper_1106_1347_gb300 as mm
+    import synthetic as S
+
+    n, p, m = 4096, 16384, 4096
+    a = S.loguniform(n, p, S.stream_seed(3, 2))
+    b = S.loguniform(p, m, S.stream_seed(3, 3))
+    ta, tb = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+    c = torch.empty((n, m), dtype=torch.float64, device=dev)
+    ms = timed(lambda: mm.emulated(ta, tb, nslices=8, out=c), 5)
+    norm_a, norm_b = float(mm.norm_inf(ta).item()), float(mm.norm_inf(tb).item())
+    rows = np.arange(0, n, n // 4)[:4]
+    return {"N": n, "P": p, "M": m, "slices": 8, "ms": ms, "tflops": 2.0 * n * p * m / (ms * 1e-3) / 1e12,
+            "slice_gemm_tflops_bf16": 36 * 2.0 * n * p * m / (ms * 1e-3) / 1e12,
+            "rel_inf_err_sampled": sampled_error(c, a, b, norm_a, norm_b, rows)}
+
+
+def badly_scaled_errors(dev, n=2048, nrows=64):
+    """Rows of A times 10^u, columns of B times 10^v (u, v uniform [-6, 6]):
+    normwise error ||C - T||/(||A|| ||B||) and componentwise
+    max |C - T|_ij / (|A| |B|)_ij of every method on sampled rows, T the oracle's
+    Dot2 product."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1106_1347_gb300 as mm
+    import synthetic as S
+
+    a, b = S.badly_scaled(n, S.stream_seed(2, 0), S.stream_seed(2, 1))
+    ta, tb = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+    rows = np.linspace(0, n - 1, nrows).astype(np.int64)
+    truth = oracle.dot2_product(a[rows], b)
+    absab = np.abs(a[rows]) @ np.abs(b)
+    na, nb = float(np.abs(a).sum(axis=1).max()), float(np.abs(b).sum(axis=1).max())
+    runs = {
+        "naive": lambda: mm.naive(ta, tb),
+        "kahan": lambda: mm.kahan(ta, tb),
+        "winograd": lambda: mm.winograd(ta, tb),
+        "winograd_scaled": lambda: mm.winograd_scaled(ta, tb),
+        "strassen": lambda: mm.strassen(ta, tb),
+        "strassen_winograd": lambda: mm.strassen_winograd(ta, tb),
+        "emulated_8_slices": lambda: mm.emulated(ta, tb, nslices=8),
+    }
+    if hasattr(mm, "winograd_rowcol_scaled"):
+        runs["winograd_rowcol_scaled"] = lambda: mm.winograd_rowcol_scaled(ta, tb)
+    out = {}
+    for name, fn in runs.items():
+        got = fn()[rows].cpu().numpy()
+        diff = np.abs(got - truth)
+        out[name] = {"normwise": float(diff.sum(axis=1).max() / (na * nb)),
+                     "componentwise": float((diff / np.maximum(absab, np.finfo(float).tiny)).max())}
+    return {"n": n, "rows_sampled": nrows, "scaling": "rows of A x 10^u, columns of B x 10^v, u, v in [-6, 6]",
+            "reference": "oracle Dot2 product", "errors": out}
+
+
+def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000):
     """The serving stream: `requests` products with N, P, M log-uniform on
     [32, 4096], entries uniform [-1, 1], tiers 1e-14 / 1e-6 half and half.
     1) saturated: every request submitted at t = 0 -> throughput;
@@ -253,6 +348,24 @@ def serve_bench(dev, requests, budget_gb, baseline_requests):
     with serving.Server(budget, method=serving.METHOD_FP64) as srv:
         st_b, _, rc_b = serving.replay(srv, base_trace, a_pool, b_pool, c_pool)
     flop_all = st["flops"]
+    # Latency against load: shorter Poisson streams at other fractions of the saturated rate.
+    sweep = {}
+    for frac in (0.3, 0.5, 1.0):
+        tr = S.serving_trace(sweep_requests, S.stream_seed(4, 3), mean_gap_s=1.0 / (frac * rate))
+        with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True) as srv:
+            st_f, _, rc_f = serving.replay(srv, tr, a_pool, b_pool, c_pool)
+        sweep[str(frac)] = {"arrival_rate_rps": frac * rate, "p50_ms": st_f["p50_ms"], "p99_ms": st_f["p99_ms"],
+                            "completed": st_f["completed"], "status": rc_f}
+    # A 1 GiB budget, where admission binds: the largest requests (about 1.5 GB with
+    # their split workspace) can never fit and are rejected, the rest queue for memory.
+    small = 1 << 30
+    tr = S.serving_trace(sweep_requests, S.stream_seed(4, 4), mean_gap_s=0.0)
+    with serving.Server(small, max_batch=256, nstreams=4, use_graphs=True) as srv:
+        st_s, comps_s, rc_s = serving.replay(srv, tr, a_pool, b_pool, c_pool)
+    tight = {"budget_gb": 1.0, "requests": len(tr), "completed": st_s["completed"], "rejected": st_s["rejected"],
+             "requests_per_s": st_s["completed"] / max(st_s["busy_s"], 1e-9),
+             "p50_ms": st_s["p50_ms"], "p99_ms": st_s["p99_ms"], "peak_arena_gb": st_s["peak_arena_bytes"] / 2 ** 30,
+             "status": rc_s}
     return {
         "requests": requests, "budget_gb": budget_gb, "dims": "N, P, M log-uniform [32, 4096]",
         "tiers": "1e-14 (8 slices) / 1e-6 (5 slices), 50/50",
@@ -266,6 +379,7 @@ def serve_bench(dev, requests, budget_gb, baseline_requests):
         "fp64_one_at_a_time": {"requests": len(base_trace), "arrival_rate_rps": 0.7 * rate,
                                "p50_ms": st_b["p50_ms"], "p99_ms": st_b["p99_ms"], "mean_ms": st_b["mean_ms"],
                                "tflops": st_b["flops"] / max(st_b["busy_s"], 1e-9) / 1e12, "status": rc_b},
+        "load_sweep": sweep, "budget_1gb_saturated": tight,
         "latency": "submit -> result in pinned host memory (H2D copies, product, D2H copy)",
     }
 
@@ -287,13 +401,14 @@ def variants_bench(dev, n):
     # FP64-pipe operations (an FMA, DADD or DMUL each, or 1/256 of an m8n8k4 MMA)
     # issued per reported flop (2n^3 per product): naive 1 FMA per 2 flop; Kahan
     # 1 DMUL + 4 DADD per k; Winograd 2 DADD + 1 FMA per pair of k.
-    pipe = {"naive": 0.5, "kahan": 2.5, "winograd": 0.75, "winograd_scaled": 0.75}
+    pipe = {"naive": 0.5, "kahan": 2.5, "winograd": 0.75, "winograd_scaled": 0.75, "winograd_rowcol_scaled": 0.75}
     peak_ops = FP64_PEAK_TFLOPS / 2.0  # FP64-pipe ops per second (1e12)
     runs = {
         "naive": lambda: mm.naive(a, b),
         "kahan": lambda: mm.kahan(a, b),
         "winograd": lambda: mm.winograd(a, b),
         "winograd_scaled": lambda: mm.winograd_scaled(a, b),
+        "winograd_rowcol_scaled": lambda: mm.winograd_rowcol_scaled(a, b),
         "strassen": lambda: mm.strassen(a, b),
         "strassen_winograd": lambda: mm.strassen_winograd(a, b),
     }
@@ -387,7 +502,10 @@ def run_ours(args):
         norm_a = float(mm.norm_inf(ta).item())
         norm_b = float(mm.norm_inf(tb).item())
         rows = np.arange(0, N, N // 4)[:4]
-        err_emu = sampled_error(c, a, b, norm_a, norm_b, rows)
+        import oracle
+
+        truth = oracle.dot2_product(a[rows], b)
+        err_emu = sampled_error(c, a, b, norm_a, norm_b, rows, truth)
         cn = torch.empty_like(c)
         mm.naive(ta, tb, out=cn)
         torch.cuda.synchronize()
@@ -398,7 +516,7 @@ def run_ours(args):
         f1.record(stream)
         torch.cuda.synchronize()
         plain_ms = f0.elapsed_time(f1) / 2
-        err_plain = sampled_error(cn, a, b, norm_a, norm_b, rows)
+        err_plain = sampled_error(cn, a, b, norm_a, norm_b, rows, truth)
         out["plain_fp64"] = {"value": flop / (plain_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms": plain_ms,
                              "kernel": "gemm_f64_dmma (mma.sync m8n8k4 f64)", "rel_inf_err_sampled": err_plain}
         out["accuracy"] = {"rel_inf_err_sampled": err_emu, "rows_sampled": [int(r) for r in rows],
@@ -427,6 +545,11 @@ def run_ours(args):
 
         if args.variants_n > 0:
             out["fp64_methods"] = variants_bench(dev, args.variants_n)
+        if not args.no_configs:
+            out["slice_sweep"] = slice_sweep(ta, tb, a, b, norm_a, norm_b, rows, truth)
+            out["shape_4096x16384x4096"] = tall_inner_shape(dev)
+            out["badly_scaled_2048"] = badly_scaled_errors(dev)
+            torch.cuda.empty_cache()
         if not args.no_serve:
             del ha, hb, hc
             out["serving"] = serve_bench(dev, args.serve_requests, args.serve_budget_gb,

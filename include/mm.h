@@ -107,6 +107,24 @@ int mm_winograd_scaled(int64_t N, int64_t P, int64_t M, const double *A, int64_t
                        void *stream);
 
 /*
+ * Per-row/column power-of-two scaling of Winograd's form (no counterpart in
+ * the paper; it takes the exact scaling of section "WinogradScaled" from one
+ * global pair of norms to every row of A and every column of B):
+ *   e_i = frexp exponent of max_j |A_ij|, f_k = that of max_j |B_jk| (0 for a
+ *   zero row or column), A' = 2^-e_i A_i,:, B' = 2^-f_k B_:,k,
+ *   C_ik = 2^(e_i + f_k) WinogradOriginal(A', B')_ik.
+ * Every paired sum then adds terms of like magnitude, which keeps the error of
+ * each C_ik relative to its own row and column scales (rows and columns of
+ * widely different magnitude).  y' and z' are bit-identical to a sequential
+ * evaluation over A' and B'; the paired sum uses FMA.  Scalings are exact
+ * unless a scaled entry leaves the normal range.
+ * Workspace: mm_winograd_rowcol_scaled_workspace_bytes.
+ */
+size_t mm_winograd_rowcol_scaled_workspace_bytes(int64_t N, int64_t P, int64_t M);
+int mm_winograd_rowcol_scaled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                              int64_t ldb, double *C, int64_t ldc, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Sections "StrassenNaiv" and "StrassenWinograd": recursive block products
  * with 7 half-size products per level (H1..H7; 18 additions for Strassen's
  * form, 15 for Winograd's variant), down to a base product on the FP64

@@ -13,7 +13,7 @@ import ctypes
 
 from ._native import KernelStat, MMError, check, lib
 
-__all__ = ["naive", "kahan", "winograd", "winograd_scaled", "strassen", "strassen_winograd", "tune_strassen", "norm_inf",
+__all__ = ["naive", "kahan", "winograd", "winograd_scaled", "winograd_rowcol_scaled", "strassen", "strassen_winograd", "tune_strassen", "norm_inf",
            "emulated", "emulated_group", "emulated_noalloc", "emulated_slices", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
            "SLICE_FP8E4M3"]
 
@@ -110,6 +110,18 @@ def winograd_scaled(a, b, out=None, return_lambda=False):
     check("mm_winograd_scaled", lib().mm_winograd_scaled(*_gemm_args(a, b, c, n, p, m), _ptr(lam), _ptr(ws), need,
                                                          _stream(a.device)))
     return (c, lam) if return_lambda else c
+
+
+def winograd_rowcol_scaled(a, b, out=None):
+    """Winograd's form with each row of A scaled by 2^-e_i and each column of B
+    by 2^-f_k (frexp exponents of their maxima), the result by 2^(e_i + f_k):
+    the power-of-two scaling of section "WinogradScaled" per row and column."""
+    a, b, c, n, p, m = _prep(a, b, out)
+    need = lib().mm_winograd_rowcol_scaled_workspace_bytes(n, p, m)
+    ws = _ws(need, a.device)
+    check("mm_winograd_rowcol_scaled", lib().mm_winograd_rowcol_scaled(*_gemm_args(a, b, c, n, p, m), _ptr(ws), need,
+                                                                       _stream(a.device)))
+    return c
 
 
 def _strassen(name, a, b, cutoff, out):

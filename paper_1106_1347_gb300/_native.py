@@ -53,6 +53,8 @@ SIGNATURES = {
     "mm_winograd": (ctypes.c_int, GEMM + [vp, sz, vp]),
     "mm_winograd_scaled_workspace_bytes": (sz, [i64, i64, i64]),
     "mm_winograd_scaled": (ctypes.c_int, GEMM + [vp, vp, sz, vp]),
+    "mm_winograd_rowcol_scaled_workspace_bytes": (sz, [i64, i64, i64]),
+    "mm_winograd_rowcol_scaled": (ctypes.c_int, GEMM + [vp, sz, vp]),
     "mm_strassen_workspace_bytes": (sz, [i64, i64, i64, i32]),
     "mm_strassen": (ctypes.c_int, GEMM + [i32, vp, sz, vp]),
     "mm_strassen_winograd_workspace_bytes": (sz, [i64, i64, i64, i32]),

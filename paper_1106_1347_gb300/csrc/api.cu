@@ -199,18 +199,21 @@ int mm_kahan(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, cons
     return run_kahan(N, P, M, A, lda, B, ldb, C, ldc, (cudaStream_t)stream);
 }
 
-size_t mm_winograd_workspace_bytes(int64_t N, int64_t P, int64_t M) { return winograd_ws_bytes(N, P, M, false); }
+size_t mm_winograd_workspace_bytes(int64_t N, int64_t P, int64_t M) { return winograd_ws_bytes(N, P, M, 0); }
 
-size_t mm_winograd_scaled_workspace_bytes(int64_t N, int64_t P, int64_t M) {
-    return winograd_ws_bytes(N, P, M, true);
+size_t mm_winograd_scaled_workspace_bytes(int64_t N, int64_t P, int64_t M) { return winograd_ws_bytes(N, P, M, 1); }
+
+size_t mm_winograd_rowcol_scaled_workspace_bytes(int64_t N, int64_t P, int64_t M) {
+    return winograd_ws_bytes(N, P, M, 2);
 }
 
-static int winograd_common(const char *fn, bool scaled, int64_t N, int64_t P, int64_t M, const double *A,
+static int winograd_common(const char *fn, int mode, int64_t N, int64_t P, int64_t M, const double *A,
                            int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc, int32_t *lambda_out,
                            void *ws, size_t ws_bytes, void *stream) {
+    const bool scaled = mode == 1;
     int rc = check_gemm_args(fn, N, P, M, A, lda, B, ldb, C, ldc);
     if (rc) return rc;
-    size_t need = winograd_ws_bytes(N, P, M, scaled);
+    size_t need = winograd_ws_bytes(N, P, M, mode);
     if (ws_bytes < need || (need && !ws))
         return fail(MM_ERR_WORKSPACE, "%s: workspace %zu bytes < %zu required", fn, ws_bytes, need);
     cudaStream_t st = (cudaStream_t)stream;
@@ -221,17 +224,23 @@ static int winograd_common(const char *fn, bool scaled, int64_t N, int64_t P, in
         }
         return MM_OK;
     }
-    return run_winograd(N, P, M, A, lda, B, ldb, C, ldc, scaled, lambda_out, ws, st);
+    return run_winograd(N, P, M, A, lda, B, ldb, C, ldc, mode, lambda_out, ws, st);
 }
 
 int mm_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
                 double *C, int64_t ldc, void *ws, size_t ws_bytes, void *stream) {
-    return winograd_common("mm_winograd", false, N, P, M, A, lda, B, ldb, C, ldc, nullptr, ws, ws_bytes, stream);
+    return winograd_common("mm_winograd", 0, N, P, M, A, lda, B, ldb, C, ldc, nullptr, ws, ws_bytes, stream);
 }
 
 int mm_winograd_scaled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
                        double *C, int64_t ldc, int32_t *lambda_out, void *ws, size_t ws_bytes, void *stream) {
-    return winograd_common("mm_winograd_scaled", true, N, P, M, A, lda, B, ldb, C, ldc, lambda_out, ws, ws_bytes,
+    return winograd_common("mm_winograd_scaled", 1, N, P, M, A, lda, B, ldb, C, ldc, lambda_out, ws, ws_bytes,
+                           stream);
+}
+
+int mm_winograd_rowcol_scaled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                              int64_t ldb, double *C, int64_t ldc, void *ws, size_t ws_bytes, void *stream) {
+    return winograd_common("mm_winograd_rowcol_scaled", 2, N, P, M, A, lda, B, ldb, C, ldc, nullptr, ws, ws_bytes,
                            stream);
 }
 

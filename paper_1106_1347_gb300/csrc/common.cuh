@@ -71,9 +71,10 @@ int run_naive(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, con
               int64_t ldc, cudaStream_t st);
 int run_kahan(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
               int64_t ldc, cudaStream_t st);
-size_t winograd_ws_bytes(int64_t N, int64_t P, int64_t M, bool scaled);
+// mode: 0 WinogradOriginal, 1 Brent's global lambda, 2 per-row/column exponents.
+size_t winograd_ws_bytes(int64_t N, int64_t P, int64_t M, int mode);
 int run_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
-                 double *C, int64_t ldc, bool scaled, int32_t *lambda_out, void *ws, cudaStream_t st);
+                 double *C, int64_t ldc, int mode, int32_t *lambda_out, void *ws, cudaStream_t st);
 int strassen_plan(int variant, int64_t N, int64_t P, int64_t M, int32_t cutoff, int *depth, int64_t *Np,
                   int64_t *Pp, int64_t *Mp);
 bool tuned_strassen_depth(int variant, int64_t N, int64_t P, int64_t M, int *depth);

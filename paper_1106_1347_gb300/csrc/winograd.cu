@@ -14,6 +14,11 @@
 //     tiles (MultiplyWithScalar by exact powers of two), and uses
 //     y' = 4^lambda y and z' = 4^-lambda z, which equal the terms of the
 //     scaled matrices bit for bit when nothing over- or underflows.
+//  4. per-row/column scaled form (Brent's exact power-of-two scaling taken to
+//     each row of A and column of B): the row pass first finds e_i, the frexp
+//     exponent of max_j |A_ij|, then sums y'_i over A'_i,: = 2^-e_i A_i,:; the
+//     column pass does the same for f_k and z'_k; the main kernel scales the
+//     staged tiles by 2^-e_i and 2^-f_k and the result by 2^(e_i + f_k).
 // y and z are bit-identical to a sequential evaluation; the paired sum uses
 // one FMA per pair (2 DADD + 1 DFMA per pair per output, the FP64 pipe bound).
 #include "common.cuh"
@@ -75,6 +80,78 @@ __global__ void __launch_bounds__(128) b_terms_kernel(int64_t P, int64_t M, cons
     z[k] = s;
 }
 
+// frexp exponent of the double with bit pattern `bits` (>= 0), 0 for zero.
+__device__ __forceinline__ int exponent_of(unsigned long long bits) {
+    if (bits == 0) return 0;
+    int e;
+    (void)frexp(__longlong_as_double((long long)bits), &e);
+    return e;
+}
+
+// Row pass of the per-row/column scaled form: e_i, then y'_i over 2^-e_i A_i,:.
+__global__ void __launch_bounds__(32) a_terms_rowcol_kernel(int64_t N, int64_t P, const double *__restrict__ A,
+                                                            int64_t lda, double *__restrict__ y,
+                                                            int32_t *__restrict__ ea) {
+    __shared__ double tile[kRows][kRows + 1];
+    const int lane = threadIdx.x;
+    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    const int64_t nrows = min((int64_t)kRows, N - row0);
+    const int64_t gamma2 = (P / 2) * 2;
+    // Pass 1: the row maximum of |A_ij| on the bit patterns (lane r owns row r).
+    unsigned long long mx = 0;
+    for (int64_t c0 = 0; c0 < P; c0 += kRows) {
+        const int64_t c = c0 + lane;
+#pragma unroll 4
+        for (int r = 0; r < kRows; ++r)
+            tile[r][lane] = (r < nrows && c < P) ? A[(row0 + r) * lda + c] : 0.0;
+        __syncwarp();
+        const int ncols = (int)min((int64_t)kRows, P - c0);
+        for (int j = 0; j < ncols; ++j) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(tile[lane][j]) & ~(1ull << 63);
+            mx = b > mx ? b : mx;
+        }
+        __syncwarp();
+    }
+    const int e = exponent_of(mx);
+    // Pass 2: y'_i = sum_j RN(A'_i,2j A'_i,2j+1) in order, A' = 2^-e_i A (exact).
+    double ys = 0.0;
+    for (int64_t c0 = 0; c0 < gamma2; c0 += kRows) {
+        const int64_t c = c0 + lane;
+#pragma unroll 4
+        for (int r = 0; r < kRows; ++r)
+            tile[r][lane] = (r < nrows && c < gamma2) ? A[(row0 + r) * lda + c] : 0.0;
+        __syncwarp();
+        const int npair = (int)min((int64_t)kRows, gamma2 - c0) / 2;
+        for (int j = 0; j < npair; ++j)
+            ys = __dadd_rn(ys, __dmul_rn(ldexp(tile[lane][2 * j], -e), ldexp(tile[lane][2 * j + 1], -e)));
+        __syncwarp();
+    }
+    if (lane < nrows) {
+        y[row0 + lane] = ys;
+        ea[row0 + lane] = e;
+    }
+}
+
+// Column pass of the per-row/column scaled form: f_k, then z'_k over 2^-f_k B_:,k.
+__global__ void __launch_bounds__(128) b_terms_rowcol_kernel(int64_t P, int64_t M, const double *__restrict__ B,
+                                                             int64_t ldb, double *__restrict__ z,
+                                                             int32_t *__restrict__ fb) {
+    const int64_t k = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (k >= M) return;
+    unsigned long long mx = 0;
+    for (int64_t j = 0; j < P; ++j) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(B[j * ldb + k]) & ~(1ull << 63);
+        mx = b > mx ? b : mx;
+    }
+    const int f = exponent_of(mx);
+    const int64_t gamma = P / 2;
+    double s = 0.0;
+    for (int64_t j = 0; j < gamma; ++j)
+        s = __dadd_rn(s, __dmul_rn(ldexp(B[(2 * j) * ldb + k], -f), ldexp(B[(2 * j + 1) * ldb + k], -f)));
+    z[k] = s;
+    fb[k] = f;
+}
+
 // Smallest lambda with 1/2 <= 4^lambda a / b <= 2, from frexp pairs (exact).
 __device__ int brent_lambda(double a, double b) {
     if (!(a > 0.0) || !(b > 0.0) || isinf(a) || isinf(b)) return 0;
@@ -91,12 +168,15 @@ __device__ int brent_lambda(double a, double b) {
 
 constexpr int TM = 64, TN = 64, TK = 16;
 
-template <bool kScaled>
+// kMode: 0 WinogradOriginal, 1 Brent's global lambda, 2 per-row/column exponents.
+template <int kMode>
 __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int64_t M, const double *__restrict__ A,
                                                        int64_t lda, const double *__restrict__ B, int64_t ldb,
                                                        double *__restrict__ C, int64_t ldc,
                                                        const double *__restrict__ y, const double *__restrict__ z,
-                                                       const double *norms, int32_t *lambda_out) {
+                                                       const double *norms, int32_t *lambda_out,
+                                                       const int32_t *__restrict__ ea, const int32_t *__restrict__ fb) {
+    constexpr bool kScaled = kMode == 1, kRowCol = kMode == 2;
     __shared__ double As[TM][TK + 1];
     __shared__ double Bs[TK][TN];
     __shared__ double s_scale[2];
@@ -122,6 +202,18 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
     double ra[4], rb[4];
+    // Per-row/column form: this thread stages rows (tid >> 4) + 16 q of A and
+    // column (tid & 63) of B in every K-step.
+    int erow[4], fcol = 0;
+    if (kRowCol) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t gi = i0 + ((tid + 256 * q) >> 4);
+            erow[q] = gi < N ? ea[gi] : 0;
+        }
+        const int64_t bj = j0 + (tid & 63);
+        fcol = bj < M ? fb[bj] : 0;
+    }
     auto fetch = [&](int64_t k0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -133,6 +225,10 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
             if (kScaled) {
                 av *= sa;
                 bv *= sb;
+            }
+            if (kRowCol) {
+                av = ldexp(av, -erow[q]);
+                bv = ldexp(bv, -fcol);
             }
             ra[q] = av;
             rb[q] = bv;
@@ -179,8 +275,9 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
         if (i >= N) continue;
         double yi = y[i];
         double alast = 0.0;
+        const int ei = kRowCol ? ea[i] : 0;
         if (kScaled) yi = (yi * sa) * sa;
-        if (odd) alast = A[i * lda + (P - 1)] * sa;
+        if (odd) alast = kRowCol ? ldexp(A[i * lda + (P - 1)], -ei) : A[i * lda + (P - 1)] * sa;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int64_t k = j0 + tx + 16 * c;
@@ -188,7 +285,13 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
             double zk = z[k];
             if (kScaled) zk = (zk * sb) * sb;
             double v = __dsub_rn(__dsub_rn(acc[r][c], yi), zk);
-            if (odd) v = __dadd_rn(v, __dmul_rn(alast, B[(P - 1) * ldb + k] * sb));
+            if (kRowCol) {
+                const int fk = fb[k];
+                if (odd) v = __dadd_rn(v, __dmul_rn(alast, ldexp(B[(P - 1) * ldb + k], -fk)));
+                v = ldexp(v, ei + fk);
+            } else if (odd) {
+                v = __dadd_rn(v, __dmul_rn(alast, B[(P - 1) * ldb + k] * sb));
+            }
             C[i * ldc + k] = v;
         }
     }
@@ -198,24 +301,29 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
 
 namespace mm {
 
-size_t winograd_ws_bytes(int64_t N, int64_t P, int64_t M, bool scaled) {
+size_t winograd_ws_bytes(int64_t N, int64_t P, int64_t M, int mode) {
     (void)P;
     if (N < 0 || M < 0) return 0;
-    size_t b = align_up((size_t)std::max<int64_t>(N, 1) * 8, 256) + align_up((size_t)std::max<int64_t>(M, 1) * 8, 256);
-    if (scaled) b += 256;
+    const size_t yb = align_up((size_t)std::max<int64_t>(N, 1) * 8, 256);
+    const size_t zb = align_up((size_t)std::max<int64_t>(M, 1) * 8, 256);
+    size_t b = yb + zb;
+    if (mode == 1) b += 256;  // the two norms
+    if (mode == 2) b += align_up((size_t)std::max<int64_t>(N, 1) * 4, 256) + align_up((size_t)std::max<int64_t>(M, 1) * 4, 256);
     return b;
 }
 
 int run_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
-                 double *C, int64_t ldc, bool scaled, int32_t *lambda_out, void *ws, cudaStream_t st) {
+                 double *C, int64_t ldc, int mode, int32_t *lambda_out, void *ws, cudaStream_t st) {
     char *w = (char *)ws;
+    const size_t yb = align_up((size_t)std::max<int64_t>(N, 1) * 8, 256);
+    const size_t zb = align_up((size_t)std::max<int64_t>(M, 1) * 8, 256);
     double *y = (double *)w;
-    double *z = (double *)(w + align_up((size_t)std::max<int64_t>(N, 1) * 8, 256));
-    double *norms = scaled ? (double *)(w + align_up((size_t)std::max<int64_t>(N, 1) * 8, 256) +
-                                        align_up((size_t)std::max<int64_t>(M, 1) * 8, 256))
-                           : nullptr;
+    double *z = (double *)(w + yb);
+    double *norms = mode == 1 ? (double *)(w + yb + zb) : nullptr;
+    int32_t *ea = mode == 2 ? (int32_t *)(w + yb + zb) : nullptr;
+    int32_t *fb = mode == 2 ? (int32_t *)(w + yb + zb + align_up((size_t)std::max<int64_t>(N, 1) * 4, 256)) : nullptr;
     int rc;
-    if (scaled) {
+    if (mode == 1) {
         cudaError_t e = cudaMemsetAsync(norms, 0, 2 * sizeof(double), st);
         if (e != cudaSuccess) return cuda_fail(e, "mm_winograd_scaled");
         rc = launch("winograd_a_terms_norm", st, [&] {
@@ -228,23 +336,40 @@ int run_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
             rc = run_norm_inf(P, M, B, ldb, norms + 1, st);
             if (rc) return rc;
         }
+    } else if (mode == 2) {
+        rc = launch("winograd_a_terms_rowcol", st, [&] {
+            a_terms_rowcol_kernel<<<(unsigned)ceil_div(N, kRows), 32, 0, st>>>(N, P, A, lda, y, ea);
+        });
+        if (rc) return rc;
     } else {
         rc = launch("winograd_a_terms", st, [&] {
             a_terms_kernel<false><<<(unsigned)ceil_div(N, kRows), 32, 0, st>>>(N, P, A, lda, y, nullptr);
         });
         if (rc) return rc;
     }
-    rc = launch("winograd_b_terms", st,
-                [&] { b_terms_kernel<<<(unsigned)ceil_div(M, 128), 128, 0, st>>>(P, M, B, ldb, z); });
+    if (mode == 2)
+        rc = launch("winograd_b_terms_rowcol", st, [&] {
+            b_terms_rowcol_kernel<<<(unsigned)ceil_div(M, 128), 128, 0, st>>>(P, M, B, ldb, z, fb);
+        });
+    else
+        rc = launch("winograd_b_terms", st,
+                    [&] { b_terms_kernel<<<(unsigned)ceil_div(M, 128), 128, 0, st>>>(P, M, B, ldb, z); });
     if (rc) return rc;
     dim3 grid((unsigned)ceil_div(M, TN), (unsigned)ceil_div(N, TM));
     if (grid.y > 65535) return fail(MM_ERR_UNSUPPORTED, "mm_winograd: N too large for one launch");
-    if (scaled)
+    if (mode == 1)
         return launch("winograd_scaled_f64", st, [&] {
-            winograd_kernel<true><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, norms, lambda_out);
+            winograd_kernel<1><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, norms, lambda_out,
+                                                     nullptr, nullptr);
+        });
+    if (mode == 2)
+        return launch("winograd_rowcol_scaled_f64", st, [&] {
+            winograd_kernel<2><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, nullptr, nullptr, ea,
+                                                     fb);
         });
     return launch("winograd_f64", st, [&] {
-        winograd_kernel<false><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, nullptr, nullptr);
+        winograd_kernel<0><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, nullptr, nullptr, nullptr,
+                                                 nullptr);
     });
 }
 

@@ -124,6 +124,51 @@ def test_winograd_scaled_paper_tie(mm, orc):
     assert np.array_equal(host(mm.winograd_scaled(dev(ai), dev(bi))), ai @ bi)
 
 
+# ---------------------------------------- per-row/column scaled Winograd
+
+@pytest.mark.parametrize("shape", SHAPES + [(33, 2047 % 97, 40)])
+def test_winograd_rowcol_integer_bit_exact(mm, orc, shape):
+    a, b = pair(*shape, "int", 21)
+    got = host(mm.winograd_rowcol_scaled(dev(a), dev(b)))
+    assert np.array_equal(got, orc.winograd_rowcol_scaled(a, b)[0])
+    assert np.array_equal(got, a @ b)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_winograd_rowcol_uniform_within_tolerance(mm, orc, shape):
+    a, b = pair(*shape, "uni", 22)
+    got = host(mm.winograd_rowcol_scaled(dev(a), dev(b)))
+    assert orc.rel_inf_error(got, orc.winograd_rowcol_scaled(a, b)[0], a, b) <= TOL
+
+
+@pytest.mark.parametrize("n", [64, 301])
+def test_winograd_rowcol_badly_scaled(mm, orc, n):
+    """Rows of A times 10^u, columns of B times 10^v: every element within the
+    elementwise bound 8 gamma (gamma + 5) u 2^(e_i + f_k) of the exact product
+    (the oracle's own pin), which plain Winograd misses by orders of magnitude."""
+    a, b = S.badly_scaled(n, S.stream_seed(2, 20 + n), S.stream_seed(2, 21 + n))
+    truth = orc.dot2_product(a, b)
+    ref, e, f = orc.winograd_rowcol_scaled(a, b)
+    got = host(mm.winograd_rowcol_scaled(dev(a), dev(b)))
+    gamma = n // 2
+    bound = 8 * gamma * (gamma + 5) * 2.0 ** -53 * np.ldexp(1.0, e[:, None] + f[None, :])
+    assert (np.abs(got - truth) <= bound).all()
+    assert (np.abs(got - ref) <= 2 * bound).all()
+
+
+def test_winograd_rowcol_power_of_two_invariance(mm):
+    """Prescaling rows of A and columns of B by powers of two leaves the scaled
+    operands unchanged, so the GPU result scales by exactly 2^(r_i + c_k)."""
+    a = S.uniform(70, 45, 23)
+    b = S.uniform(45, 66, 24)
+    rng = np.random.default_rng(12)
+    r = rng.integers(-60, 61, size=70)
+    c = rng.integers(-60, 61, size=66)
+    c0 = host(mm.winograd_rowcol_scaled(dev(a), dev(b)))
+    c1 = host(mm.winograd_rowcol_scaled(dev(np.ldexp(a, r[:, None])), dev(np.ldexp(b, c[None, :]))))
+    assert np.array_equal(c1, np.ldexp(c0, r[:, None] + c[None, :]))
+
+
 # --------------------------------------------------------------- Strassen
 
 STRASSEN = [("strassen", "strassen_naiv"), ("strassen_winograd", "strassen_winograd")]
@@ -265,8 +310,8 @@ def test_emulated_group_rejects_overlapping_outputs(mm):
 
 # ------------------------------------------------------------ edge cases
 
-@pytest.mark.parametrize("name", ["naive", "kahan", "winograd", "winograd_scaled", "strassen", "strassen_winograd",
-                                  "emulated"])
+@pytest.mark.parametrize("name", ["naive", "kahan", "winograd", "winograd_scaled", "winograd_rowcol_scaled",
+                                  "strassen", "strassen_winograd", "emulated"])
 def test_degenerate_shapes(mm, name):
     import torch
 
@@ -281,7 +326,7 @@ def test_degenerate_shapes(mm, name):
     assert fn(a, b).shape == (0, 3)
 
 
-@pytest.mark.parametrize("name", ["naive", "kahan", "winograd", "strassen", "emulated"])
+@pytest.mark.parametrize("name", ["naive", "kahan", "winograd", "winograd_rowcol_scaled", "strassen", "emulated"])
 def test_strided_views(mm, orc, name):
     """Leading dimensions larger than the column count (sub-matrix views)."""
     big_a = S.integers(90, 120, 181)
