@@ -53,6 +53,10 @@ def _load():
             lib.oracle_winograd_terms.argtypes = [i64, i64, i64, dp, i64, dp, i64, dp, dp]
             lib.oracle_winograd_scaled.argtypes = gemm
             lib.oracle_winograd_scaled.restype = ctypes.c_int
+            lib.oracle_naiv_on_array.argtypes = gemm
+            lib.oracle_naiv_on_array.restype = None
+            lib.oracle_naiv_unrolled.argtypes = gemm + [ctypes.c_int]
+            lib.oracle_naiv_unrolled.restype = ctypes.c_int
             lib.oracle_winograd_rowcol_scaled.argtypes = gemm + [ip, ip]
             lib.oracle_winograd_rowcol_scaled.restype = None
             lib.oracle_brent_lambda.argtypes = [ctypes.c_double, ctypes.c_double]
@@ -116,6 +120,30 @@ def naiv_standard(a, b):
 
 def naiv_kahan(a, b):
     return _gemm("oracle_naiv_kahan", a, b)[0]
+
+
+def naiv_on_array(a, b):
+    return _gemm("oracle_naiv_on_array", a, b)[0]
+
+
+def naiv_unrolled(a, b, u: int):
+    """NaivLoopUnrollingTwo/Three/Four for u = 2/3/4 (u = 1: NaivStandard)."""
+    c, rc = _gemm("oracle_naiv_unrolled", a, b, int(u))
+    if rc != 0:
+        raise ValueError("unroll factor must be >= 1")
+    return c
+
+
+def naiv_unrolled_2(a, b):
+    return naiv_unrolled(a, b, 2)
+
+
+def naiv_unrolled_3(a, b):
+    return naiv_unrolled(a, b, 3)
+
+
+def naiv_unrolled_4(a, b):
+    return naiv_unrolled(a, b, 4)
 
 
 def winograd_original(a, b):

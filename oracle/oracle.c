@@ -92,6 +92,50 @@ void oracle_naiv_standard(int64_t N, int64_t P, int64_t M, const double *A, int6
         }
 }
 
+/* Section "NaivOnArray": the naive sum accumulated in C itself rather than in
+ * an auxiliary variable (C_ij = 0, then C_ij = C_ij + A_ik B_kj for k in
+ * order).  Each step still rounds to double, so the value equals NaivStandard's. */
+void oracle_naiv_on_array(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                          int64_t ldb, double *C, int64_t ldc) {
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < M; ++j) {
+            AT(C, ldc, i, j) = 0.0;
+            for (int64_t k = 0; k < P; ++k) AT(C, ldc, i, j) = AT(C, ldc, i, j) + AT(A, lda, i, k) * AT(B, ldb, k, j);
+        }
+}
+
+/* Section "Loop unrolling" (NaivLoopUnrollingTwo, -Three, -Four): the naive
+ * sum taken u terms at a time, each group summed left to right before it is
+ * added to the running sum,
+ *   aux = aux + ((A_i,uk-u+1 B_uk-u+1,j + A_i,uk-u+2 B_uk-u+2,j) + ...),
+ * for k = 1 .. floor(P/u), then the P mod u leftover terms added one by one in
+ * index order (the "correction terms").  The printed A_i,2k B_2k,j of the
+ * three-term formula is read as A_i,3k B_3k,j; the four-term form prints no
+ * formula and follows the same pattern.  u = 1 is NaivStandard. */
+int oracle_naiv_unrolled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                         double *C, int64_t ldc, int u) {
+    if (u < 1) return -1;
+    const int64_t full = (P / u) * u;
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < M; ++j) {
+            double aux = 0.0;
+            for (int64_t k = 0; k < full; k += u) {
+                double grp = AT(A, lda, i, k) * AT(B, ldb, k, j);
+                for (int t = 1; t < u; ++t) {
+                    double prod = AT(A, lda, i, k + t) * AT(B, ldb, k + t, j);
+                    grp = grp + prod;
+                }
+                aux = aux + grp;
+            }
+            for (int64_t k = full; k < P; ++k) {
+                double prod = AT(A, lda, i, k) * AT(B, ldb, k, j);
+                aux = aux + prod;
+            }
+            AT(C, ldc, i, j) = aux;
+        }
+    return 0;
+}
+
 /* Section "NaivKahan": the naive sum with the compensated update
  *   err = err + x; t = sum + err; err = (sum - t) + err; sum = t
  * applied to x = A_ik * B_kj (rounded).  The result is sum. */

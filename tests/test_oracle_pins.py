@@ -16,8 +16,9 @@ import synthetic as S
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_pins.json")))
 U = 2.0 ** -53
 
-GEMMS = ["naiv_standard", "naiv_kahan", "winograd_original", "winograd_scaled", "winograd_rowcol_scaled",
-         "strassen_naiv", "strassen_winograd", "dot2_product"]
+GEMMS = ["naiv_standard", "naiv_on_array", "naiv_unrolled_2", "naiv_unrolled_3", "naiv_unrolled_4", "naiv_kahan",
+         "winograd_original", "winograd_scaled", "winograd_rowcol_scaled", "strassen_naiv", "strassen_winograd",
+         "dot2_product"]
 
 
 def run(orc, name, a, b, **kw):
@@ -188,7 +189,8 @@ def test_kahan_error_bound_and_gain(orc):
     assert abs(Fraction(float(k)) - exact) <= U * exact  # within half an ulp of 1
 
 
-@pytest.mark.parametrize("name", ["naiv_standard", "winograd_original", "winograd_scaled", "winograd_rowcol_scaled",
+@pytest.mark.parametrize("name", ["naiv_standard", "naiv_unrolled_2", "naiv_unrolled_3", "naiv_unrolled_4",
+                                  "winograd_original", "winograd_scaled", "winograd_rowcol_scaled",
                                   "strassen_naiv", "strassen_winograd"])
 def test_real_inputs_near_exact(orc, name):
     """Random reals: normwise error against the exact product stays far below 1e-14."""
@@ -365,3 +367,53 @@ def test_rowcol_elementwise_bound_on_badly_scaled(orc):
     bound = 8 * gamma * (gamma + 5) * U * np.ldexp(1.0, e[:, None] + f[None, :])
     assert (np.abs(c - truth) <= bound).all()
     assert not (np.abs(orc.winograd_original(a, b) - truth) <= bound).all()
+
+
+# ------------------------------------------------ NaivOnArray, loop unrolling
+
+def test_loop_unrolling_discriminator_golden(orc):
+    """Hand-derived sums where the grouping of the unrolled forms changes the
+    rounded result (section 'Loop unrolling')."""
+    g = GOLD["loop_unrolling_discriminator"]
+    for case in g["cases"]:
+        a = np.array([case["row"]])
+        b = np.ones((a.shape[1], 1))
+        assert orc.naiv_standard(a, b)[0, 0] == case["naive"]
+        assert orc.naiv_on_array(a, b)[0, 0] == case["on_array"]
+        for u in (2, 3, 4):
+            assert orc.naiv_unrolled(a, b, u)[0, 0] == case[f"u{u}"], u
+
+
+def test_unroll_one_and_on_array_are_naiv_standard(orc):
+    """u = 1 is the plain sum, and accumulating in C rounds exactly as an auxiliary does."""
+    a = S.loguniform(9, 37, 95)
+    b = S.loguniform(37, 7, 96)
+    ref = orc.naiv_standard(a, b)
+    assert np.array_equal(orc.naiv_unrolled(a, b, 1), ref)
+    assert np.array_equal(orc.naiv_on_array(a, b), ref)
+
+
+@pytest.mark.parametrize("u", [2, 3, 4])
+def test_unrolled_grouping_by_exact_rationals(orc, u):
+    """Each unrolled result equals the same grouping evaluated with exact
+    rational arithmetic and a rounding to double after every operation, for
+    every P mod u (the correction terms included)."""
+    rng = np.random.default_rng(40 + u)
+    for p in range(1, 3 * u + 2):
+        a = rng.uniform(-1, 1, size=(1, p)) * np.ldexp(1.0, rng.integers(-30, 30, size=(1, p)))
+        b = rng.uniform(-1, 1, size=(p, 1))
+
+        def rn(fr):
+            return Fraction(float(fr))  # correctly rounded to double
+
+        prods = [rn(Fraction(float(a[0, k])) * Fraction(float(b[k, 0]))) for k in range(p)]
+        aux = Fraction(0)
+        full = (p // u) * u
+        for k in range(0, full, u):
+            grp = prods[k]
+            for t in range(1, u):
+                grp = rn(grp + prods[k + t])
+            aux = rn(aux + grp)
+        for k in range(full, p):
+            aux = rn(aux + prods[k])
+        assert orc.naiv_unrolled(a, b, u)[0, 0] == float(aux)
