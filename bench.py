@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the slice sweep, the 4096x16384x4096 shape and the badly scaled errors")
-    ap.add_argument("--variants-n", type=int, default=4096, help="size of the per-method FP64 timings (0: skip)")
+    ap.add_argument("--variants-n", type=int, default=1, help="0: skip the per-method FP64 sweep and the paper's table")
     ap.add_argument("--fp64-only", action="store_true", help="only the per-method FP64 timings (profiling runs)")
     args = ap.parse_args()
     global N, P, M, WORKLOAD
@@ -387,47 +387,95 @@ def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000
 FP64_PEAK_TFLOPS = 1.056  # DFMA and mma.sync f64 on GB300, measured by the library's own probe
 
 
-def variants_bench(dev, n):
-    """Each FP64 method at n^3 (uniform [-1, 1] inputs): TFLOP/s as 2n^3/t and
-    the FP64-pipe work it issues against the measured FP64 peak."""
+FP64_SWEEP = (256, 1024, 2047, 2048, 4095, 4096, 8192)
+
+
+def variants_bench(dev, sizes=FP64_SWEEP):
+    """Each FP64 method at n^3 for n in `sizes` (uniform [-1, 1] inputs; odd n
+    exercise Winograd's odd-P term): TFLOP/s as 2n^3/t and, for the methods
+    with a fixed operation count, the fraction of the FP64 pipe kept busy."""
     import torch
 
     import paper_1106_1347_gb300 as mm
     import synthetic as S
 
-    a = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 0))).to(dev)
-    b = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 1))).to(dev)
-    out = {}
     # FP64-pipe operations (an FMA, DADD or DMUL each, or 1/256 of an m8n8k4 MMA)
-    # issued per reported flop (2n^3 per product): naive 1 FMA per 2 flop; Kahan
-    # 1 DMUL + 4 DADD per k; Winograd 2 DADD + 1 FMA per pair of k.
-    pipe = {"naive": 0.5, "kahan": 2.5, "winograd": 0.75, "winograd_scaled": 0.75, "winograd_rowcol_scaled": 0.75}
+    # issued per reported flop (2n^3 per product): naive 1 FMA per 2 flop; the
+    # ordered naive sum 1 DMUL + 1 DADD per k (plus 1 DADD per group of 4 when
+    # unrolled); Kahan 1 DMUL + 4 DADD per k; Winograd 2 DADD + 1 FMA per pair of k.
+    pipe = {"naive": 0.5, "naive_ordered": 1.0, "naive_unrolled_4": 1.125, "kahan": 2.5, "winograd": 0.75,
+            "winograd_scaled": 0.75, "winograd_rowcol_scaled": 0.75}
     peak_ops = FP64_PEAK_TFLOPS / 2.0  # FP64-pipe ops per second (1e12)
-    runs = {
-        "naive": lambda: mm.naive(a, b),
-        "kahan": lambda: mm.kahan(a, b),
-        "winograd": lambda: mm.winograd(a, b),
-        "winograd_scaled": lambda: mm.winograd_scaled(a, b),
-        "winograd_rowcol_scaled": lambda: mm.winograd_rowcol_scaled(a, b),
-        "strassen": lambda: mm.strassen(a, b),
-        "strassen_winograd": lambda: mm.strassen_winograd(a, b),
-    }
-    for name, fn in runs.items():
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        fn()
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        tf = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
-        entry = {"ms": ms, "tflops": tf}
-        if name in pipe:  # fraction of the FP64 pipe kept busy
-            entry["fp64_pipe_frac"] = tf * pipe[name] / peak_ops
-        out[name] = entry
-    return {"n": n, "inputs": "uniform [-1, 1]", "fp64_peak_tflops": FP64_PEAK_TFLOPS,
-            "fp64_peak_source": "own probe: DFMA and mma.sync m8n8k4 f64 both ~1.06 TFLOP/s", "methods": out}
+    by_size = {}
+    for n in sizes:
+        a = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 0))).to(dev)
+        b = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 1))).to(dev)
+        c = torch.empty((n, n), dtype=torch.float64, device=dev)
+        runs = {
+            "naive": lambda: mm.naive(a, b, out=c),
+            "naive_ordered": lambda: mm.naive_unrolled(a, b, unroll=1, out=c),
+            "naive_unrolled_4": lambda: mm.naive_unrolled(a, b, unroll=4, out=c),
+            "kahan": lambda: mm.kahan(a, b, out=c),
+            "winograd": lambda: mm.winograd(a, b, out=c),
+            "winograd_scaled": lambda: mm.winograd_scaled(a, b, out=c),
+            "winograd_rowcol_scaled": lambda: mm.winograd_rowcol_scaled(a, b, out=c),
+            "strassen": lambda: mm.strassen(a, b, out=c),
+            "strassen_winograd": lambda: mm.strassen_winograd(a, b, out=c),
+            "emulated_8_slices": lambda: mm.emulated(a, b, nslices=8, out=c),
+        }
+        out = {}
+        for name, fn in runs.items():
+            ms = timed(fn, 1 if n >= 4095 else 3)
+            tf = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+            entry = {"ms": ms, "tflops": tf}
+            if name in pipe:  # fraction of the FP64 pipe kept busy
+                entry["fp64_pipe_frac"] = tf * pipe[name] / peak_ops
+            out[name] = entry
+        by_size[str(n)] = out
+        del a, b, c
+    return {"inputs": "uniform [-1, 1]", "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+            "fp64_peak_source": "own probe: DFMA and mma.sync m8n8k4 f64 both ~1.06 TFLOP/s", "by_size": by_size}
+
+
+def paper_table(dev, sizes=(200, 400, 800), repeats=10):
+    """The paper's own test (section 'Tests'): C = A (8A) for a random n x n A,
+    every method timed over `repeats` runs, and NormInf(N - C) with N the
+    NaivKahan result -- the same table on the GPU.  NaivOnArray runs the
+    ordered naive kernel (its arithmetic is NaivStandard's); Strassen uses the
+    paper's padding rule."""
+    import torch
+
+    import paper_1106_1347_gb300 as mm
+    import synthetic as S
+
+    table = {}
+    for n in sizes:
+        a_h, b_h = S.paper_pair(n, S.stream_seed(5, n))
+        a = torch.from_numpy(a_h).to(dev)
+        b = torch.from_numpy(b_h).to(dev)
+        ref = mm.kahan(a, b)
+        methods = {
+            "NaivKahan (N)": lambda: mm.kahan(a, b),
+            "NaivStandard": lambda: mm.naive_unrolled(a, b, unroll=1),
+            "NaivOnArray": lambda: mm.naive_unrolled(a, b, unroll=1),
+            "NaivLoopUnrollingTwo": lambda: mm.naive_unrolled(a, b, unroll=2),
+            "NaivLoopUnrollingThree": lambda: mm.naive_unrolled(a, b, unroll=3),
+            "NaivLoopUnrollingFour": lambda: mm.naive_unrolled(a, b, unroll=4),
+            "StrassenNaiv": lambda: mm.strassen(a, b, cutoff=0),
+            "StrassenWinograd": lambda: mm.strassen_winograd(a, b, cutoff=0),
+            "WinogradOriginal": lambda: mm.winograd(a, b),
+            "WinogradScaled": lambda: mm.winograd_scaled(a, b),
+            "naive (FP64 DMMA)": lambda: mm.naive(a, b),
+            "emulated, 8 BF16 slices": lambda: mm.emulated(a, b, nslices=8),
+        }
+        rows = {}
+        for name, fn in methods.items():
+            ms = timed(fn, repeats)
+            c = fn()
+            err = float(mm.norm_inf(ref - c).item())
+            rows[name] = {"time_s": ms * 1e-3, "gflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e9, "norm_inf_N_minus_C": err}
+        table[str(n)] = rows
+    return {"workload": "C = A (8A), A uniform [-1, 1]", "repeats": repeats, "time": "mean of one product", "n": table}
 
 
 def run_ours(args):
@@ -544,7 +592,8 @@ def run_ours(args):
                       "h2d_bytes_per_step": int(a.nbytes + b.nbytes), "d2h_bytes_per_step": int(N * M * 8)}
 
         if args.variants_n > 0:
-            out["fp64_methods"] = variants_bench(dev, args.variants_n)
+            out["fp64_methods"] = variants_bench(dev)
+            out["paper_table"] = paper_table(dev)
         if not args.no_configs:
             out["slice_sweep"] = slice_sweep(ta, tb, a, b, norm_a, norm_b, rows, truth)
             out["shape_4096x16384x4096"] = tall_inner_shape(dev)
@@ -586,7 +635,7 @@ def main():
         from paper_1106_1347_gb300 import build as mmbuild
 
         mmbuild.build()
-        print(json.dumps(variants_bench(torch.device("cuda", 0), args.variants_n)), flush=True)
+        print(json.dumps(variants_bench(torch.device("cuda", 0))), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

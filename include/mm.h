@@ -83,6 +83,21 @@ int mm_kahan(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, cons
              double *C, int64_t ldc, void *stream);
 
 /*
+ * Sections "NaivStandard", "NaivOnArray" and "Loop unrolling": the naive sum in
+ * the paper's evaluation orders, every product and sum rounded on its own (no
+ * FMA), bit-identical to the sequential CPU evaluation.
+ *   unroll = 1: aux = aux + A_ik B_kj for k in order (NaivStandard; NaivOnArray
+ *               accumulates in C itself and gives the same value);
+ *   unroll = 2, 3, 4: NaivLoopUnrollingTwo/Three/Four -- u products summed left
+ *               to right, the group added to aux, then the P mod u leftover
+ *               products added one by one.
+ * Other unroll values return MM_ERR_ARG.  The FP64-pipe kernel runs at about
+ * half the rate of mm_naive (no FMA, 2 operations per k); use mm_naive for speed.
+ */
+int mm_naive_unrolled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                      double *C, int64_t ldc, int32_t unroll, void *stream);
+
+/*
  * Section "WinogradOriginal": with gamma = floor(P/2),
  *   y_i = sum_j A_i,2j-1 A_i,2j,  z_k = sum_j B_2j-1,k B_2j,k   (1-based),
  *   C_ik = (sum_j (A_i,2j-1 + B_2j,k)(A_i,2j + B_2j-1,k) - y_i) - z_k

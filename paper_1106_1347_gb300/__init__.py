@@ -13,7 +13,7 @@ import ctypes
 
 from ._native import KernelStat, MMError, check, lib
 
-__all__ = ["naive", "kahan", "winograd", "winograd_scaled", "winograd_rowcol_scaled", "strassen", "strassen_winograd", "tune_strassen", "norm_inf",
+__all__ = ["naive", "naive_unrolled", "kahan", "winograd", "winograd_scaled", "winograd_rowcol_scaled", "strassen", "strassen_winograd", "tune_strassen", "norm_inf",
            "emulated", "emulated_group", "emulated_noalloc", "emulated_slices", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
            "SLICE_FP8E4M3"]
 
@@ -88,6 +88,14 @@ def kahan(a, b, out=None):
     """Section "NaivKahan": naive product with the paper's compensated sum."""
     a, b, c, n, p, m = _prep(a, b, out)
     check("mm_kahan", lib().mm_kahan(*_gemm_args(a, b, c, n, p, m), _stream(a.device)))
+    return c
+
+
+def naive_unrolled(a, b, unroll=1, out=None):
+    """Sections "NaivStandard"/"NaivOnArray" (unroll=1) and "Loop unrolling"
+    (unroll=2, 3, 4): the naive sum in the paper's order, bit-exact."""
+    a, b, c, n, p, m = _prep(a, b, out)
+    check("mm_naive_unrolled", lib().mm_naive_unrolled(*_gemm_args(a, b, c, n, p, m), int(unroll), _stream(a.device)))
     return c
 
 

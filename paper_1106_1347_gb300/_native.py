@@ -49,6 +49,7 @@ SIGNATURES = {
     "mm_norm_inf": (ctypes.c_int, [i64, i64, vp, i64, vp, vp]),
     "mm_naive": (ctypes.c_int, GEMM + [vp]),
     "mm_kahan": (ctypes.c_int, GEMM + [vp]),
+    "mm_naive_unrolled": (ctypes.c_int, GEMM + [i32, vp]),
     "mm_winograd_workspace_bytes": (sz, [i64, i64, i64]),
     "mm_winograd": (ctypes.c_int, GEMM + [vp, sz, vp]),
     "mm_winograd_scaled_workspace_bytes": (sz, [i64, i64, i64]),

@@ -190,6 +190,16 @@ int mm_naive(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, cons
     return run_naive(N, P, M, A, lda, B, ldb, C, ldc, (cudaStream_t)stream);
 }
 
+int mm_naive_unrolled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                      double *C, int64_t ldc, int32_t unroll, void *stream) {
+    if (unroll < 1 || unroll > 4) return fail(MM_ERR_ARG, "mm_naive_unrolled: unroll must be 1, 2, 3 or 4 (got %d)", unroll);
+    int rc = check_gemm_args("mm_naive_unrolled", N, P, M, A, lda, B, ldb, C, ldc);
+    if (rc) return rc;
+    if (N == 0 || M == 0) return MM_OK;
+    if (P == 0) return run_zero(N, M, C, ldc, (cudaStream_t)stream);
+    return run_unrolled(N, P, M, A, lda, B, ldb, C, ldc, unroll, (cudaStream_t)stream);
+}
+
 int mm_kahan(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
              int64_t ldc, void *stream) {
     int rc = check_gemm_args("mm_kahan", N, P, M, A, lda, B, ldb, C, ldc);

@@ -69,6 +69,8 @@ int run_norm_inf(int64_t N, int64_t P, const double *A, int64_t lda, double *out
 int run_zero(int64_t N, int64_t M, double *C, int64_t ldc, cudaStream_t st);
 int run_naive(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
               int64_t ldc, cudaStream_t st);
+int run_unrolled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                 double *C, int64_t ldc, int unroll, cudaStream_t st);
 int run_kahan(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
               int64_t ldc, cudaStream_t st);
 // mode: 0 WinogradOriginal, 1 Brent's global lambda, 2 per-row/column exponents.

@@ -124,6 +124,43 @@ def test_winograd_scaled_paper_tie(mm, orc):
     assert np.array_equal(host(mm.winograd_scaled(dev(ai), dev(bi))), ai @ bi)
 
 
+# ------------------------------------------- NaivOnArray, loop unrolling
+
+@pytest.mark.parametrize("u", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", SHAPES + [(70, 97, 45), (33, 1001, 65)])
+def test_naive_unrolled_bit_exact_on_reals(mm, orc, shape, u):
+    """Every product and sum rounded on its own, in the paper's grouping: the
+    GPU result equals the sequential CPU one bit for bit (P mod u = 0..3)."""
+    a, b = pair(*shape, "log", 30 + u)
+    got = host(mm.naive_unrolled(dev(a), dev(b), unroll=u))
+    assert np.array_equal(got, orc.naiv_unrolled(a, b, u))
+    if u == 1:
+        assert np.array_equal(got, orc.naiv_on_array(a, b))
+
+
+def test_naive_unrolled_discriminator(mm):
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_pins.json")))
+    for case in g["loop_unrolling_discriminator"]["cases"]:
+        a = np.array([case["row"]])
+        b = np.ones((a.shape[1], 1))
+        assert host(mm.naive_unrolled(dev(a), dev(b), unroll=1))[0, 0] == case["naive"]
+        for u in (2, 3, 4):
+            assert host(mm.naive_unrolled(dev(a), dev(b), unroll=u))[0, 0] == case[f"u{u}"]
+
+
+def test_naive_unrolled_rejects_bad_factor(mm):
+    import torch
+
+    a = torch.ones((4, 4), dtype=torch.float64, device="cuda")
+    c = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
+    for u in (0, 5, -1):
+        rc = mm.lib().mm_naive_unrolled(4, 4, 4, a.data_ptr(), 4, a.data_ptr(), 4, c.data_ptr(), 4, u, None)
+        assert rc == -1
+
+
 # ---------------------------------------- per-row/column scaled Winograd
 
 @pytest.mark.parametrize("shape", SHAPES + [(33, 2047 % 97, 40)])
@@ -310,8 +347,8 @@ def test_emulated_group_rejects_overlapping_outputs(mm):
 
 # ------------------------------------------------------------ edge cases
 
-@pytest.mark.parametrize("name", ["naive", "kahan", "winograd", "winograd_scaled", "winograd_rowcol_scaled",
-                                  "strassen", "strassen_winograd", "emulated"])
+@pytest.mark.parametrize("name", ["naive", "naive_unrolled", "kahan", "winograd", "winograd_scaled",
+                                  "winograd_rowcol_scaled", "strassen", "strassen_winograd", "emulated"])
 def test_degenerate_shapes(mm, name):
     import torch
 
