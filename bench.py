@@ -244,7 +244,8 @@ def timed(fn, reps):
 
 
 def slice_sweep(ta, tb, a, b, norm_a, norm_b, rows, truth):
-    """The emulated product at the bench shape for every BF16 slice count 3..8:
+    """The emulated product at the bench shape for every slice count 3..8, with
+    BF16 slices (beta = 7) and FP8-E4M3 slices (beta = 5, kind::f8f6f4):
     FP64-equivalent TFLOP/s (2NPM / t) and the sampled normwise error."""
     import torch
 
@@ -253,11 +254,14 @@ def slice_sweep(ta, tb, a, b, norm_a, norm_b, rows, truth):
     n, p, m = a.shape[0], a.shape[1], b.shape[1]
     c = torch.empty((n, m), dtype=torch.float64, device=ta.device)
     out = {}
-    for s in range(3, 9):
-        ms = timed(lambda: mm.emulated(ta, tb, nslices=s, out=c), 3)
-        out[str(s)] = {"ms": ms, "tflops": 2.0 * n * p * m / (ms * 1e-3) / 1e12,
-                       "slice_pairs": s * (s + 1) // 2,
-                       "rel_inf_err_sampled": sampled_error(c, a, b, norm_a, norm_b, rows, truth)}
+    for kind, label in ((mm.SLICE_BF16, "bf16"), (mm.SLICE_FP8E4M3, "fp8_e4m3")):
+        res = {}
+        for s in range(3, 9):
+            ms = timed(lambda: mm.emulated(ta, tb, nslices=s, kind=kind, out=c), 3)
+            res[str(s)] = {"ms": ms, "tflops": 2.0 * n * p * m / (ms * 1e-3) / 1e12,
+                           "slice_pairs": s * (s + 1) // 2,
+                           "rel_inf_err_sampled": sampled_error(c, a, b, norm_a, norm_b, rows, truth)}
+        out[label] = res
     return out
 
 

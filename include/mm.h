@@ -192,17 +192,22 @@ int mm_tune_clear(void);
  * per-row/per-column power-of-two scaling generalises section
  * "WinogradScaled").  Each row i of A is scaled by 2^-e_i (e_i the frexp
  * exponent of max_k |A_ik|), rounded to an integer V_ik with beta*s - 1 bits
- * and cut into s balanced base-2^beta digits stored as BF16 (beta = 7); B is
- * split per column the same way.  The slice pairs (sigma, tau) with
- * sigma + tau <= s - 1 are multiplied on tcgen05 with FP32 accumulation in
- * TMEM, drained every K-chunk while every partial sum is an exact integer
- * below 2^24, accumulated exactly in integers, and rounded once to double
- * with the 2^(e_i + f_j) scaling.  The result equals, bit for bit,
- * RN(sum of the kept digit products) scaled -- see the oracle's definition.
- *   kind:     MM_SLICE_BF16 (MM_SLICE_FP8E4M3 returns MM_ERR_UNSUPPORTED);
- *   nslices:  1..8, or 0 to choose from `tier`;
+ * and cut into s balanced base-2^beta digits; B is split per column the same
+ * way.  The slice pairs (sigma, tau) with sigma + tau <= s - 1 are multiplied
+ * on tcgen05 with FP32 accumulation in TMEM, read out before any partial sum
+ * can leave the integers FP32 holds exactly (|x| <= 2^24), accumulated exactly
+ * in integers, and rounded once to double with the 2^(e_i + f_j) scaling.
+ * The result equals, bit for bit, RN(sum of the kept digit products) scaled --
+ * see the oracle's definition.
+ *   kind:     MM_SLICE_BF16 (beta = 7, digits |d| <= 64, kind::f16 MMA) or
+ *             MM_SLICE_FP8E4M3 (beta = 5, digits |d| <= 16, kind::f8f6f4 MMA at
+ *             twice the rate per pair); anything else returns MM_ERR_ARG;
+ *   nslices:  1..8, or 0 to choose from `tier`: s = ceil((log2(1/tier) + 9) / beta);
  *   tier:     target ||C - AB||_inf / (||A||_inf ||B||_inf) when nslices == 0
- *             (<= 1e-14 selects 8 slices).
+ *             (<= 1e-14 selects 8 BF16 slices; FP8 reaches tiers down to about
+ *             1e-9 -- a tier that needs more than 8 slices returns
+ *             MM_ERR_UNSUPPORTED, because the kernel keeps one 64-column TMEM
+ *             accumulator per diagonal and TMEM holds 8).
  * Requires N, M >= 1 and P <= 2^20 (larger P returns MM_ERR_UNSUPPORTED).
  */
 size_t mm_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t kind, int32_t nslices, double tier);

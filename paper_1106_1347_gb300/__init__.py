@@ -177,7 +177,7 @@ def emulated_slices(nslices=0, tier=1e-14, kind=SLICE_BF16):
 
 
 def emulated(a, b, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
-    """FP64-accurate product from BF16 slices on tcgen05 (see include/mm.h)."""
+    """FP64-accurate product from BF16 or FP8-E4M3 slices on tcgen05 (see include/mm.h)."""
     a, b, c, n, p, m = _prep(a, b, out)
     need = lib().mm_emulated_workspace_bytes(n, p, m, kind, nslices, tier)
     ws = _ws(need, a.device)

@@ -305,7 +305,21 @@ int mm_emulated_slices(int32_t kind, int32_t nslices, double tier) { return emul
 size_t mm_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t kind, int32_t nslices, double tier) {
     int s = emulated_slices(kind, nslices, tier);
     if (s <= 0 || N < 0 || P < 0 || M < 0) return 0;
-    return emulated_ws_bytes(N, P, M, s);
+    return emulated_ws_bytes(N, P, M, s, kind);
+}
+
+// Slice count of a request, or the failure (with its message) when the format,
+// the count or the tier is invalid or the tier needs more than 8 slices.
+static int slices_or_fail(const char *fn, int32_t kind, int32_t nslices, double tier) {
+    if (kind != MM_SLICE_BF16 && kind != MM_SLICE_FP8E4M3) return fail(MM_ERR_ARG, "%s: unknown slice kind %d", fn, kind);
+    if (nslices < 0 || nslices > 8) return fail(MM_ERR_ARG, "%s: nslices must be 0..8", fn);
+    if (nslices == 0 && !(tier > 0.0)) return fail(MM_ERR_ARG, "%s: tier must be > 0 when nslices == 0", fn);
+    const int s = emulated_slices(kind, nslices, tier);
+    if (s == MM_ERR_UNSUPPORTED)
+        return fail(MM_ERR_UNSUPPORTED, "%s: tier %g needs more than 8 %s slices", fn, tier,
+                    kind == MM_SLICE_FP8E4M3 ? "FP8-E4M3" : "BF16");
+    if (s <= 0) return fail(MM_ERR_ARG, "%s: invalid slice request", fn);
+    return s;
 }
 
 int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
@@ -313,19 +327,16 @@ int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, c
                 void *stream) {
     int rc = check_gemm_args("mm_emulated", N, P, M, A, lda, B, ldb, C, ldc);
     if (rc) return rc;
-    if (kind == MM_SLICE_FP8E4M3) return fail(MM_ERR_UNSUPPORTED, "mm_emulated: FP8-E4M3 slices are not built");
-    if (kind != MM_SLICE_BF16) return fail(MM_ERR_ARG, "mm_emulated: unknown slice kind %d", kind);
-    if (nslices < 0 || nslices > 8) return fail(MM_ERR_ARG, "mm_emulated: nslices must be 0..8");
-    if (nslices == 0 && !(tier > 0.0)) return fail(MM_ERR_ARG, "mm_emulated: tier must be > 0 when nslices == 0");
+    const int s = slices_or_fail("mm_emulated", kind, nslices, tier);
+    if (s < 0) return s;
     if (P > (int64_t(1) << 20)) return fail(MM_ERR_UNSUPPORTED, "mm_emulated: P > 2^20");
-    int s = emulated_slices(kind, nslices, tier);
     cudaStream_t st = (cudaStream_t)stream;
     if (N == 0 || M == 0) return MM_OK;
     if (P == 0) return run_zero(N, M, C, ldc, st);
-    size_t need = emulated_ws_bytes(N, P, M, s);
+    size_t need = emulated_ws_bytes(N, P, M, s, kind);
     if (ws_bytes < need || !ws)
         return fail(MM_ERR_WORKSPACE, "mm_emulated: workspace %zu bytes < %zu required", ws_bytes, need);
-    return run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, ws, st);
+    return run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st);
 }
 
 int mm_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
@@ -333,17 +344,13 @@ int mm_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_
                         void *stream) {
     int rc = check_gemm_args("mm_emulated_noalloc", N, P, M, A, lda, B, ldb, C, ldc);
     if (rc) return rc;
-    if (kind == MM_SLICE_FP8E4M3)
-        return fail(MM_ERR_UNSUPPORTED, "mm_emulated_noalloc: FP8-E4M3 slices are not built");
-    if (kind != MM_SLICE_BF16) return fail(MM_ERR_ARG, "mm_emulated_noalloc: unknown slice kind %d", kind);
-    if (nslices < 0 || nslices > 8) return fail(MM_ERR_ARG, "mm_emulated_noalloc: nslices must be 0..8");
-    if (nslices == 0 && !(tier > 0.0))
-        return fail(MM_ERR_ARG, "mm_emulated_noalloc: tier must be > 0 when nslices == 0");
-    const int s = emulated_slices(kind, nslices, tier);
+    const int s = slices_or_fail("mm_emulated_noalloc", kind, nslices, tier);
+    if (s < 0) return s;
+    if (P > (int64_t(1) << 20)) return fail(MM_ERR_UNSUPPORTED, "mm_emulated_noalloc: P > 2^20");
     cudaStream_t st = (cudaStream_t)stream;
     if (N == 0 || M == 0) return MM_OK;
     if (P == 0) return run_zero(N, M, C, ldc, st);
-    return run_emulated_noalloc(N, P, M, A, lda, B, ldb, C, ldc, s, st);
+    return run_emulated_noalloc(N, P, M, A, lda, B, ldb, C, ldc, s, kind, st);
 }
 
 size_t mm_emulated_noalloc_capacity(void) { return emulated_noalloc_capacity(); }
@@ -351,10 +358,8 @@ size_t mm_emulated_noalloc_capacity(void) { return emulated_noalloc_capacity(); 
 static int check_group(const char *fn, const mm_problem *probs, int32_t count, int32_t kind, int32_t nslices,
                        double tier) {
     if (count < 0 || (count > 0 && !probs)) return fail(MM_ERR_ARG, "%s: bad problem list", fn);
-    if (kind == MM_SLICE_FP8E4M3) return fail(MM_ERR_UNSUPPORTED, "%s: FP8-E4M3 slices are not built", fn);
-    if (kind != MM_SLICE_BF16) return fail(MM_ERR_ARG, "%s: unknown slice kind %d", fn, kind);
-    if (nslices < 0 || nslices > 8) return fail(MM_ERR_ARG, "%s: nslices must be 0..8", fn);
-    if (nslices == 0 && !(tier > 0.0)) return fail(MM_ERR_ARG, "%s: tier must be > 0 when nslices == 0", fn);
+    const int s = slices_or_fail(fn, kind, nslices, tier);
+    if (s < 0) return s;
     for (int32_t i = 0; i < count; ++i) {
         const mm_problem &q = probs[i];
         int rc = check_gemm_args(fn, q.N, q.P, q.M, q.A, q.lda, q.B, q.ldb, q.C, q.ldc);
@@ -374,7 +379,7 @@ size_t mm_emulated_group_workspace_bytes(const mm_problem *probs, int32_t count,
                                          double tier) {
     const int s = emulated_slices(kind, nslices, tier);
     if (s <= 0 || count <= 0 || !probs) return 0;
-    return emulated_group_ws_bytes(probs, count, s);
+    return emulated_group_ws_bytes(probs, count, s, kind);
 }
 
 int mm_emulated_group(const mm_problem *probs, int32_t count, int32_t kind, int32_t nslices, double tier, void *ws,
@@ -383,10 +388,10 @@ int mm_emulated_group(const mm_problem *probs, int32_t count, int32_t kind, int3
     if (rc) return rc;
     if (count == 0) return MM_OK;
     const int s = emulated_slices(kind, nslices, tier);
-    const size_t need = emulated_group_ws_bytes(probs, count, s);
+    const size_t need = emulated_group_ws_bytes(probs, count, s, kind);
     if (ws_bytes < need || !ws)
         return fail(MM_ERR_WORKSPACE, "mm_emulated_group: workspace %zu bytes < %zu required", ws_bytes, need);
-    return run_emulated_group(probs, count, s, ws, (cudaStream_t)stream);
+    return run_emulated_group(probs, count, s, kind, ws, (cudaStream_t)stream);
 }
 
 int mm_profile_enable(int on) {

@@ -85,10 +85,11 @@ int run_strassen(int variant, int64_t N, int64_t P, int64_t M, const double *A, 
                  int64_t ldb, double *C, int64_t ldc, int depth, int64_t Np, int64_t Pp, int64_t Mp, void *ws,
                  cudaStream_t st);
 int emulated_slices(int32_t kind, int32_t nslices, double tier);
-size_t emulated_ws_bytes(int64_t N, int64_t P, int64_t M, int s);
+// kind: MM_SLICE_BF16 or MM_SLICE_FP8E4M3.
+size_t emulated_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind);
 int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
-                 double *C, int64_t ldc, int s, void *ws, cudaStream_t st);
-size_t emulated_group_ws_bytes(const mm_problem *probs, int count, int s);
+                 double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st);
+size_t emulated_group_ws_bytes(const mm_problem *probs, int count, int s, int kind);
 
 // Pieces of a grouped emulated launch, for runtimes that place the table part
 // (problem table, header, prefix arrays) and the data part (column maxima,
@@ -97,19 +98,19 @@ struct GroupLaunch {
     const void *tab, *hdr;    // device table and header (table part)
     const int64_t *begin[5];  // device prefix arrays
     int64_t grid[5];          // CTAs per kernel; may be raised to upper bounds
-    int s;
+    int s, kind;              // slice count and format
 };
 size_t group_table_bytes(int count);
-size_t problem_data_bytes(const mm_problem &q, int s);
-size_t group_data_bytes(const mm_problem *probs, int count, int s);
+size_t problem_data_bytes(const mm_problem &q, int s, int kind = MM_SLICE_BF16);
+size_t group_data_bytes(const mm_problem *probs, int count, int s, int kind = MM_SLICE_BF16);
 int group_build(const mm_problem *probs, int count, int capacity, int s, void *table_dev, char *const *data,
-                std::vector<unsigned char> &image, GroupLaunch &gl);
+                std::vector<unsigned char> &image, GroupLaunch &gl, int kind = MM_SLICE_BF16);
 int group_kernels(const GroupLaunch &gl, cudaStream_t st);
 void prof_suspend(bool on);  // skip kernel timing while a stream is being captured
-int run_emulated_group(const mm_problem *probs, int count, int s, void *ws, cudaStream_t st);
+int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void *ws, cudaStream_t st);
 size_t emulated_noalloc_capacity();
 int run_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
-                         int64_t ldb, double *C, int64_t ldc, int s, cudaStream_t st);
+                         int64_t ldb, double *C, int64_t ldc, int s, int kind, cudaStream_t st);
 
 }  // namespace mm
 
@@ -213,6 +214,17 @@ __device__ __forceinline__ void mma_bf16_elect(uint32_t d_tmem, uint64_t adesc, 
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// The same for kind::f8f6f4 with E4M3 A and B (K = 32 per instruction).
+__device__ __forceinline__ void mma_e4m3_elect(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred e, p;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 // Arrive once on `bar` when every tcgen05.mma issued so far by the warp's
 // elected lane completes.  Called by a whole converged warp.
 __device__ __forceinline__ void mma_commit_elect(uint64_t *bar) {
@@ -258,6 +270,11 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) { return smem
 // bits 24-28.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+// kind::f8f6f4: FP32 accumulator, A and B E4M3 (format code 0 in bits 7-9 and
+// 10-12), both K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(uint32_t M, uint32_t N) {
+    return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
 }  // namespace mmdev

@@ -33,6 +33,7 @@
 // Every mbarrier wait is bounded; on timeout the kernel raises the device
 // status word, waits (bounded) for its own copies and MMAs, frees TMEM and exits.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <mutex>
 #include <vector>
@@ -41,8 +42,20 @@
 
 namespace {
 
-constexpr int kBeta = 7;
-constexpr int BM = 128, BN = 64, BKE = 32;  // tile rows, tile cols, K-block (bf16: 64 bytes)
+constexpr int BM = 128, BN = 64;  // output tile rows and columns
+constexpr int KB_BYTES = 64;       // one K-block of one slice row: 32 BF16 or 64 FP8 values
+
+// Slice formats.  BF16 holds balanced base-2^7 digits (|d| <= 64, 8-bit
+// significand); FP8-E4M3 holds balanced base-2^5 digits (|d| <= 16: every
+// integer up to 16 in magnitude has at most 4 significant bits).
+__host__ __device__ constexpr int fmt_beta(int kind) { return kind == MM_SLICE_FP8E4M3 ? 5 : 7; }
+__host__ __device__ constexpr int fmt_esize(int kind) { return kind == MM_SLICE_FP8E4M3 ? 1 : 2; }
+__host__ __device__ constexpr int fmt_bke(int kind) { return KB_BYTES / fmt_esize(kind); }
+// K-blocks over which one slice pair's products (each at most 2^(2 beta - 2) in
+// magnitude) sum to an integer FP32 holds exactly (<= 2^24).
+__host__ __device__ constexpr int fmt_pair_blocks(int kind) {
+    return (1 << (26 - 2 * fmt_beta(kind))) / fmt_bke(kind);
+}
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kSmemLimit = 232448;  // opt-in dynamic shared memory per block on sm_103
@@ -91,31 +104,50 @@ __device__ __forceinline__ int64_t round_scaled(double x, int sh) {
     return neg ? -(int64_t)q : (int64_t)q;
 }
 
-// Balanced base-2^7 digits, most significant first: dig[0] is the top digit.
-__device__ __forceinline__ void balanced_digits(int64_t V, int s, int (&dig)[8]) {
+// Balanced base-2^beta digits, most significant first: dig[0] is the top digit.
+__device__ __forceinline__ void balanced_digits(int64_t V, int s, int beta, int (&dig)[8]) {
+    const int base = 1 << beta, half = base >> 1;
 #pragma unroll
     for (int t = 0; t < 7; ++t) {
         if (t < s - 1) {
-            int d = (int)(V & 127);
-            if (d >= 64) d -= 128;
+            int d = (int)(V & (base - 1));
+            if (d >= half) d -= base;
             dig[s - 1 - t] = d;
-            V = (V - d) >> 7;
+            V = (V - d) >> beta;
         }
     }
     dig[0] = (int)V;
+}
+
+// Two digits stored side by side in a slice row (element size 2 or 1 bytes).
+__device__ __forceinline__ void store_digit_pair(unsigned char *dst, int d0, int d1, int kind) {
+    if (kind == MM_SLICE_FP8E4M3) {
+        const uint16_t lo = __nv_cvt_float_to_fp8((float)d0, __NV_SATFINITE, __NV_E4M3);
+        const uint16_t hi = __nv_cvt_float_to_fp8((float)d1, __NV_SATFINITE, __NV_E4M3);
+        *reinterpret_cast<uint16_t *>(dst) = (uint16_t)(lo | (hi << 8));
+    } else {
+        *reinterpret_cast<__nv_bfloat162 *>(dst) = __floats2bfloat162_rn((float)d0, (float)d1);
+    }
+}
+__device__ __forceinline__ void store_digit(unsigned char *dst, int d, int kind) {
+    if (kind == MM_SLICE_FP8E4M3)
+        *dst = (unsigned char)__nv_cvt_float_to_fp8((float)d, __NV_SATFINITE, __NV_E4M3);
+    else
+        *reinterpret_cast<__nv_bfloat16 *>(dst) = __float2bfloat16_rn((float)d);
 }
 
 // Everything one split of A needs (one problem).
 struct SplitA {
     int64_t N, P, lda, Nr, Pp;
     const double *A;
-    int s;
+    int s, kind;
     int32_t *ea;
-    __nv_bfloat16 *slices;
+    unsigned char *slices;  // [s][Nr][Pp] elements of the slice format
 };
 
 // One warp per row of A: max |A_ik| by integer max on the bit patterns, then
-// the digits, written as BF16 slices [s][Nr][Pp].
+// the digits, written as slices [s][Nr][Pp] (BF16 or FP8-E4M3).
+template <int KIND>
 __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int lane) {
     const double *a = p.A + row * p.lda;
     const int64_t P = p.P, Pp = p.Pp;
@@ -127,39 +159,40 @@ __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int lane
         mx = umax64(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mx, o));
     const int e = frexp_exp_bits(mx);
     if (lane == 0) p.ea[row] = e;
-    const int sh = kBeta * s - 1 - e;
+    constexpr int beta = fmt_beta(KIND), es = fmt_esize(KIND);
+    const int sh = beta * s - 1 - e;
     // Columns [P, Pp) are written as zero digits so every K-block read stays defined.
     for (int64_t c0 = 0; c0 < Pp; c0 += 64) {
         const int64_t c = c0 + 2 * lane;
         if (c >= Pp) break;
         int d0[8], d1[8];
-        balanced_digits(c < P ? round_scaled(a[c], sh) : 0, s, d0);
+        balanced_digits(c < P ? round_scaled(a[c], sh) : 0, s, beta, d0);
         const bool two = c + 1 < Pp;
-        balanced_digits((two && c + 1 < P) ? round_scaled(a[c + 1], sh) : 0, s, d1);
+        balanced_digits((two && c + 1 < P) ? round_scaled(a[c + 1], sh) : 0, s, beta, d1);
         for (int t = 0; t < s; ++t) {
-            __nv_bfloat16 *dst = p.slices + ((int64_t)t * p.Nr + row) * Pp + c;
-            if (two) {
-                *reinterpret_cast<__nv_bfloat162 *>(dst) = __floats2bfloat162_rn((float)d0[t], (float)d1[t]);
-            } else {
-                dst[0] = __float2bfloat16_rn((float)d0[t]);
-            }
+            unsigned char *dst = p.slices + (((int64_t)t * p.Nr + row) * Pp + c) * es;
+            if (two)
+                store_digit_pair(dst, d0[t], d1[t], KIND);
+            else
+                store_digit(dst, d0[t], KIND);
         }
     }
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(256) split_rows_kernel(const SplitA p) {
     const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (row < p.N) split_row(p, row, threadIdx.x & 31);
+    if (row < p.N) split_row<KIND>(p, row, threadIdx.x & 31);
 }
 
 // Everything the column split of B needs (one problem).
 struct SplitB {
     int64_t P, M, ldb, Mr, Pp;
     const double *B;
-    int s;
+    int s, kind;
     unsigned long long *colmax;  // zeroed before col_max runs
     int32_t *fb;
-    __nv_bfloat16 *slices;
+    unsigned char *slices;  // [s][Mr][Pp] elements of the slice format
 };
 
 // Column maxima of rows [k0, k0 + 256) folded into colmax with atomicMax on the bits.
@@ -179,7 +212,8 @@ constexpr int SC_K = 32, SC_J = 64;
 
 // A 32 (k) x 64 (j) tile of B: digits, transposed through shared memory into
 // the K-major slices [s][Mr][Pp] (each slice row is one column of B).
-__device__ __forceinline__ void split_cols_tile(const SplitB &p, int64_t jt, int64_t kt, __nv_bfloat16 *sm) {
+template <int KIND>
+__device__ __forceinline__ void split_cols_tile(const SplitB &p, int64_t jt, int64_t kt, unsigned char *sm) {
     constexpr int LD = SC_K + 2;
     const int tid = threadIdx.x;
     const int64_t j0 = jt * SC_J, k0 = kt * SC_K;
@@ -189,17 +223,18 @@ __device__ __forceinline__ void split_cols_tile(const SplitB &p, int64_t jt, int
     const int64_t j = j0 + jj;
     const int f = (j < M) ? frexp_exp_bits(p.colmax[j]) : 0;
     if (kt == 0 && tid < 64 && j < M) p.fb[j] = f;
-    const int sh = kBeta * s - 1 - f;
+    constexpr int beta = fmt_beta(KIND), es = fmt_esize(KIND);
+    const int sh = beta * s - 1 - f;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int kk = (tid >> 6) + 4 * r;
         const int64_t k = k0 + kk;
         int dig[8];
-        balanced_digits((k < P && j < M) ? round_scaled(p.B[k * p.ldb + j], sh) : 0, s, dig);
-        for (int t = 0; t < s; ++t) sm[(t * SC_J + jj) * LD + kk] = __float2bfloat16_rn((float)dig[t]);
+        balanced_digits((k < P && j < M) ? round_scaled(p.B[k * p.ldb + j], sh) : 0, s, beta, dig);
+        for (int t = 0; t < s; ++t) store_digit(sm + ((t * SC_J + jj) * LD + kk) * es, dig[t], KIND);
     }
     __syncthreads();
-    // Write each slice's 64 columns x 32 k as K-major rows (16 threads per 64-byte row).
+    // Write each slice's 64 columns x 32 k as K-major rows (16 threads per row, two digits each).
     for (int t = 0; t < s; ++t) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -207,28 +242,30 @@ __device__ __forceinline__ void split_cols_tile(const SplitB &p, int64_t jt, int
             const int jr = w >> 4, kp = (w & 15) * 2;
             const int64_t gj = j0 + jr, gk = k0 + kp;
             if (gj >= M || gk >= Pp) continue;  // [P, Pp) receives zero digits
-            const __nv_bfloat16 *src = sm + (t * SC_J + jr) * LD + kp;
-            __nv_bfloat16 *dst = p.slices + ((int64_t)t * p.Mr + gj) * Pp + gk;
+            const unsigned char *src = sm + ((t * SC_J + jr) * LD + kp) * es;
+            unsigned char *dst = p.slices + (((int64_t)t * p.Mr + gj) * Pp + gk) * es;
             if (gk + 1 < Pp) {
-                __nv_bfloat162 v;
-                v.x = src[0];
-                v.y = src[1];
-                *reinterpret_cast<__nv_bfloat162 *>(dst) = v;
+                if (es == 2)
+                    *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(src);
+                else
+                    *reinterpret_cast<uint16_t *>(dst) = *reinterpret_cast<const uint16_t *>(src);
             } else {
-                dst[0] = src[0];
+                for (int b = 0; b < es; ++b) dst[b] = src[b];
             }
         }
     }
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(256) split_cols_kernel(const SplitB p) {
-    extern __shared__ __align__(16) __nv_bfloat16 sm[];  // [s][SC_J][SC_K + 2]
-    split_cols_tile(p, blockIdx.x, blockIdx.y, sm);
+    extern __shared__ __align__(16) unsigned char sm[];  // [s][SC_J][SC_K + 2] elements
+    split_cols_tile<KIND>(p, blockIdx.x, blockIdx.y, sm);
 }
 
 struct EmuParams {
     int64_t N, P, M;
     int s, stages, chunk_blocks, hsplit, tmem_cols;
+    int kind, beta, bke, pair_blocks;  // slice format, K-block in elements, exact K-blocks of one pair
     int tiles_m, tiles_n;
     const int32_t *ea, *fb;
     double *C;
@@ -272,15 +309,15 @@ __device__ __forceinline__ void tile_of(int64_t id, int tiles_m, int tiles_n, in
 }
 
 // Accumulator d holds d + 1 slice pairs, so its exact length is
-// L_d = 2^12 / (BKE (d + 1)) K-blocks, a whole number r_d = floor(L_d / CB) of
+// L_d = pair_blocks / (d + 1) K-blocks, a whole number r_d = floor(L_d / CB) of
 // chunks of CB = L_(s-1) K-blocks: at each chunk end only the accumulators
 // whose r_d chunks are complete are read out (plus all of them at the tile's
 // last chunk), which cuts the TMEM traffic of the drains by a third for 8
 // slices.  The countdowns live in one register, 4 bits per diagonal.
-__device__ __forceinline__ uint32_t drain_periods(int CB) {
+__device__ __forceinline__ uint32_t drain_periods(int CB, int pair_blocks) {
     uint32_t R = 0;
 #pragma unroll
-    for (int d = 0; d < 8; ++d) R |= (uint32_t)(max(1, (4096 / BKE / (d + 1)) / CB) - 1) << (4 * d);
+    for (int d = 0; d < 8; ++d) R |= (uint32_t)(min(16, max(1, (pair_blocks / (d + 1)) / CB)) - 1) << (4 * d);
     return R;
 }
 // Diagonals due at this chunk end; advances the countdowns.
@@ -313,7 +350,7 @@ struct TileJob {
 // soon as the epilogue has read the accumulators out -- the final rounding and
 // the stores of C overlap them.  `c` holds the launch-wide constants (slice
 // count, stages, chunk, TMEM columns).
-template <class Tiles>
+template <bool kFP8, class Tiles>
 __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, const EmuParams &c,
                                             bool maps_in_global) {
     extern __shared__ uint8_t smem_raw[];
@@ -321,8 +358,10 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
     __shared__ uint32_t tmem_slot;
     if ((int64_t)blockIdx.x >= total) return;  // whole CTA, before any barrier
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int KIND = kFP8 ? MM_SLICE_FP8E4M3 : MM_SLICE_BF16;
+    constexpr int bke = fmt_bke(KIND), pair_blocks = fmt_pair_blocks(KIND);
     const int s = c.s, S = c.stages, CB = c.chunk_blocks;
-    const uint32_t a_bytes = (uint32_t)s * BM * BKE * 2, b_bytes = (uint32_t)s * BN * BKE * 2;
+    const uint32_t a_bytes = (uint32_t)s * BM * KB_BYTES, b_bytes = (uint32_t)s * BN * KB_BYTES;
     const uint32_t stage_bytes = a_bytes + b_bytes;
     uint64_t *full = bars, *empty = bars + 8, *acc_full = bars + 16, *acc_empty = bars + 17, *mma_done = bars + 18;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -359,7 +398,7 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                 }
                 mmdev::prefetch_tmap(j.tmA);
                 mmdev::prefetch_tmap(j.tmB);
-                const int nkb = (int)((j.p.P + BKE - 1) / BKE);
+                const int nkb = (int)((j.p.P + bke - 1) / bke);
                 const int32_t m0 = j.tm * BM, n0 = j.tn * BN;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const uint32_t st = it % S, use = it / S;
@@ -370,8 +409,8 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                     }
                     uint8_t *sa = smem + (size_t)st * stage_bytes;
                     mmdev::mbar_arrive_expect_tx(&full[st], stage_bytes);
-                    mmdev::tma_load_3d(sa, j.tmA, &full[st], kb * BKE, m0, 0);
-                    mmdev::tma_load_3d(sa + a_bytes, j.tmB, &full[st], kb * BKE, n0, 0);
+                    mmdev::tma_load_3d(sa, j.tmA, &full[st], kb * bke, m0, 0);
+                    mmdev::tma_load_3d(sa + a_bytes, j.tmB, &full[st], kb * bke, n0, 0);
                 }
             }
             // Wait (bounded) for the last load into each stage, so no copy is in flight at exit.
@@ -383,14 +422,14 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
         // elected lane.  Descriptors are the stage's base descriptors plus
         // compile-time offsets (the start-address field cannot carry: shared
         // addresses stay below 2^18).
-        const uint32_t idesc = mmdev::idesc_bf16_f32(BM, BN);
-        const uint32_t R = drain_periods(CB);
+        const uint32_t idesc = kFP8 ? mmdev::idesc_e4m3_f32(BM, BN) : mmdev::idesc_bf16_f32(BM, BN);
+        const uint32_t R = drain_periods(CB, pair_blocks);
         uint32_t it = 0, ev = 0;  // K-blocks consumed and chunks handed to the epilogue, over all tiles
         bool ok = true;
         for (int64_t id = blockIdx.x; id < total && ok; id += gridDim.x) {
             TileJob j;
             tiles.get(id, j);
-            const int nkb = (int)((j.p.P + BKE - 1) / BKE);
+            const int nkb = (int)((j.p.P + bke - 1) / bke);
             int kin = 0;                // K-block within the current exact chunk
             uint32_t cnt = R, fresh = 0xffu;  // accumulators that start over at the next chunk
             for (int kb = 0; kb < nkb; ++kb, ++it) {
@@ -413,10 +452,13 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                         for (int sg = 0; sg <= d; ++sg) {
 #pragma unroll
                             for (int kk = 0; kk < 2; ++kk) {
-                                const uint64_t ad = da + (uint64_t)((sg * (BM * BKE * 2) + kk * 32) >> 4);
-                                const uint64_t bd = db + (uint64_t)(((d - sg) * (BN * BKE * 2) + kk * 32) >> 4);
-                                mmdev::mma_bf16_elect(tmem + (uint32_t)(d * BN), ad, bd, idesc,
-                                                      (sg == 0 && kk == 0) ? first : 1u);
+                                const uint64_t ad = da + (uint64_t)((sg * (BM * KB_BYTES) + kk * 32) >> 4);
+                                const uint64_t bd = db + (uint64_t)(((d - sg) * (BN * KB_BYTES) + kk * 32) >> 4);
+                                const uint32_t acc = (sg == 0 && kk == 0) ? first : 1u;
+                                if (kFP8)
+                                    mmdev::mma_e4m3_elect(tmem + (uint32_t)(d * BN), ad, bd, idesc, acc);
+                                else
+                                    mmdev::mma_bf16_elect(tmem + (uint32_t)(d * BN), ad, bd, idesc, acc);
                             }
                         }
                     }
@@ -440,13 +482,14 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
         uint32_t ev = 0;
         bool ok = true;
         const int hsplit = c.hsplit;
-        const uint32_t R = drain_periods(CB);
+        constexpr int beta = fmt_beta(KIND);
+        const uint32_t R = drain_periods(CB, pair_blocks);
         for (int64_t id = blockIdx.x; id < total && ok; id += gridDim.x) {
             int nchunks;
             {
                 TileJob j;
                 tiles.get(id, j);
-                nchunks = ((int)((j.p.P + BKE - 1) / BKE) + CB - 1) / CB;
+                nchunks = ((int)((j.p.P + bke - 1) / bke) + CB - 1) / CB;
             }
             int64_t whi[32], wlo[32];
 #pragma unroll
@@ -466,11 +509,11 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                     mmdev::tmem_ld_32x32b_x32(tbase + (uint32_t)(d * BN), v);
                     mmdev::tmem_wait_ld();
                     if (d < hsplit) {
-                        const int sh = kBeta * (hsplit - 1 - d);
+                        const int sh = beta * (hsplit - 1 - d);
 #pragma unroll
                         for (int k = 0; k < 32; ++k) whi[k] += (int64_t)__float2int_rn(__uint_as_float(v[k])) << sh;
                     } else {
-                        const int sh = kBeta * (s - 1 - d);
+                        const int sh = beta * (s - 1 - d);
 #pragma unroll
                         for (int k = 0; k < 32; ++k) wlo[k] += (int64_t)__float2int_rn(__uint_as_float(v[k])) << sh;
                     }
@@ -487,7 +530,7 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
             const int64_t row = (int64_t)j.tm * BM + 32 * q + lane, n0 = (int64_t)j.tn * BN;
             if (ok && row < p.N) {
                 const int e = p.ea[row];
-                const int sh2 = kBeta * (s - hsplit);
+                const int sh2 = beta * (s - hsplit);
                 double *crow = p.C + row * p.ldc;
 #pragma unroll
                 for (int k = 0; k < 32; k += 2) {
@@ -503,7 +546,7 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                         hi += (wl >> 63) + (lo2 < lo ? 1 : 0);
                         lo = lo2;
                         const int f = (col < p.M) ? p.fb[col] : 0;
-                        out[u] = ldexp(int128_to_double(hi, lo), e + f + 2 - kBeta * (s + 1));
+                        out[u] = ldexp(int128_to_double(hi, lo), e + f + 2 - beta * (s + 1));
                     }
                     const int64_t col = n0 + 32 * h + k;
                     double *dst = crow + col;
@@ -538,11 +581,12 @@ struct SingleTiles {
     }
 };
 
+template <bool kFP8>
 __global__ void __launch_bounds__(kThreads, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const EmuParams p) {
     const SingleTiles tiles{&tmA, &tmB, &p};
-    slice_tiles(tiles, (int64_t)p.tiles_m * p.tiles_n, p, false);
+    slice_tiles<kFP8>(tiles, (int64_t)p.tiles_m * p.tiles_n, p, false);
 }
 
 // ------------------------------------------------------------ grouped launch
@@ -590,6 +634,7 @@ __global__ void __launch_bounds__(256) group_zero_colmax_kernel(const EmuProblem
     if (j < p.M) p.colmax[j] = 0ull;
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(256) group_split_rows_kernel(const EmuProblem *tab, const int64_t *begin,
                                                                const GroupHeader *hdr) {
     const int64_t u = blockIdx.x;
@@ -597,7 +642,7 @@ __global__ void __launch_bounds__(256) group_split_rows_kernel(const EmuProblem 
     const int g = find_problem(begin, hdr->count, u);
     const SplitA &p = tab[g].spa;
     const int64_t row = (u - begin[g]) * 8 + (threadIdx.x >> 5);
-    if (row < p.N) split_row(p, row, threadIdx.x & 31);
+    if (row < p.N) split_row<KIND>(p, row, threadIdx.x & 31);
 }
 
 __global__ void __launch_bounds__(128) group_col_max_kernel(const EmuProblem *tab, const int64_t *begin,
@@ -610,15 +655,16 @@ __global__ void __launch_bounds__(128) group_col_max_kernel(const EmuProblem *ta
     col_max_part(p, (local % nj) * 128 + threadIdx.x, (local / nj) * 256);
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(256) group_split_cols_kernel(const EmuProblem *tab, const int64_t *begin,
                                                                const GroupHeader *hdr) {
-    extern __shared__ __align__(16) __nv_bfloat16 sm[];
+    extern __shared__ __align__(16) unsigned char sm[];
     const int64_t u = blockIdx.x;
     if (u >= hdr->units[U_SPLITCOLS]) return;
     const int g = find_problem(begin, hdr->count, u);
     const SplitB &p = tab[g].spb;
     const int64_t local = u - begin[g], nj = (p.M + SC_J - 1) / SC_J;
-    split_cols_tile(p, local % nj, local / nj, sm);
+    split_cols_tile<KIND>(p, local % nj, local / nj, sm);
 }
 
 struct GroupTiles {
@@ -635,13 +681,14 @@ struct GroupTiles {
     }
 };
 
+template <bool kFP8>
 __global__ void __launch_bounds__(kThreads, 1) group_slice_gemm_kernel(const EmuProblem *tab, const int64_t *begin,
                                                                        const GroupHeader *hdr) {
     const int64_t total = hdr->units[U_TILES];
     if (total <= 0) return;
     const GroupTiles tiles{tab, begin, hdr->count};
-    const EmuParams c = tab[0].prm;  // one slice count per launch: the constants are the same for every problem
-    slice_tiles(tiles, total, c, true);
+    const EmuParams c = tab[0].prm;  // one slice format and count per launch: the constants are common
+    slice_tiles<kFP8>(tiles, total, c, true);
 }
 
 cudaError_t slice_smem_attributes();
@@ -652,12 +699,15 @@ struct Layout {
     size_t off_ea, off_fb, off_colmax, off_a, off_b, total;
 };
 
-Layout layout(int64_t N, int64_t P, int64_t M, int s) {
+// Slice rows are Pp elements long: a multiple of 16 bytes (TMA strides) and at
+// least one K-block.
+Layout layout(int64_t N, int64_t P, int64_t M, int s, int kind) {
     Layout L{};
     L.s = s;
+    const int es = fmt_esize(kind), q = 16 / es;
     L.Nr = mm::ceil_div(std::max<int64_t>(N, 1), BM) * BM;
     L.Mr = mm::ceil_div(std::max<int64_t>(M, 1), BN) * BN;
-    L.Pp = std::max<int64_t>(mm::ceil_div(std::max<int64_t>(P, 1), 8) * 8, BKE);
+    L.Pp = std::max<int64_t>(mm::ceil_div(std::max<int64_t>(P, 1), q) * q, fmt_bke(kind));
     size_t o = 0;
     L.off_ea = o;
     o += mm::align_up((size_t)L.Nr * 4, 1024);
@@ -666,62 +716,100 @@ Layout layout(int64_t N, int64_t P, int64_t M, int s) {
     L.off_colmax = o;
     o += mm::align_up((size_t)L.Mr * 8, 1024);
     L.off_a = o;
-    o += mm::align_up((size_t)s * L.Nr * L.Pp * 2, 1024);
+    o += mm::align_up((size_t)s * L.Nr * L.Pp * es, 1024);
     L.off_b = o;
-    o += mm::align_up((size_t)s * L.Mr * L.Pp * 2, 1024);
+    o += mm::align_up((size_t)s * L.Mr * L.Pp * es, 1024);
     L.total = o;
     return L;
 }
 
-// Slices [s][rows][Pp] bf16; the K extent is Pp (zero-padded by the split
-// kernels), K-blocks past Pp read the TMA zero fill.
-int encode_slices(CUtensorMap *map, void *base, int64_t rows, int64_t Pp, int s, int box_rows) {
+// Slices [s][rows][Pp] of the slice format (FP8 as bytes); the K extent is Pp
+// (zero-padded by the split kernels), K-blocks past Pp read the TMA zero fill.
+int encode_slices(CUtensorMap *map, void *base, int64_t rows, int64_t Pp, int s, int box_rows, int kind) {
     mm::EncodeTiledFn enc = mm::encode_tiled_fn();
     if (!enc) return mm::fail(MM_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const int es = fmt_esize(kind);
     cuuint64_t dims[3] = {(cuuint64_t)Pp, (cuuint64_t)rows, (cuuint64_t)s};
-    cuuint64_t strides[2] = {(cuuint64_t)Pp * 2, (cuuint64_t)(rows * Pp * 2)};
-    cuuint32_t box[3] = {(cuuint32_t)BKE, (cuuint32_t)box_rows, (cuuint32_t)s};
+    cuuint64_t strides[2] = {(cuuint64_t)Pp * es, (cuuint64_t)(rows * Pp * es)};
+    cuuint32_t box[3] = {(cuuint32_t)fmt_bke(kind), (cuuint32_t)box_rows, (cuuint32_t)s};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+    const CUtensorMapDataType dt = kind == MM_SLICE_FP8E4M3 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = enc(map, dt, 3, base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return mm::fail(MM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return MM_OK;
 }
 
+// Per-launch constants shared by every problem of one slice format and count.
+// A stage holds one K-block (64 bytes per slice row) of all s slices of A and B.
+void fill_common(EmuParams &prm, int s, int kind) {
+    const uint32_t stage_bytes = (uint32_t)s * (BM + BN) * KB_BYTES;
+    prm.s = s;
+    prm.kind = kind;
+    prm.beta = fmt_beta(kind);
+    prm.bke = fmt_bke(kind);
+    prm.pair_blocks = fmt_pair_blocks(kind);
+    prm.stages = std::min(4, (int)((kSmemLimit - 2048) / stage_bytes));
+    prm.chunk_blocks = std::max(1, prm.pair_blocks / s);  // the exact length of diagonal s - 1
+    prm.hsplit = (s + 1) / 2;
+    int cols = 32;
+    while (cols < s * BN) cols <<= 1;
+    prm.tmem_cols = cols;
+}
+
+size_t slice_smem_bytes(int s) {
+    const uint32_t stage_bytes = (uint32_t)s * (BM + BN) * KB_BYTES;
+    const int stages = std::min(4, (int)((kSmemLimit - 2048) / stage_bytes));
+    return (size_t)stages * stage_bytes + 1024;
+}
+
+size_t split_cols_smem_bytes(int s, int kind) { return (size_t)s * SC_J * (SC_K + 2) * fmt_esize(kind); }
+
 }  // namespace
 
 namespace mm {
 
+// Slice count for a tier, or for an explicit count: MM_ERR_ARG for an unknown
+// format or an invalid request, MM_ERR_UNSUPPORTED when the tier needs more
+// than the 8 slices (8 TMEM accumulators of 64 columns) the kernel holds.
 int emulated_slices(int32_t kind, int32_t nslices, double tier) {
-    if (kind != MM_SLICE_BF16) return -1;
-    if (nslices > 0) return nslices <= 8 ? nslices : -1;
-    if (!(tier > 0.0)) return -1;
+    if (kind != MM_SLICE_BF16 && kind != MM_SLICE_FP8E4M3) return MM_ERR_ARG;
+    if (nslices > 0) return nslices <= 8 ? nslices : MM_ERR_ARG;
+    if (!(tier > 0.0)) return MM_ERR_ARG;
     // beta*s - 1 bits of each row/column; about 8 more bits than -log2(tier) keep the
     // normwise error below the tier on wide-exponent inputs.
-    const double need = (-log2(tier) + 9.0) / kBeta;
-    int s = (int)ceil(need);
-    return std::min(8, std::max(1, s));
+    const double need = (-log2(tier) + 9.0) / fmt_beta(kind);
+    const int s = std::max(1, (int)ceil(need));
+    if (s > 8) return MM_ERR_UNSUPPORTED;
+    return s;
 }
 
-size_t emulated_ws_bytes(int64_t N, int64_t P, int64_t M, int s) { return layout(N, P, M, s).total; }
+size_t emulated_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind) {
+    return layout(N, P, M, s, kind).total;
+}
 
 int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
-                 double *C, int64_t ldc, int s, void *ws, cudaStream_t st) {
-    const Layout L = layout(N, P, M, s);
+                 double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st) {
+    const Layout L = layout(N, P, M, s, kind);
     char *w = (char *)ws;
     int32_t *ea = (int32_t *)(w + L.off_ea);
     int32_t *fb = (int32_t *)(w + L.off_fb);
     unsigned long long *colmax = (unsigned long long *)(w + L.off_colmax);
-    __nv_bfloat16 *sa = (__nv_bfloat16 *)(w + L.off_a);
-    __nv_bfloat16 *sb = (__nv_bfloat16 *)(w + L.off_b);
+    unsigned char *sa = (unsigned char *)(w + L.off_a);
+    unsigned char *sb = (unsigned char *)(w + L.off_b);
     int rc;
     cudaError_t e = cudaMemsetAsync(colmax, 0, (size_t)M * 8, st);
     if (e != cudaSuccess) return cuda_fail(e, "mm_emulated");
-    const SplitA spa{N, P, lda, L.Nr, L.Pp, A, s, ea, sa};
-    const SplitB spb{P, M, ldb, L.Mr, L.Pp, B, s, colmax, fb, sb};
+    const SplitA spa{N, P, lda, L.Nr, L.Pp, A, s, kind, ea, sa};
+    const SplitB spb{P, M, ldb, L.Mr, L.Pp, B, s, kind, colmax, fb, sb};
     rc = launch("emu_split_rows", st,
-                [&] { split_rows_kernel<<<(unsigned)ceil_div(N, 8), 256, 0, st>>>(spa); });
+                [&] {
+                    if (kind == MM_SLICE_FP8E4M3)
+                        split_rows_kernel<MM_SLICE_FP8E4M3><<<(unsigned)ceil_div(N, 8), 256, 0, st>>>(spa);
+                    else
+                        split_rows_kernel<MM_SLICE_BF16><<<(unsigned)ceil_div(N, 8), 256, 0, st>>>(spa);
+                });
     if (rc) return rc;
     rc = launch("emu_col_max", st, [&] {
         dim3 g((unsigned)ceil_div(M, 128), (unsigned)ceil_div(P, 256));
@@ -730,27 +818,22 @@ int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
     if (rc) return rc;
     rc = launch("emu_split_cols", st, [&] {
         dim3 g((unsigned)ceil_div(M, SC_J), (unsigned)ceil_div(L.Pp, SC_K));
-        const size_t sm = (size_t)s * SC_J * (SC_K + 2) * sizeof(__nv_bfloat16);
-        split_cols_kernel<<<g, 256, sm, st>>>(spb);
+        if (kind == MM_SLICE_FP8E4M3)
+            split_cols_kernel<MM_SLICE_FP8E4M3><<<g, 256, split_cols_smem_bytes(s, kind), st>>>(spb);
+        else
+            split_cols_kernel<MM_SLICE_BF16><<<g, 256, split_cols_smem_bytes(s, kind), st>>>(spb);
     });
     if (rc) return rc;
 
     CUtensorMap tmA, tmB;
-    if ((rc = encode_slices(&tmA, sa, L.Nr, L.Pp, s, BM))) return rc;
-    if ((rc = encode_slices(&tmB, sb, L.Mr, L.Pp, s, BN))) return rc;
+    if ((rc = encode_slices(&tmA, sa, L.Nr, L.Pp, s, BM, kind))) return rc;
+    if ((rc = encode_slices(&tmB, sb, L.Mr, L.Pp, s, BN, kind))) return rc;
 
     EmuParams prm{};
+    fill_common(prm, s, kind);
     prm.N = N;
     prm.P = P;
     prm.M = M;
-    prm.s = s;
-    const uint32_t stage_bytes = (uint32_t)s * (BM + BN) * BKE * 2;
-    prm.stages = std::min(4, (int)((kSmemLimit - 2048) / stage_bytes));
-    prm.chunk_blocks = std::max(1, (int)((1 << 24) / ((int64_t)s * 4096) / BKE));
-    prm.hsplit = (s + 1) / 2;
-    int cols = 32;
-    while (cols < s * BN) cols <<= 1;
-    prm.tmem_cols = cols;
     prm.tiles_m = (int)ceil_div(N, BM);
     prm.tiles_n = (int)ceil_div(M, BN);
     prm.ea = ea;
@@ -758,13 +841,16 @@ int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
     prm.C = C;
     prm.ldc = ldc;
     prm.status = device_status_ptr();
-    const size_t smem = (size_t)prm.stages * stage_bytes + 1024;
+    const size_t smem = slice_smem_bytes(s);
     const cudaError_t attr_err = slice_smem_attributes();
     if (attr_err != cudaSuccess) return cuda_fail(attr_err, "mm_emulated: shared memory attribute");
     const int64_t tiles = (int64_t)prm.tiles_m * prm.tiles_n;
     const unsigned grid = (unsigned)std::min<int64_t>(tiles, sm_count());  // persistent: one CTA per SM
+    if (kind == MM_SLICE_FP8E4M3)
+        return launch("emu_slice_gemm_tcgen05_fp8", st,
+                      [&] { slice_gemm_kernel<true><<<grid, kThreads, smem, st>>>(tmA, tmB, prm); });
     return launch("emu_slice_gemm_tcgen05", st,
-                  [&] { slice_gemm_kernel<<<grid, kThreads, smem, st>>>(tmA, tmB, prm); });
+                  [&] { slice_gemm_kernel<false><<<grid, kThreads, smem, st>>>(tmA, tmB, prm); });
 }
 
 }  // namespace mm
@@ -773,36 +859,21 @@ int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
 
 namespace {
 
-size_t slices_bytes(int64_t rows_padded, int64_t Pp, int s) {
-    return mm::align_up((size_t)s * rows_padded * Pp * 2, 1024);
+size_t slices_bytes(int64_t rows_padded, int64_t Pp, int s, int kind) {
+    return mm::align_up((size_t)s * rows_padded * Pp * fmt_esize(kind), 1024);
 }
 
-// Per-launch constants shared by every problem of a slice count s.
-void fill_common(EmuParams &prm, int s) {
-    const uint32_t stage_bytes = (uint32_t)s * (BM + BN) * BKE * 2;
-    prm.s = s;
-    prm.stages = std::min(4, (int)((kSmemLimit - 2048) / stage_bytes));
-    prm.chunk_blocks = std::max(1, (int)((1 << 24) / ((int64_t)s * 4096) / BKE));
-    prm.hsplit = (s + 1) / 2;
-    int cols = 32;
-    while (cols < s * BN) cols <<= 1;
-    prm.tmem_cols = cols;
-}
-
-size_t slice_smem_bytes(int s) {
-    const uint32_t stage_bytes = (uint32_t)s * (BM + BN) * BKE * 2;
-    const int stages = std::min(4, (int)((kSmemLimit - 2048) / stage_bytes));
-    return (size_t)stages * stage_bytes + 1024;
-}
 
 cudaError_t slice_smem_attributes() {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-        err = cudaFuncSetAttribute(slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit - 1024);
-        if (err == cudaSuccess)
-            err = cudaFuncSetAttribute(group_slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kSmemLimit - 1024);
+        const void *kernels[4] = {(const void *)slice_gemm_kernel<false>, (const void *)slice_gemm_kernel<true>,
+                                  (const void *)group_slice_gemm_kernel<false>,
+                                  (const void *)group_slice_gemm_kernel<true>};
+        for (const void *k : kernels)
+            if (err == cudaSuccess)
+                err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit - 1024);
     });
     return err;
 }
@@ -839,21 +910,21 @@ static GroupLayout group_layout(int count) {
 
 size_t group_table_bytes(int count) { return group_layout(count).table_bytes; }
 
-size_t problem_data_bytes(const mm_problem &q, int s) {
-    const Layout L = layout(q.N, q.P, q.M, s);
+size_t problem_data_bytes(const mm_problem &q, int s, int kind) {
+    const Layout L = layout(q.N, q.P, q.M, s, kind);
     return align_up((size_t)L.Mr * 8, 1024) + align_up((size_t)L.Nr * 4, 1024) + align_up((size_t)L.Mr * 4, 1024) +
-           slices_bytes(L.Nr, L.Pp, s) + slices_bytes(L.Mr, L.Pp, s);
+           slices_bytes(L.Nr, L.Pp, s, kind) + slices_bytes(L.Mr, L.Pp, s, kind);
 }
 
-size_t group_data_bytes(const mm_problem *probs, int count, int s) {
+size_t group_data_bytes(const mm_problem *probs, int count, int s, int kind) {
     size_t d = 0;
-    for (int i = 0; i < count; ++i) d += problem_data_bytes(probs[i], s);
+    for (int i = 0; i < count; ++i) d += problem_data_bytes(probs[i], s, kind);
     return d;
 }
 
-size_t emulated_group_ws_bytes(const mm_problem *probs, int count, int s) {
+size_t emulated_group_ws_bytes(const mm_problem *probs, int count, int s, int kind) {
     if (count <= 0) return 0;
-    return group_table_bytes(count) + group_data_bytes(probs, count, s);
+    return group_table_bytes(count) + group_data_bytes(probs, count, s, kind);
 }
 
 // The five kernels of a grouped launch (no memset or copy: capturable).
@@ -869,9 +940,10 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
     if (rc) return rc;
     if (gl.grid[U_ROWS] > 0)
         rc = launch("emu_group_split_rows", st, [&] {
-            group_split_rows_kernel<<<(unsigned)gl.grid[U_ROWS], 256, 0, st>>>((const EmuProblem *)gl.tab,
-                                                                                 gl.begin[U_ROWS],
-                                                                                 (const GroupHeader *)gl.hdr);
+            const auto k = gl.kind == MM_SLICE_FP8E4M3 ? group_split_rows_kernel<MM_SLICE_FP8E4M3>
+                                                       : group_split_rows_kernel<MM_SLICE_BF16>;
+            k<<<(unsigned)gl.grid[U_ROWS], 256, 0, st>>>((const EmuProblem *)gl.tab, gl.begin[U_ROWS],
+                                                         (const GroupHeader *)gl.hdr);
         });
     if (rc) return rc;
     if (gl.grid[U_COLMAX] > 0)
@@ -883,15 +955,21 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
     if (rc) return rc;
     if (gl.grid[U_SPLITCOLS] > 0)
         rc = launch("emu_group_split_cols", st, [&] {
-            const size_t sm = (size_t)gl.s * SC_J * (SC_K + 2) * sizeof(__nv_bfloat16);
-            group_split_cols_kernel<<<(unsigned)gl.grid[U_SPLITCOLS], 256, sm, st>>>(
+            const auto k = gl.kind == MM_SLICE_FP8E4M3 ? group_split_cols_kernel<MM_SLICE_FP8E4M3>
+                                                       : group_split_cols_kernel<MM_SLICE_BF16>;
+            k<<<(unsigned)gl.grid[U_SPLITCOLS], 256, split_cols_smem_bytes(gl.s, gl.kind), st>>>(
                 (const EmuProblem *)gl.tab, gl.begin[U_SPLITCOLS], (const GroupHeader *)gl.hdr);
         });
     if (rc) return rc;
-    if (gl.grid[U_TILES] > 0)
+    const unsigned tiles_grid = (unsigned)std::min<int64_t>(gl.grid[U_TILES], sm_count());  // persistent
+    if (gl.grid[U_TILES] > 0 && gl.kind == MM_SLICE_FP8E4M3)
+        rc = launch("emu_group_slice_gemm_tcgen05_fp8", st, [&] {
+            group_slice_gemm_kernel<true><<<tiles_grid, kThreads, slice_smem_bytes(gl.s), st>>>(
+                (const EmuProblem *)gl.tab, gl.begin[U_TILES], (const GroupHeader *)gl.hdr);
+        });
+    else if (gl.grid[U_TILES] > 0)
         rc = launch("emu_group_slice_gemm_tcgen05", st, [&] {
-            group_slice_gemm_kernel<<<(unsigned)std::min<int64_t>(gl.grid[U_TILES], sm_count()), kThreads,
-                                      slice_smem_bytes(gl.s), st>>>(
+            group_slice_gemm_kernel<false><<<tiles_grid, kThreads, slice_smem_bytes(gl.s), st>>>(
                 (const EmuProblem *)gl.tab, gl.begin[U_TILES], (const GroupHeader *)gl.hdr);
         });
     return rc;
@@ -899,10 +977,10 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
 
 // Builds the host image of the table part for the problems (all N, P, M >= 1)
 // -- to be copied to `table_dev` -- and the launch description.  data[i] is
-// problem i's data region of problem_data_bytes(probs[i], s) bytes; the table
-// is laid out for `capacity` problems (>= count).
+// problem i's data region of problem_data_bytes(probs[i], s, kind) bytes; the
+// table is laid out for `capacity` problems (>= count).
 int group_build(const mm_problem *probs, int count, int capacity, int s, void *table_dev, char *const *data,
-                std::vector<unsigned char> &image, GroupLaunch &gl) {
+                std::vector<unsigned char> &image, GroupLaunch &gl, int kind) {
     if (capacity < count) return fail(MM_ERR_ARG, "grouped launch: %d problems exceed capacity %d", count, capacity);
     const GroupLayout G = group_layout(capacity);
     char *t = (char *)table_dev;
@@ -915,7 +993,7 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
     int *status = device_status_ptr();
     for (int i = 0; i < count; ++i) {
         const mm_problem &q = probs[i];
-        const Layout L = layout(q.N, q.P, q.M, s);
+        const Layout L = layout(q.N, q.P, q.M, s, kind);
         EmuProblem &e = tab[i];
         char *w = data[i];
         unsigned long long *cm = (unsigned long long *)w;
@@ -924,12 +1002,12 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
         w += align_up((size_t)L.Nr * 4, 1024);
         int32_t *fb = (int32_t *)w;
         w += align_up((size_t)L.Mr * 4, 1024);
-        __nv_bfloat16 *sa = (__nv_bfloat16 *)w;
-        w += slices_bytes(L.Nr, L.Pp, s);
-        __nv_bfloat16 *sb = (__nv_bfloat16 *)w;
-        e.spa = SplitA{q.N, q.P, q.lda, L.Nr, L.Pp, q.A, s, ea, sa};
-        e.spb = SplitB{q.P, q.M, q.ldb, L.Mr, L.Pp, q.B, s, cm, fb, sb};
-        fill_common(e.prm, s);
+        unsigned char *sa = (unsigned char *)w;
+        w += slices_bytes(L.Nr, L.Pp, s, kind);
+        unsigned char *sb = (unsigned char *)w;
+        e.spa = SplitA{q.N, q.P, q.lda, L.Nr, L.Pp, q.A, s, kind, ea, sa};
+        e.spb = SplitB{q.P, q.M, q.ldb, L.Mr, L.Pp, q.B, s, kind, cm, fb, sb};
+        fill_common(e.prm, s, kind);
         e.prm.N = q.N;
         e.prm.P = q.P;
         e.prm.M = q.M;
@@ -940,8 +1018,8 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
         e.prm.C = q.C;
         e.prm.ldc = q.ldc;
         e.prm.status = status;
-        int rc = encode_slices(&e.tmA, sa, L.Nr, L.Pp, s, BM);
-        if (!rc) rc = encode_slices(&e.tmB, sb, L.Mr, L.Pp, s, BN);
+        int rc = encode_slices(&e.tmA, sa, L.Nr, L.Pp, s, BM, kind);
+        if (!rc) rc = encode_slices(&e.tmB, sb, L.Mr, L.Pp, s, BN, kind);
         if (rc) return rc;
         for (int k = 0; k < 5; ++k) begin[k][i] = units[k];
         units[U_ROWS] += ceil_div(q.N, 8);
@@ -960,10 +1038,11 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
     gl.tab = t + G.off_table;
     gl.hdr = t + G.off_hdr;
     gl.s = s;
+    gl.kind = kind;
     return MM_OK;
 }
 
-int run_emulated_group(const mm_problem *probs, int count, int s, void *ws, cudaStream_t st) {
+int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void *ws, cudaStream_t st) {
     std::vector<mm_problem> live;
     live.reserve(count);
     for (int i = 0; i < count; ++i) {
@@ -983,9 +1062,9 @@ int run_emulated_group(const mm_problem *probs, int count, int s, void *ws, cuda
     char *d = (char *)ws + group_table_bytes((int)live.size());
     for (size_t i = 0; i < live.size(); ++i) {
         data[i] = d;
-        d += problem_data_bytes(live[i], s);
+        d += problem_data_bytes(live[i], s, kind);
     }
-    int rc = group_build(live.data(), (int)live.size(), (int)live.size(), s, ws, data.data(), image, gl);
+    int rc = group_build(live.data(), (int)live.size(), (int)live.size(), s, ws, data.data(), image, gl, kind);
     if (rc) return rc;
     // Pageable source: the copy is staged before cudaMemcpyAsync returns, so `image` may go.
     cudaError_t e = cudaMemcpyAsync((void *)gl.tab, image.data(), image.size(), cudaMemcpyHostToDevice, st);
@@ -1036,8 +1115,8 @@ namespace mm {
 size_t emulated_noalloc_capacity() { return kNoAllocScratchBytes; }
 
 int run_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
-                         int64_t ldb, double *C, int64_t ldc, int s, cudaStream_t st) {
-    const size_t need = emulated_ws_bytes(N, P, M, s);
+                         int64_t ldb, double *C, int64_t ldc, int s, int kind, cudaStream_t st) {
+    const size_t need = emulated_ws_bytes(N, P, M, s, kind);
     if (need > kNoAllocScratchBytes)
         return fail(MM_ERR_NOMEM,
                     "mm_emulated_noalloc: this product needs %zu bytes of scratch, more than the %zu-byte static "
@@ -1048,7 +1127,7 @@ int run_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64
     if (rc) return rc;
     // The only region that must start at zero (the column maxima) is cleared by
     // run_emulated itself on every call; everything else is fully rewritten.
-    return run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, scratch, st);
+    return run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, kind, scratch, st);
 }
 
 }  // namespace mm

@@ -70,7 +70,14 @@ def test_host_side_queries_and_checks(native):
     # degenerate shapes are no-ops that return MM_OK without a device
     assert lib.mm_naive(0, 5, 5, None, 5, fake, 5, None, 5, None) == 0
     assert lib.mm_emulated(3, 3, 3, fake, 3, ctypes.c_void_p(0x30000), 3, ctypes.c_void_p(0x50000), 3, 1, 0, 1e-14,
-                           None, 0, None) == -4  # FP8 slices not built
+                           None, 0, None) == -4  # 1e-14 needs 12 FP8-E4M3 slices, more than 8
+    assert lib.mm_emulated_slices(1, 0, 1e-6) == 6  # beta = 5: ceil((log2(1e6) + 9) / 5)
+    assert lib.mm_emulated_slices(0, 0, 1e-6) == 5  # beta = 7
+    assert lib.mm_emulated_slices(2, 0, 1e-6) < 0  # unknown format
+    # FP8 slices take one byte per digit: about half the BF16 workspace
+    bf = lib.mm_emulated_workspace_bytes(1024, 1024, 1024, 0, 6, 1e-14)
+    f8 = lib.mm_emulated_workspace_bytes(1024, 1024, 1024, 1, 6, 1e-14)
+    assert 0 < f8 < bf
     # the paper's Strassen rule beyond 2401 innermost launches is refused
     assert lib.mm_strassen_workspace_bytes(4096, 4096, 4096, 0) == 0
     assert lib.mm_strassen(4096, 4096, 4096, fake, 4096, ctypes.c_void_p(0x30000), 4096, ctypes.c_void_p(0x10000000000),
