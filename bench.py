@@ -348,6 +348,15 @@ def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000
     paced = S.serving_trace(requests, S.stream_seed(4, 2), mean_gap_s=1.0 / (0.7 * rate))
     with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True) as srv:
         st, comps, rc = serving.replay(srv, paced, a_pool, b_pool, c_pool)
+    # The same two runs when each request takes the cheaper of BF16 and FP8 slices for its tier.
+    with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True,
+                        method=serving.METHOD_EMULATED_AUTO) as srv:
+        st_sat_a, _, rc_sat_a = serving.replay(srv, sat_trace, a_pool, b_pool, c_pool)
+    rate_a = st_sat_a["completed"] / max(st_sat_a["busy_s"], 1e-9)
+    paced_a = S.serving_trace(requests, S.stream_seed(4, 2), mean_gap_s=1.0 / (0.7 * rate_a))
+    with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True,
+                        method=serving.METHOD_EMULATED_AUTO) as srv:
+        st_a, _, rc_a = serving.replay(srv, paced_a, a_pool, b_pool, c_pool)
     base_trace = paced[:baseline_requests]
     with serving.Server(budget, method=serving.METHOD_FP64) as srv:
         st_b, _, rc_b = serving.replay(srv, base_trace, a_pool, b_pool, c_pool)
@@ -383,6 +392,12 @@ def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000
         "fp64_one_at_a_time": {"requests": len(base_trace), "arrival_rate_rps": 0.7 * rate,
                                "p50_ms": st_b["p50_ms"], "p99_ms": st_b["p99_ms"], "mean_ms": st_b["mean_ms"],
                                "tflops": st_b["flops"] / max(st_b["busy_s"], 1e-9) / 1e12, "status": rc_b},
+        "auto_format": {"formats": "1e-14: 8 BF16 slices; 1e-6: 6 FP8-E4M3 slices",
+                        "saturated": {"requests_per_s": rate_a,
+                                      "tflops": st_sat_a["flops"] / max(st_sat_a["busy_s"], 1e-9) / 1e12,
+                                      "status": rc_sat_a},
+                        "paced": {"arrival_rate_rps": 0.7 * rate_a, "p50_ms": st_a["p50_ms"], "p99_ms": st_a["p99_ms"],
+                                  "completed": st_a["completed"], "status": rc_a}},
         "load_sweep": sweep, "budget_1gb_saturated": tight,
         "latency": "submit -> result in pinned host memory (H2D copies, product, D2H copy)",
     }

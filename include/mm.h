@@ -277,16 +277,22 @@ int mm_emulated_group(const mm_problem *probs, int32_t count, int32_t kind, int3
  *     not fit yet) once their A, B and C fit; a request that can never fit
  *     completes with MM_ERR_NOMEM;
  *   - continuous batching: whenever a stream is free, all admitted requests of
- *     the oldest request's slice count (up to max_batch) run as one grouped
- *     emulated launch (method 0), replayed from a CUDA graph cached per stream,
- *     slice count and size bucket when use_graphs != 0; method 1 instead runs
- *     one request at a time with mm_naive's FP64 kernel (a baseline);
+ *     the oldest request's slice format and count (up to max_batch) run as one
+ *     grouped emulated launch, replayed from a CUDA graph cached per stream,
+ *     slice format and count and size bucket when use_graphs != 0;
+ *   - method 0: BF16 slices, the tier's count (mm_emulated_slices);
+ *     method 2: per request the cheaper of BF16 and FP8-E4M3 slices for its
+ *     tier (FP8 when the tier needs at most 8 FP8 slices and their pairs, at
+ *     twice the BF16 rate, cost less -- e.g. 6 FP8 slices for 1e-6 against 5
+ *     BF16 ones); method 1 runs one request at a time with mm_naive's FP64
+ *     kernel (a baseline);
  *   - per request: host-to-device copies of A and B, the product, and the copy
  *     of C back into the caller's host buffer, whose completion ends the
  *     request's latency (measured from mm_server_submit).
  * Host buffers must stay valid until the request completes; pinned host
  * memory lets copies overlap.  Each result is bit-identical to mm_emulated on
- * the same operands with the tier's slice count (or to mm_naive for method 1).
+ * the same operands with the slice format and count the completion reports
+ * (or to mm_naive for method 1).
  */
 typedef struct mm_server mm_server;
 typedef struct {
@@ -297,13 +303,15 @@ typedef struct {
     int64_t ldb;
     double *C; /* host output, ldc >= M */
     int64_t ldc;
-    double tier; /* requested ||C - AB||_inf / (||A||_inf ||B||_inf) (method 0) */
+    double tier; /* requested ||C - AB||_inf / (||A||_inf ||B||_inf) (methods 0 and 2) */
     int64_t tag; /* caller's identifier, echoed in the completion */
 } mm_request;
 typedef struct {
     int64_t tag;
     int32_t status; /* MM_OK, MM_ERR_NOMEM (never fits), MM_ERR_TIMEOUT (cancelled), MM_ERR_CUDA */
     int32_t slices; /* slice count used (0 for method 1) */
+    int32_t kind;   /* slice format used (mm_slice_kind) */
+    int32_t reserved;
     double queue_ms;   /* submit -> launch */
     double latency_ms; /* submit -> C in the host buffer */
 } mm_completion;

@@ -28,7 +28,8 @@ class Request(ctypes.Structure):
 
 
 class Completion(ctypes.Structure):
-    _fields_ = [("tag", i64), ("status", i32), ("slices", i32), ("queue_ms", dbl), ("latency_ms", dbl)]
+    _fields_ = [("tag", i64), ("status", i32), ("slices", i32), ("kind", i32), ("reserved", i32), ("queue_ms", dbl),
+                ("latency_ms", dbl)]
 
 
 class ServerStats(ctypes.Structure):

@@ -94,7 +94,7 @@ class ArenaAlloc {
 
 struct Req {
     mm_request r;
-    int s = 0;
+    int s = 0, kind = MM_SLICE_BF16;  // slice count (0: plain FP64) and format
     Clock::time_point arrival, launched;
     char *block = nullptr;
     size_t block_bytes = 0;
@@ -131,10 +131,25 @@ size_t operand_bytes(const mm_request &r) {
 
 // Device bytes one request holds from admission to completion: A, B, C and,
 // for the emulated method, its split workspace.
-size_t request_bytes(const mm_request &r, int s) {
+size_t request_bytes(const mm_request &r, int s, int kind) {
     size_t b = operand_bytes(r);
-    if (s > 0) b += mm::problem_data_bytes(mm_problem{r.N, r.P, r.M, nullptr, r.P, nullptr, r.M, nullptr, r.M}, s);
+    if (s > 0)
+        b += mm::problem_data_bytes(mm_problem{r.N, r.P, r.M, nullptr, r.P, nullptr, r.M, nullptr, r.M}, s, kind);
     return b;
+}
+
+// The slice format and count for a tier.  Method 2 takes FP8-E4M3 slices when
+// the tier allows them (at most 8) and their pairs, at twice the BF16 rate,
+// cost less than the BF16 pairs the tier needs.
+void choose_slices(int method, double tier, int *s, int *kind) {
+    *kind = MM_SLICE_BF16;
+    *s = mm::emulated_slices(MM_SLICE_BF16, 0, tier);
+    if (method != 2) return;
+    const int s8 = mm::emulated_slices(MM_SLICE_FP8E4M3, 0, tier);
+    if (s8 > 0 && s8 * (s8 + 1) < 2 * (*s) * (*s + 1)) {
+        *s = s8;
+        *kind = MM_SLICE_FP8E4M3;
+    }
 }
 
 }  // namespace
@@ -179,6 +194,7 @@ struct mm_server {
         c.tag = q->r.tag;
         c.status = status;
         c.slices = q->s;
+        c.kind = q->kind;
         c.queue_ms = q->launched.time_since_epoch().count() ? ms_between(q->arrival, q->launched) : 0.0;
         c.latency_ms = ms_between(q->arrival, now);
         {
@@ -221,7 +237,7 @@ struct mm_server {
         int looked = 0;
         for (auto it = pending.begin(); it != pending.end() && looked < 256; ++looked) {
             Req *q = *it;
-            const size_t need = request_bytes(q->r, q->s);
+            const size_t need = request_bytes(q->r, q->s, q->kind);
             if (need > arena.capacity()) {  // can never fit this budget
                 it = pending.erase(it);
                 finish(q, MM_ERR_NOMEM, Clock::now());
@@ -248,8 +264,8 @@ struct mm_server {
         b.slot = slot_index;
         std::vector<mm_problem> probs;
         std::vector<char *> data;
-        const int s = reqs[0]->s;
-        if (method == 0) {
+        const int s = reqs[0]->s, kind = reqs[0]->kind;
+        if (method != 1) {
             for (Req *q : reqs) {
                 probs.push_back(mm_problem{q->r.N, q->r.P, q->r.M, q->dA, q->r.P, q->dB, q->r.M, q->dC, q->r.M});
                 data.push_back(q->block + operand_bytes(q->r));
@@ -277,14 +293,14 @@ struct mm_server {
             std::vector<unsigned char> image;
             mm::GroupLaunch gl{};
             rc = mm::group_build(probs.data(), (int)probs.size(), max_batch, s, sl.table_dev, data.data(), image,
-                                 gl);
+                                 gl, kind);
             if (rc) return give_back(rc);
             std::memcpy(sl.staging, image.data(), image.size());
             cudaError_t e = cudaMemcpyAsync(sl.table_dev, sl.staging, image.size(), cudaMemcpyHostToDevice, st);
             if (e != cudaSuccess) return give_back(mm::cuda_fail(e, "server: table upload"));
             if (use_graphs) {
                 for (int k = 0; k < 5; ++k) gl.grid[k] = bucket(gl.grid[k]);
-                const GraphKey key{s, gl.grid[0], gl.grid[1], gl.grid[2], gl.grid[3], gl.grid[4]};
+                const GraphKey key{s + 16 * kind, gl.grid[0], gl.grid[1], gl.grid[2], gl.grid[3], gl.grid[4]};
                 auto it = sl.graphs.find(key);
                 if (it == sl.graphs.end()) {
                     cudaGraph_t graph = nullptr;
@@ -336,11 +352,11 @@ struct mm_server {
         bool any = false;
         for (size_t k = 0; k < slots.size() && !admitted.empty(); ++k) {
             if (slots[k].busy) continue;
-            const int s = admitted.front()->s;
+            const int s = admitted.front()->s, kind = admitted.front()->kind;
             const int cap = method == 1 ? 1 : max_batch;
             std::vector<Req *> take;
             for (auto it = admitted.begin(); it != admitted.end() && (int)take.size() < cap;) {
-                if ((*it)->s == s) {
+                if ((*it)->s == s && (*it)->kind == kind) {
                     take.push_back(*it);
                     it = admitted.erase(it);
                 } else {
@@ -401,13 +417,13 @@ int mm_server_create(void *arena, size_t arena_bytes, int32_t max_batch, int32_t
                      int32_t method, mm_server **out) {
     if (!out) return mm::fail(MM_ERR_ARG, "mm_server_create: NULL out");
     if (!arena || arena_bytes == 0) return mm::fail(MM_ERR_ARG, "mm_server_create: empty arena");
-    if (max_batch < 1 || max_batch > 4096 || nstreams < 1 || nstreams > 32 || method < 0 || method > 1)
-        return mm::fail(MM_ERR_ARG, "mm_server_create: max_batch 1..4096, nstreams 1..32, method 0 or 1");
+    if (max_batch < 1 || max_batch > 4096 || nstreams < 1 || nstreams > 32 || method < 0 || method > 2)
+        return mm::fail(MM_ERR_ARG, "mm_server_create: max_batch 1..4096, nstreams 1..32, method 0, 1 or 2");
     mm_server *s = new mm_server();
     cudaGetDevice(&s->device);
     s->max_batch = method == 1 ? 1 : max_batch;
     s->method = method;
-    s->use_graphs = use_graphs != 0 && method == 0;
+    s->use_graphs = use_graphs != 0 && method != 1;
     const size_t table_cap = mm::group_table_bytes(s->max_batch);
     const int ns = method == 1 ? 1 : nstreams;
     // Per-slot table parts live at the front of the arena.
@@ -441,12 +457,12 @@ int mm_server_submit(mm_server *s, const mm_request *req) {
         return mm::fail(MM_ERR_ARG, "mm_server_submit: bad shape or leading dimension");
     if ((r.N && r.P && !r.A) || (r.P && r.M && !r.B) || (r.N && r.M && !r.C))
         return mm::fail(MM_ERR_ARG, "mm_server_submit: NULL host pointer");
-    if (s->method == 0 && !(r.tier > 0.0)) return mm::fail(MM_ERR_ARG, "mm_server_submit: tier must be > 0");
+    if (s->method != 1 && !(r.tier > 0.0)) return mm::fail(MM_ERR_ARG, "mm_server_submit: tier must be > 0");
     if (r.P > (int64_t(1) << 20)) return mm::fail(MM_ERR_UNSUPPORTED, "mm_server_submit: P > 2^20");
     Req *q = new Req();
     q->r = r;
     q->arrival = Clock::now();
-    q->s = s->method == 1 ? 0 : mm::emulated_slices(MM_SLICE_BF16, 0, r.tier);
+    if (s->method != 1) choose_slices(s->method, r.tier, &q->s, &q->kind);
     {
         std::lock_guard<std::mutex> g(s->res_mu);
         ++s->submitted;

@@ -22,8 +22,9 @@ def _declare():
     return lib()
 
 
-METHOD_EMULATED = 0
-METHOD_FP64 = 1
+METHOD_EMULATED = 0       # BF16 slices
+METHOD_FP64 = 1           # one request at a time with the plain FP64 kernel (baseline)
+METHOD_EMULATED_AUTO = 2  # per request the cheaper of BF16 and FP8-E4M3 slices for its tier
 
 
 class Server:
@@ -80,7 +81,7 @@ class Server:
         for i in range(n):
             c = buf[i]
             self._keep.pop(int(c.tag), None)
-            out.append({"tag": int(c.tag), "status": int(c.status), "slices": int(c.slices),
+            out.append({"tag": int(c.tag), "status": int(c.status), "slices": int(c.slices), "kind": int(c.kind),
                         "queue_ms": float(c.queue_ms), "latency_ms": float(c.latency_ms)})
         return out
 

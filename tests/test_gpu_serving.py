@@ -70,6 +70,29 @@ def test_alone_and_in_the_mix_agree(srv):
         assert np.array_equal(alone[i], ref)
 
 
+def test_auto_format_uses_fp8_for_low_tiers(srv):
+    """Method 2 serves the 1e-6 tier from FP8-E4M3 slices (6 of them cost 21
+    pairs at twice the BF16 rate, against 15 BF16 pairs) and 1e-14 from 8 BF16
+    slices; each result equals the single call with the reported format."""
+    mm, serving = srv
+    cases = [_case(200 + i, *sh) for i, sh in enumerate(SHAPES)]
+    with serving.Server(1 << 30, max_batch=64, nstreams=2, use_graphs=True,
+                        method=serving.METHOD_EMULATED_AUTO) as s:
+        for i, (a, b, c) in enumerate(cases):
+            s.submit(a, b, c, tier=TIERS[i], tag=i)
+        assert s.wait(120) == 0
+        comps = {x["tag"]: x for x in s.poll()}
+    for i, (a, b, c) in enumerate(cases):
+        comp = comps[i]
+        assert comp["status"] == 0
+        if TIERS[i] == 1e-6:
+            assert (comp["kind"], comp["slices"]) == (mm.SLICE_FP8E4M3, 6)
+        else:
+            assert (comp["kind"], comp["slices"]) == (mm.SLICE_BF16, 8)
+        ref = mm.emulated(a.cuda(), b.cuda(), nslices=comp["slices"], kind=comp["kind"]).cpu().numpy()
+        assert np.array_equal(c.numpy(), ref), f"request {i}"
+
+
 def test_budget_binds_and_is_respected(srv):
     mm, serving = srv
     budget = 48 << 20
