@@ -215,6 +215,24 @@ int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, c
                 double *C, int64_t ldc, int32_t kind, int32_t nslices, double tier, void *ws, size_t ws_bytes,
                 void *stream);
 
+/*
+ * mm_emulated with HOST operands: A, B and C are host pointers (pinned memory
+ * lets the copies overlap the products), `ws` is a device workspace of
+ * mm_emulated_host_workspace_bytes bytes holding the device copies of A, B, C
+ * and the split.  B is copied and split first; A goes up in up to 4 row blocks
+ * on an internal copy stream, each block's product follows its copy, and its
+ * rows of C are copied back on a second internal stream while later blocks
+ * run.  Asynchronous on `stream` (which waits for the last copy back); the
+ * host buffers must stay valid and C unread until the stream completes.  With
+ * P == 0 the call writes C = 0 on the host before returning.  Results are
+ * bit-identical to mm_emulated.  Errors as for mm_emulated.
+ */
+size_t mm_emulated_host_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t kind, int32_t nslices,
+                                        double tier);
+int mm_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                     double *C, int64_t ldc, int32_t kind, int32_t nslices, double tier, void *ws, size_t ws_bytes,
+                     void *stream);
+
 /* Slice count mm_emulated uses for (kind, nslices, tier). */
 int mm_emulated_slices(int32_t kind, int32_t nslices, double tier);
 

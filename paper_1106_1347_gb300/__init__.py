@@ -14,7 +14,7 @@ import ctypes
 from ._native import KernelStat, MMError, check, lib
 
 __all__ = ["naive", "naive_unrolled", "kahan", "winograd", "winograd_scaled", "winograd_rowcol_scaled", "strassen", "strassen_winograd", "tune_strassen", "norm_inf",
-           "emulated", "emulated_group", "emulated_noalloc", "emulated_slices", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
+           "emulated", "emulated_host", "emulated_group", "emulated_noalloc", "emulated_slices", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
            "SLICE_FP8E4M3"]
 
 SLICE_BF16 = 0
@@ -183,6 +183,42 @@ def emulated(a, b, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
     ws = _ws(need, a.device)
     check("mm_emulated", lib().mm_emulated(*_gemm_args(a, b, c, n, p, m), kind, nslices, float(tier), _ptr(ws), need,
                                            _stream(a.device)))
+    return c
+
+
+def emulated_host(a, b, out=None, nslices=0, tier=1e-14, kind=SLICE_BF16, device=None):
+    """mm_emulated_host: host (CPU) float64 operands, device workspace; copies
+    overlap the products.  Returns the host result after the stream completes."""
+    import numpy as np
+
+    torch = _torch()
+
+    def host(x):
+        x = x.numpy() if isinstance(x, torch.Tensor) else np.asarray(x)
+        if x.dtype != np.float64 or x.ndim != 2 or x.strides[1] != 8:
+            raise TypeError("host operands must be 2-D float64 with unit column stride")
+        return x
+
+    a, b = host(a), host(b)
+    n, p = a.shape
+    p2, m = b.shape
+    if p != p2:
+        raise ValueError("inner dimensions differ")
+    c = np.empty((n, m)) if out is None else host(out)
+    if c.shape != (n, m):
+        raise ValueError("output shape mismatch")
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    need = lib().mm_emulated_host_workspace_bytes(n, p, m, kind, nslices, tier)
+    ws = _ws(need, dev)
+
+    def ld(x):
+        return max(1, x.strides[0] // 8 if x.shape[0] > 1 else x.shape[1])
+
+    stream = torch.cuda.current_stream(dev)
+    check("mm_emulated_host", lib().mm_emulated_host(n, p, m, a.ctypes.data, ld(a), b.ctypes.data, ld(b),
+                                                     c.ctypes.data, ld(c), kind, nslices, float(tier), _ptr(ws), need,
+                                                     ctypes.c_void_p(stream.cuda_stream)))
+    stream.synchronize()
     return c
 
 

@@ -339,6 +339,33 @@ int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, c
     return run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st);
 }
 
+size_t mm_emulated_host_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t kind, int32_t nslices,
+                                        double tier) {
+    const int s = emulated_slices(kind, nslices, tier);
+    if (s <= 0 || N < 0 || P < 0 || M < 0) return 0;
+    return emulated_host_ws_bytes(N, P, M, s, kind);
+}
+
+int mm_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                     double *C, int64_t ldc, int32_t kind, int32_t nslices, double tier, void *ws, size_t ws_bytes,
+                     void *stream) {
+    int rc = check_gemm_args("mm_emulated_host", N, P, M, A, lda, B, ldb, C, ldc);
+    if (rc) return rc;
+    const int s = slices_or_fail("mm_emulated_host", kind, nslices, tier);
+    if (s < 0) return s;
+    if (P > (int64_t(1) << 20)) return fail(MM_ERR_UNSUPPORTED, "mm_emulated_host: P > 2^20");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N == 0 || M == 0) return MM_OK;
+    if (P == 0) {  // C = 0 in host memory, in stream order
+        for (int64_t i = 0; i < N; ++i) memset(C + i * ldc, 0, (size_t)M * 8);
+        return MM_OK;
+    }
+    const size_t need = emulated_host_ws_bytes(N, P, M, s, kind);
+    if (ws_bytes < need || !ws)
+        return fail(MM_ERR_WORKSPACE, "mm_emulated_host: workspace %zu bytes < %zu required", ws_bytes, need);
+    return run_emulated_host(N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st);
+}
+
 int mm_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
                         int64_t ldb, double *C, int64_t ldc, int32_t kind, int32_t nslices, double tier,
                         void *stream) {

@@ -90,6 +90,9 @@ size_t emulated_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind);
 int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
                  double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st);
 size_t emulated_group_ws_bytes(const mm_problem *probs, int count, int s, int kind);
+size_t emulated_host_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind);
+int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                      double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st);
 
 // Pieces of a grouped emulated launch, for runtimes that place the table part
 // (problem table, header, prefix arrays) and the data part (column maxima,

@@ -725,12 +725,16 @@ Layout layout(int64_t N, int64_t P, int64_t M, int s, int kind) {
 
 // Slices [s][rows][Pp] of the slice format (FP8 as bytes); the K extent is Pp
 // (zero-padded by the split kernels), K-blocks past Pp read the TMA zero fill.
-int encode_slices(CUtensorMap *map, void *base, int64_t rows, int64_t Pp, int s, int box_rows, int kind) {
+// `slice_rows` is the row count from one slice to the next (>= rows; larger for
+// a block of rows inside a taller slice).
+int encode_slices(CUtensorMap *map, void *base, int64_t rows, int64_t Pp, int s, int box_rows, int kind,
+                  int64_t slice_rows = 0) {
     mm::EncodeTiledFn enc = mm::encode_tiled_fn();
     if (!enc) return mm::fail(MM_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     const int es = fmt_esize(kind);
+    if (slice_rows < rows) slice_rows = rows;
     cuuint64_t dims[3] = {(cuuint64_t)Pp, (cuuint64_t)rows, (cuuint64_t)s};
-    cuuint64_t strides[2] = {(cuuint64_t)Pp * es, (cuuint64_t)(rows * Pp * es)};
+    cuuint64_t strides[2] = {(cuuint64_t)Pp * es, (cuuint64_t)(slice_rows * Pp * es)};
     cuuint32_t box[3] = {(cuuint32_t)fmt_bke(kind), (cuuint32_t)box_rows, (cuuint32_t)s};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt = kind == MM_SLICE_FP8E4M3 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
@@ -789,68 +793,205 @@ size_t emulated_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind) {
     return layout(N, P, M, s, kind).total;
 }
 
-int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
-                 double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st) {
-    const Layout L = layout(N, P, M, s, kind);
-    char *w = (char *)ws;
-    int32_t *ea = (int32_t *)(w + L.off_ea);
-    int32_t *fb = (int32_t *)(w + L.off_fb);
-    unsigned long long *colmax = (unsigned long long *)(w + L.off_colmax);
-    unsigned char *sa = (unsigned char *)(w + L.off_a);
-    unsigned char *sb = (unsigned char *)(w + L.off_b);
-    int rc;
-    cudaError_t e = cudaMemsetAsync(colmax, 0, (size_t)M * 8, st);
-    if (e != cudaSuccess) return cuda_fail(e, "mm_emulated");
-    const SplitA spa{N, P, lda, L.Nr, L.Pp, A, s, kind, ea, sa};
-    const SplitB spb{P, M, ldb, L.Mr, L.Pp, B, s, kind, colmax, fb, sb};
-    rc = launch("emu_split_rows", st,
-                [&] {
-                    if (kind == MM_SLICE_FP8E4M3)
-                        split_rows_kernel<MM_SLICE_FP8E4M3><<<(unsigned)ceil_div(N, 8), 256, 0, st>>>(spa);
-                    else
-                        split_rows_kernel<MM_SLICE_BF16><<<(unsigned)ceil_div(N, 8), 256, 0, st>>>(spa);
-                });
-    if (rc) return rc;
-    rc = launch("emu_col_max", st, [&] {
-        dim3 g((unsigned)ceil_div(M, 128), (unsigned)ceil_div(P, 256));
+}  // namespace mm
+
+namespace {
+
+// Pointers of one product's split workspace (layout()).
+struct EmuWork {
+    Layout L;
+    int32_t *ea, *fb;
+    unsigned long long *colmax;
+    unsigned char *sa, *sb;
+};
+
+EmuWork emu_work(int64_t N, int64_t P, int64_t M, int s, int kind, void *ws) {
+    EmuWork w;
+    w.L = layout(N, P, M, s, kind);
+    char *b = (char *)ws;
+    w.ea = (int32_t *)(b + w.L.off_ea);
+    w.fb = (int32_t *)(b + w.L.off_fb);
+    w.colmax = (unsigned long long *)(b + w.L.off_colmax);
+    w.sa = (unsigned char *)(b + w.L.off_a);
+    w.sb = (unsigned char *)(b + w.L.off_b);
+    return w;
+}
+
+// Column exponents and slices of B.
+int split_b(const EmuWork &w, int64_t P, int64_t M, const double *B, int64_t ldb, int s, int kind,
+            cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(w.colmax, 0, (size_t)M * 8, st);
+    if (e != cudaSuccess) return mm::cuda_fail(e, "mm_emulated");
+    const SplitB spb{P, M, ldb, w.L.Mr, w.L.Pp, B, s, kind, w.colmax, w.fb, w.sb};
+    int rc = mm::launch("emu_col_max", st, [&] {
+        dim3 g((unsigned)mm::ceil_div(M, 128), (unsigned)mm::ceil_div(P, 256));
         col_max_kernel<<<g, 128, 0, st>>>(spb);
     });
     if (rc) return rc;
-    rc = launch("emu_split_cols", st, [&] {
-        dim3 g((unsigned)ceil_div(M, SC_J), (unsigned)ceil_div(L.Pp, SC_K));
+    return mm::launch("emu_split_cols", st, [&] {
+        dim3 g((unsigned)mm::ceil_div(M, SC_J), (unsigned)mm::ceil_div(w.L.Pp, SC_K));
         if (kind == MM_SLICE_FP8E4M3)
             split_cols_kernel<MM_SLICE_FP8E4M3><<<g, 256, split_cols_smem_bytes(s, kind), st>>>(spb);
         else
             split_cols_kernel<MM_SLICE_BF16><<<g, 256, split_cols_smem_bytes(s, kind), st>>>(spb);
     });
-    if (rc) return rc;
+}
 
+// Rows [r0, r0 + n) of A (A points at row r0): exponents and slices.
+int split_a_rows(const EmuWork &w, int64_t r0, int64_t n, int64_t P, const double *A, int64_t lda, int s, int kind,
+                 cudaStream_t st) {
+    const SplitA spa{n, P, lda, w.L.Nr, w.L.Pp, A, s, kind, w.ea + r0,
+                     w.sa + (size_t)r0 * w.L.Pp * fmt_esize(kind)};
+    return mm::launch("emu_split_rows", st, [&] {
+        if (kind == MM_SLICE_FP8E4M3)
+            split_rows_kernel<MM_SLICE_FP8E4M3><<<(unsigned)mm::ceil_div(n, 8), 256, 0, st>>>(spa);
+        else
+            split_rows_kernel<MM_SLICE_BF16><<<(unsigned)mm::ceil_div(n, 8), 256, 0, st>>>(spa);
+    });
+}
+
+// The slice product for rows [r0, r0 + n) of C (r0 a multiple of the tile
+// height; C points at row r0).
+int slice_product(const EmuWork &w, int64_t r0, int64_t n, int64_t P, int64_t M, double *C, int64_t ldc, int s,
+                  int kind, cudaStream_t st) {
     CUtensorMap tmA, tmB;
-    if ((rc = encode_slices(&tmA, sa, L.Nr, L.Pp, s, BM, kind))) return rc;
-    if ((rc = encode_slices(&tmB, sb, L.Mr, L.Pp, s, BN, kind))) return rc;
-
+    const size_t es = fmt_esize(kind);
+    const int64_t nr = mm::ceil_div(n, BM) * BM;
+    int rc = encode_slices(&tmA, w.sa + (size_t)r0 * w.L.Pp * es, nr, w.L.Pp, s, BM, kind, w.L.Nr);
+    if (!rc) rc = encode_slices(&tmB, w.sb, w.L.Mr, w.L.Pp, s, BN, kind);
+    if (rc) return rc;
     EmuParams prm{};
     fill_common(prm, s, kind);
-    prm.N = N;
+    prm.N = n;
     prm.P = P;
     prm.M = M;
-    prm.tiles_m = (int)ceil_div(N, BM);
-    prm.tiles_n = (int)ceil_div(M, BN);
-    prm.ea = ea;
-    prm.fb = fb;
+    prm.tiles_m = (int)mm::ceil_div(n, BM);
+    prm.tiles_n = (int)mm::ceil_div(M, BN);
+    prm.ea = w.ea + r0;
+    prm.fb = w.fb;
     prm.C = C;
     prm.ldc = ldc;
-    prm.status = device_status_ptr();
+    prm.status = mm::device_status_ptr();
     const size_t smem = slice_smem_bytes(s);
     const cudaError_t attr_err = slice_smem_attributes();
-    if (attr_err != cudaSuccess) return cuda_fail(attr_err, "mm_emulated: shared memory attribute");
+    if (attr_err != cudaSuccess) return mm::cuda_fail(attr_err, "mm_emulated: shared memory attribute");
     const int64_t tiles = (int64_t)prm.tiles_m * prm.tiles_n;
-    const unsigned grid = (unsigned)std::min<int64_t>(tiles, sm_count());  // persistent: one CTA per SM
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, mm::sm_count());  // persistent: one CTA per SM
     if (kind == MM_SLICE_FP8E4M3)
-        return launch("emu_slice_gemm_tcgen05_fp8", st,
-                      [&] { slice_gemm_kernel<true><<<grid, kThreads, smem, st>>>(tmA, tmB, prm); });
-    return launch("emu_slice_gemm_tcgen05", st,
-                  [&] { slice_gemm_kernel<false><<<grid, kThreads, smem, st>>>(tmA, tmB, prm); });
+        return mm::launch("emu_slice_gemm_tcgen05_fp8", st,
+                          [&] { slice_gemm_kernel<true><<<grid, kThreads, smem, st>>>(tmA, tmB, prm); });
+    return mm::launch("emu_slice_gemm_tcgen05", st,
+                      [&] { slice_gemm_kernel<false><<<grid, kThreads, smem, st>>>(tmA, tmB, prm); });
+}
+
+}  // namespace
+
+namespace mm {
+
+int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                 double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st) {
+    const EmuWork w = emu_work(N, P, M, s, kind, ws);
+    int rc = split_a_rows(w, 0, N, P, A, lda, s, kind, st);
+    if (!rc) rc = split_b(w, P, M, B, ldb, s, kind, st);
+    if (!rc) rc = slice_product(w, 0, N, P, M, C, ldc, s, kind, st);
+    return rc;
+}
+
+// Host operands: device copies of A, B and C and the split workspace are carved
+// from ws.  B is copied and split on the caller's stream while the row blocks
+// of A go up on a copy stream; each block's split and slice product follow its
+// copy, and its rows of C come back on a second copy stream as soon as they
+// are done, so transfers overlap the products of other blocks.  The caller's
+// stream waits for the last copy back, and the copy streams wait for the
+// caller's earlier work, so consecutive calls on one stream stay ordered.
+size_t emulated_host_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind) {
+    return align_up((size_t)N * P * 8, 1024) + align_up((size_t)P * M * 8, 1024) + align_up((size_t)N * M * 8, 1024) +
+           layout(N, P, M, s, kind).total;
+}
+
+namespace {
+struct CopyStreams {
+    cudaStream_t up = nullptr, down = nullptr;
+};
+std::mutex g_copy_mu;
+std::vector<CopyStreams> g_copy;
+
+int copy_streams(CopyStreams *out) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(g_copy_mu);
+    if ((int)g_copy.size() <= dev) g_copy.resize(dev + 1);
+    CopyStreams &c = g_copy[dev];
+    if (!c.up) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c.up, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.down, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "mm_emulated_host: copy streams");
+    }
+    *out = c;
+    return MM_OK;
+}
+}  // namespace
+
+int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                      double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st) {
+    CopyStreams cs;
+    int rc = copy_streams(&cs);
+    if (rc) return rc;
+    char *w8 = (char *)ws;
+    double *dA = (double *)w8;
+    w8 += align_up((size_t)N * P * 8, 1024);
+    double *dB = (double *)w8;
+    w8 += align_up((size_t)P * M * 8, 1024);
+    double *dC = (double *)w8;
+    w8 += align_up((size_t)N * M * 8, 1024);
+    const EmuWork w = emu_work(N, P, M, s, kind, w8);
+    // Up to 4 row blocks of whole tiles.
+    const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(4, ceil_div(N, 512)));
+    const int64_t R = ceil_div(ceil_div(N, nb), BM) * BM;
+    std::vector<cudaEvent_t> ev;
+    auto event = [&](cudaEvent_t *e) {
+        cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+        if (r == cudaSuccess) ev.push_back(*e);
+        return r;
+    };
+    auto done = [&](int r) {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);  // released once their work completes
+        return r;
+    };
+    cudaEvent_t e0, eA, eC, eEnd;
+    cudaError_t e = event(&e0);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.up, e0, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.down, e0, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(dB, (size_t)M * 8, B, (size_t)ldb * 8, (size_t)M * 8, P, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
+    rc = split_b(w, P, M, dB, M, s, kind, st);
+    if (rc) return done(rc);
+    for (int64_t r0 = 0; r0 < N; r0 += R) {
+        const int64_t n = std::min(R, N - r0);
+        e = cudaMemcpy2DAsync(dA + r0 * P, (size_t)P * 8, A + r0 * lda, (size_t)lda * 8, (size_t)P * 8, n,
+                              cudaMemcpyHostToDevice, cs.up);
+        if (e == cudaSuccess) e = event(&eA);
+        if (e == cudaSuccess) e = cudaEventRecord(eA, cs.up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, eA, 0);
+        if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
+        rc = split_a_rows(w, r0, n, P, dA + r0 * P, P, s, kind, st);
+        if (!rc) rc = slice_product(w, r0, n, P, M, dC + r0 * M, M, s, kind, st);
+        if (rc) return done(rc);
+        e = event(&eC);
+        if (e == cudaSuccess) e = cudaEventRecord(eC, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.down, eC, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(C + r0 * ldc, (size_t)ldc * 8, dC + r0 * M, (size_t)M * 8, (size_t)M * 8, n,
+                                  cudaMemcpyDeviceToHost, cs.down);
+        if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
+    }
+    e = event(&eEnd);
+    if (e == cudaSuccess) e = cudaEventRecord(eEnd, cs.down);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, eEnd, 0);
+    if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
+    return done(MM_OK);
 }
 
 }  // namespace mm

@@ -358,6 +358,33 @@ def test_emulated_fp8_group_matches_single_calls(mm, orc):
         assert np.array_equal(host(c), orc.split_product(a, b, 5, 5))
 
 
+# ------------------------------------------------- host-operand pipeline
+
+@pytest.mark.parametrize("shape", [(2500, 300, 190), (129, 65, 65), (1, 1, 1), (700, 1000, 64)])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_emulated_host_matches_device_call(mm, shape, kind):
+    """Row blocks copied up, multiplied and copied back on overlapping streams
+    give the device call's result bit for bit (ragged last block included)."""
+    a, b = pair(*shape, "log", 70 + kind)
+    s = 8 if kind == 0 else 6
+    ref = host(mm.emulated(dev(a), dev(b), nslices=s, kind=kind))
+    assert np.array_equal(mm.emulated_host(a, b, nslices=s, kind=kind), ref)
+
+
+def test_emulated_host_pinned_strided_views(mm, orc):
+    import torch
+
+    big_a = torch.from_numpy(S.loguniform(1100, 260, 73)).pin_memory()
+    big_b = torch.from_numpy(S.loguniform(250, 90, 74)).pin_memory()
+    big_c = torch.zeros((1200, 100), dtype=torch.float64).pin_memory()
+    a, b, c = big_a[7:1037, 3:243], big_b[2:242, 5:85], big_c[11:1041, 7:87]
+    mm.emulated_host(a, b, out=c, nslices=8)
+    assert np.array_equal(c.numpy(), orc.split_product(a.numpy(), b.numpy(), 7, 8))
+    mask = np.ones(big_c.shape, dtype=bool)
+    mask[11:1041, 7:87] = False
+    assert np.all(big_c.numpy()[mask] == 0.0)
+
+
 # ---------------------------------------------------------- grouped launch
 
 def test_emulated_group_matches_single_calls(mm, orc):
