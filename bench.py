@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "split-precision vs plain FP64 GEMM TFLOP/s at rel ∞-err ≤1e-14; serve p50/p99 ms"
 N = P = M = 8192
 SLICES = 8
+KIND = 0  # MM_SLICE_BF16
 WORKLOAD = "fp64-accurate GEMM 8192x8192x8192, log-uniform |a| in 2^-20..2^20 with random sign"
 DOMINANT = "emu_slice_gemm_tcgen05"
 PROFILE_FILE = os.path.join(ROOT, "profiles", "emu_slice_gemm_tcgen05_8192.json")
@@ -48,6 +49,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--n", type=int, default=8192, help="N = P = M (profiling runs use a smaller case)")
     ap.add_argument("--quick", action="store_true", help="only the timed product (for profiler captures)")
+    ap.add_argument("--fp8", type=int, default=0, metavar="S",
+                    help="profiling runs: time S FP8-E4M3 slices instead of 8 BF16 ones (with --quick)")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-baseline-requests", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
@@ -57,7 +60,11 @@ def parse():
     ap.add_argument("--variants-n", type=int, default=1, help="0: skip the per-method FP64 sweep and the paper's table")
     ap.add_argument("--fp64-only", action="store_true", help="only the per-method FP64 timings (profiling runs)")
     args = ap.parse_args()
-    global N, P, M, WORKLOAD
+    global N, P, M, WORKLOAD, SLICES, KIND, DOMINANT
+    if args.fp8:
+        if not args.quick:
+            ap.error("--fp8 is for profiling runs: use it with --quick")
+        SLICES, KIND, DOMINANT = args.fp8, 1, "emu_slice_gemm_tcgen05_fp8"
     if args.n != 8192:
         N = P = M = args.n
         WORKLOAD = WORKLOAD.replace("8192x8192x8192", f"{N}x{N}x{N}")
@@ -534,7 +541,7 @@ def run_ours(args):
     ta = torch.from_numpy(a).to(dev)
     tb = torch.from_numpy(b).to(dev)
     c = torch.empty((N, M), dtype=torch.float64, device=dev)
-    ws_bytes = mm.lib().mm_emulated_workspace_bytes(N, P, M, 0, SLICES, 1e-14)
+    ws_bytes = mm.lib().mm_emulated_workspace_bytes(N, P, M, KIND, SLICES, 1e-14)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     lib = mm.lib()
@@ -542,7 +549,7 @@ def run_ours(args):
 
     def step(out=c):
         rc = lib.mm_emulated(N, P, M, ctypes.c_void_p(ta.data_ptr()), P, ctypes.c_void_p(tb.data_ptr()), M,
-                             ctypes.c_void_p(out.data_ptr()), M, 0, SLICES, 1e-14, ctypes.c_void_p(ws.data_ptr()),
+                             ctypes.c_void_p(out.data_ptr()), M, KIND, SLICES, 1e-14, ctypes.c_void_p(ws.data_ptr()),
                              ws_bytes, ctypes.c_void_p(stream.cuda_stream))
         if rc != 0:
             raise RuntimeError(lib.mm_last_error().decode())
@@ -571,10 +578,15 @@ def run_ours(args):
     tensor_flop_per_launch = pairs * flop
     achieved = tensor_flop_per_launch / (kms / max(launches, 1) * 1e-3) / 1e12 if launches else None
     peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
+    peak_source = f"{pk_kind} bf16_tflops_sustained"
+    if KIND == 1:  # FP8: the measured BF16 peak times the nominal FP8/BF16 ratio (4.5 / 2.25)
+        peak, peak_source = 2.0 * peak, peak_source + " x 2 (nominal FP8/BF16 ratio)"
+    fmt = "FP8-E4M3" if KIND == 1 else "BF16"
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": dominant_traffic(),
-                "kernel": DOMINANT, "peak_source": f"{pk_kind} bf16_tflops_sustained",
-                "algorithmic_unit": f"{pairs} slice pairs x 2NPM BF16 flops per launch"}
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": dominant_traffic() if KIND == 0 else None,
+                "kernel": DOMINANT, "peak_source": peak_source,
+                "algorithmic_unit": f"{pairs} slice pairs x 2NPM {fmt} flops per launch"}
     gpu_launches = sum(v[0] for v in prof.stats.values())
     kernel_ms = {k: round(v[1] / max(v[0], 1), 4) for k, v in prof.stats.items()}
 
@@ -666,9 +678,10 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "precision": "FP64-accurate: 8 BF16 slices, exact FP32 TMEM chunks, exact int64 recombination",
-        "config": {"workload": WORKLOAD, "N": N, "P": P, "M": M, "slices": SLICES, "beta": 7,
+        "vs_baseline": None, "dtype": "fp8" if KIND == 1 else "bf16", "data": "synthetic",
+        "precision": (f"{SLICES} {fmt} slices, exact FP32 TMEM chunks, exact int64 recombination"
+                      + ("" if KIND == 1 else " (FP64-accurate)")),
+        "config": {"workload": WORKLOAD, "N": N, "P": P, "M": M, "slices": SLICES, "beta": 5 if KIND == 1 else 7,
                    "parallelism": "replicas" if world > 1 else "single", "l2": "inputs (1 GiB) larger than L2"},
         "roofline": roofline, "kernel_ms_per_launch": kernel_ms, "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
