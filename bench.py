@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the slice sweep, the 4096x16384x4096 shape and the badly scaled errors")
     ap.add_argument("--variants-n", type=int, default=1, help="0: skip the per-method FP64 sweep and the paper's table")
-    ap.add_argument("--fp64-only", action="store_true", help="only the per-method FP64 timings (profiling runs)")
+    ap.add_argument("--fp64-only", action="store_true",
+                    help="only the per-method FP64 timings at n = --n, one run each (profiling runs)")
     args = ap.parse_args()
     global N, P, M, WORKLOAD, SLICES, KIND, DOMINANT
     if args.fp8:
@@ -435,7 +436,7 @@ FP64_PEAK_TFLOPS = 1.056  # DFMA and mma.sync f64 on GB300, measured by the libr
 FP64_SWEEP = (256, 1024, 2047, 2048, 4095, 4096, 8192)
 
 
-def variants_bench(dev, sizes=FP64_SWEEP):
+def variants_bench(dev, sizes=FP64_SWEEP, reps=None):
     """Each FP64 method at n^3 for n in `sizes` (uniform [-1, 1] inputs; odd n
     exercise Winograd's odd-P term): TFLOP/s as 2n^3/t and, for the methods
     with a fixed operation count, the fraction of the FP64 pipe kept busy."""
@@ -470,7 +471,7 @@ def variants_bench(dev, sizes=FP64_SWEEP):
         }
         out = {}
         for name, fn in runs.items():
-            ms = timed(fn, 1 if n >= 4095 else 3)
+            ms = timed(fn, reps or (1 if n >= 4095 else 3))
             tf = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
             entry = {"ms": ms, "tflops": tf}
             if name in pipe:  # fraction of the FP64 pipe kept busy
@@ -698,7 +699,8 @@ def main():
         from paper_1106_1347_gb300 import build as mmbuild
 
         mmbuild.build()
-        print(json.dumps(variants_bench(torch.device("cuda", 0))), flush=True)
+        # profiling runs: every FP64 method once (after one warm-up) at n = --n
+        print(json.dumps(variants_bench(torch.device("cuda", 0), (args.n,), reps=1)), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
