@@ -56,6 +56,13 @@ const char *mm_last_error(void);
  * MM_ERR_TIMEOUT; *code_out (may be NULL) receives the raw word. */
 int mm_device_status(void *stream, int32_t *code_out);
 
+/* Failure-detection self-test: enqueues on `stream` a kernel whose bounded
+ * wait on a barrier that nothing completes runs out (2^16 polls), so it sets
+ * the device status word (code 8) and returns; the next mm_device_status then
+ * reports MM_ERR_TIMEOUT and the context stays usable.  Returns MM_OK once
+ * enqueued. */
+int mm_selftest_wait_timeout(void *stream);
+
 /*
  * Section "NormInf": *out = ||A||_inf = max_i sum_j |A_ij| for the N x P
  * matrix A.  Each row is summed in index order, so the value is bit-identical
@@ -224,7 +231,7 @@ int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, c
  * rows of C are copied back on a second internal stream while later blocks
  * run.  Asynchronous on `stream` (which waits for the last copy back); the
  * host buffers must stay valid and C unread until the stream completes.  With
- * P == 0 the call writes C = 0 on the host before returning.  Results are
+ * P == 0 the call synchronises `stream` and writes C = 0 on the host.  Results are
  * bit-identical to mm_emulated.  Errors as for mm_emulated.
  */
 size_t mm_emulated_host_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t kind, int32_t nslices,

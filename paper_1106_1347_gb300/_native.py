@@ -47,6 +47,7 @@ SIGNATURES = {
     "mm_version": (ctypes.c_int, []),
     "mm_last_error": (ctypes.c_char_p, []),
     "mm_device_status": (ctypes.c_int, [vp, ctypes.POINTER(i32)]),
+    "mm_selftest_wait_timeout": (ctypes.c_int, [vp]),
     "mm_norm_inf": (ctypes.c_int, [i64, i64, vp, i64, vp, vp]),
     "mm_naive": (ctypes.c_int, GEMM + [vp]),
     "mm_kahan": (ctypes.c_int, GEMM + [vp]),

@@ -174,6 +174,8 @@ int mm_device_status(void *stream, int32_t *code_out) {
     return MM_OK;
 }
 
+int mm_selftest_wait_timeout(void *stream) { return run_selftest_wait(stream); }
+
 int mm_norm_inf(int64_t N, int64_t P, const double *A, int64_t lda, double *out, void *stream) {
     if (N < 0 || P < 0) return fail(MM_ERR_ARG, "mm_norm_inf: negative size");
     if (lda < std::max<int64_t>(1, P)) return fail(MM_ERR_ARG, "mm_norm_inf: lda too small");
@@ -356,7 +358,9 @@ int mm_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t l
     if (P > (int64_t(1) << 20)) return fail(MM_ERR_UNSUPPORTED, "mm_emulated_host: P > 2^20");
     cudaStream_t st = (cudaStream_t)stream;
     if (N == 0 || M == 0) return MM_OK;
-    if (P == 0) {  // C = 0 in host memory, in stream order
+    if (P == 0) {  // C = 0 in host memory, after the stream's earlier work (which may still write C)
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "mm_emulated_host");
         for (int64_t i = 0; i < N; ++i) memset(C + i * ldc, 0, (size_t)M * 8);
         return MM_OK;
     }

@@ -28,6 +28,8 @@ int sm_count();
 constexpr int kStatusTimeoutTma = 1;
 constexpr int kStatusTimeoutMma = 2;
 constexpr int kStatusTimeoutEpi = 4;
+constexpr int kStatusTimeoutSelftest = 8;  // mm_selftest_wait_timeout
+int run_selftest_wait(void *stream);
 
 // Kernel timing: begin/end bracket one launch on `stream` when profiling is on.
 void prof_begin(const char *name, cudaStream_t stream);
@@ -153,9 +155,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: true when the phase completed, false after kMaxPolls polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kMaxPolls; ++i)
+// Bounded wait: true when the phase completed, false after max_polls polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t max_polls = kMaxPolls) {
+    for (uint32_t i = 0; i < max_polls; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

@@ -66,3 +66,27 @@ int run_zero(int64_t N, int64_t M, double *C, int64_t ldc, cudaStream_t st) {
 }
 
 }  // namespace mm
+
+// Failure-detection self-test: one thread waits on an mbarrier that nothing
+// arrives at, with the same bounded wait the kernels use (a shorter limit),
+// gives up, raises the device status word and returns -- the context stays
+// usable.  Nothing faults, traps or hangs.
+namespace {
+__global__ void selftest_wait_kernel(int *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mmdev::mbar_init(&bar, 1);
+        mmdev::fence_mbar_init();
+        if (!mmdev::mbar_wait(&bar, 0, 1u << 16)) atomicOr(status, mm::kStatusTimeoutSelftest);
+    }
+}
+}  // namespace
+
+namespace mm {
+int run_selftest_wait(void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    int *status = device_status_ptr();
+    if (!status) return fail(MM_ERR_CUDA, "mm_selftest_wait_timeout: no device status symbol");
+    return launch("selftest_wait", st, [&] { selftest_wait_kernel<<<1, 32, 0, st>>>(status); });
+}
+}  // namespace mm

@@ -465,6 +465,25 @@ def test_argument_errors(mm):
         mm.naive(a, torch.zeros((5, 4), dtype=torch.float64, device="cuda"))
 
 
+def test_bounded_wait_gives_up_and_context_survives(mm, orc):
+    """A device wait on a barrier nothing completes gives up after its poll
+    limit, raises the status word and returns; the context keeps working."""
+    import ctypes
+
+    import torch
+
+    lib = mm.lib()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    code = ctypes.c_int32(0)
+    lib.mm_device_status(st, ctypes.byref(code))  # clear anything earlier
+    assert lib.mm_selftest_wait_timeout(st) == 0
+    assert lib.mm_device_status(st, ctypes.byref(code)) == -5  # MM_ERR_TIMEOUT
+    assert code.value == 8
+    a, b = pair(70, 90, 50, "int", 60)
+    assert np.array_equal(host(mm.naive(dev(a), dev(b))), a @ b)
+    assert lib.mm_device_status(st, ctypes.byref(code)) == 0 and code.value == 0
+
+
 def test_no_timeouts_raised(mm):
     assert mm.device_status() == 0
 
