@@ -302,9 +302,11 @@ int mm_emulated_group(const mm_problem *probs, int32_t count, int32_t kind, int3
  *     not fit yet) once their A, B and C fit; a request that can never fit
  *     completes with MM_ERR_NOMEM;
  *   - continuous batching: whenever a stream is free, all admitted requests of
- *     the oldest request's slice format and count (up to max_batch) run as one
- *     grouped emulated launch, replayed from a CUDA graph cached per stream,
- *     slice format and count and size bucket when use_graphs != 0;
+ *     the oldest request's slice format and count (up to max_batch; the
+ *     environment variable MM_SERVER_BATCH_MS, read at creation, also caps a
+ *     batch's estimated milliseconds of work) run as one grouped emulated
+ *     launch, replayed from a CUDA graph cached per stream, slice format and
+ *     count when use_graphs != 0;
  *   - method 0: BF16 slices, the tier's count (mm_emulated_slices);
  *     method 2: per request the cheaper of BF16 and FP8-E4M3 slices for its
  *     tier (FP8 when the tier needs at most 8 FP8 slices and their pairs, at

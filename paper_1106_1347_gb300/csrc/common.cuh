@@ -102,7 +102,7 @@ int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t 
 struct GroupLaunch {
     const void *tab, *hdr;    // device table and header (table part)
     const int64_t *begin[5];  // device prefix arrays
-    int64_t grid[5];          // CTAs per kernel; may be raised to upper bounds
+    int64_t grid[5];          // CTAs per kernel (grid-stride kernels: any size works)
     int s, kind;              // slice count and format
 };
 size_t group_table_bytes(int count);
@@ -111,6 +111,7 @@ size_t group_data_bytes(const mm_problem *probs, int count, int s, int kind = MM
 int group_build(const mm_problem *probs, int count, int capacity, int s, void *table_dev, char *const *data,
                 std::vector<unsigned char> &image, GroupLaunch &gl, int kind = MM_SLICE_BF16);
 int group_kernels(const GroupLaunch &gl, cudaStream_t st);
+int64_t group_grid_cap(int kernel);  // fixed grid of grouped kernel `kernel` (0..4)
 void prof_suspend(bool on);  // skip kernel timing while a stream is being captured
 int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void *ws, cudaStream_t st);
 size_t emulated_noalloc_capacity();

@@ -594,9 +594,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Many products with one slice count in one launch per kernel.  The host
 // writes a table of EmuProblem entries, four prefix arrays (per kernel, the
 // first CTA of each problem) and a header with the totals into the workspace;
-// each CTA finds its problem by binary search over the prefix array.  Grids
-// may exceed the totals (the serving loop captures a launch once per size
-// bucket in a CUDA graph); surplus CTAs return before touching anything.
+// each CTA finds its problem by binary search over the prefix array.  Every
+// kernel strides over its units, so its grid is a fixed size independent of
+// the batch: the serving loop captures the five launches once per slice
+// format and count in a CUDA graph and replays it for any batch.
 struct __align__(64) EmuProblem {
     CUtensorMap tmA, tmB;
     EmuParams prm;
@@ -624,47 +625,55 @@ __device__ __forceinline__ int find_problem(const int64_t *begin, int64_t count,
     return (int)lo;
 }
 
+// The grouped split kernels stride over their units (grid-stride loops), so
+// one fixed grid serves any batch and a CUDA graph captured once per slice
+// format and count is replayed for every batch.
 __global__ void __launch_bounds__(256) group_zero_colmax_kernel(const EmuProblem *tab, const int64_t *begin,
                                                                 const GroupHeader *hdr) {
-    const int64_t u = blockIdx.x;
-    if (u >= hdr->units[U_ZERO]) return;
-    const int g = find_problem(begin, hdr->count, u);
-    const SplitB &p = tab[g].spb;
-    const int64_t j = (u - begin[g]) * 256 + threadIdx.x;
-    if (j < p.M) p.colmax[j] = 0ull;
+    const int64_t units = hdr->units[U_ZERO];
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int g = find_problem(begin, hdr->count, u);
+        const SplitB &p = tab[g].spb;
+        const int64_t j = (u - begin[g]) * 256 + threadIdx.x;
+        if (j < p.M) p.colmax[j] = 0ull;
+    }
 }
 
 template <int KIND>
 __global__ void __launch_bounds__(256) group_split_rows_kernel(const EmuProblem *tab, const int64_t *begin,
                                                                const GroupHeader *hdr) {
-    const int64_t u = blockIdx.x;
-    if (u >= hdr->units[U_ROWS]) return;
-    const int g = find_problem(begin, hdr->count, u);
-    const SplitA &p = tab[g].spa;
-    const int64_t row = (u - begin[g]) * 8 + (threadIdx.x >> 5);
-    if (row < p.N) split_row<KIND>(p, row, threadIdx.x & 31);
+    const int64_t units = hdr->units[U_ROWS];
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int g = find_problem(begin, hdr->count, u);
+        const SplitA &p = tab[g].spa;
+        const int64_t row = (u - begin[g]) * 8 + (threadIdx.x >> 5);
+        if (row < p.N) split_row<KIND>(p, row, threadIdx.x & 31);
+    }
 }
 
 __global__ void __launch_bounds__(128) group_col_max_kernel(const EmuProblem *tab, const int64_t *begin,
                                                             const GroupHeader *hdr) {
-    const int64_t u = blockIdx.x;
-    if (u >= hdr->units[U_COLMAX]) return;
-    const int g = find_problem(begin, hdr->count, u);
-    const SplitB &p = tab[g].spb;
-    const int64_t local = u - begin[g], nj = (p.M + 127) / 128;
-    col_max_part(p, (local % nj) * 128 + threadIdx.x, (local / nj) * 256);
+    const int64_t units = hdr->units[U_COLMAX];
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int g = find_problem(begin, hdr->count, u);
+        const SplitB &p = tab[g].spb;
+        const int64_t local = u - begin[g], nj = (p.M + 127) / 128;
+        col_max_part(p, (local % nj) * 128 + threadIdx.x, (local / nj) * 256);
+    }
 }
 
 template <int KIND>
 __global__ void __launch_bounds__(256) group_split_cols_kernel(const EmuProblem *tab, const int64_t *begin,
                                                                const GroupHeader *hdr) {
     extern __shared__ __align__(16) unsigned char sm[];
-    const int64_t u = blockIdx.x;
-    if (u >= hdr->units[U_SPLITCOLS]) return;
-    const int g = find_problem(begin, hdr->count, u);
-    const SplitB &p = tab[g].spb;
-    const int64_t local = u - begin[g], nj = (p.M + SC_J - 1) / SC_J;
-    split_cols_tile<KIND>(p, local % nj, local / nj, sm);
+    const int64_t units = hdr->units[U_SPLITCOLS];
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int g = find_problem(begin, hdr->count, u);
+        const SplitB &p = tab[g].spb;
+        const int64_t local = u - begin[g], nj = (p.M + SC_J - 1) / SC_J;
+        split_cols_tile<KIND>(p, local % nj, local / nj, sm);
+        __syncthreads();  // the next unit rewrites the shared tile
+    }
 }
 
 struct GroupTiles {
@@ -1069,6 +1078,20 @@ size_t emulated_group_ws_bytes(const mm_problem *probs, int count, int s, int ki
 }
 
 // The five kernels of a grouped launch (no memset or copy: capturable).
+// Fixed grid of each grouped kernel: enough CTAs to fill the GPU, each
+// striding over the units (the slice product is persistent, one CTA per SM).
+int64_t group_grid_cap(int kernel) {
+    const int64_t sms = sm_count();
+    switch (kernel) {
+    case U_TILES:
+        return sms;
+    case U_SPLITCOLS:
+        return 4 * sms;
+    default:
+        return 8 * sms;
+    }
+}
+
 int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
     cudaError_t e = slice_smem_attributes();
     if (e != cudaSuccess) return cuda_fail(e, "grouped emulated product: shared memory attribute");
@@ -1173,7 +1196,7 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
     for (int k = 0; k < 5; ++k) {
         begin[k][count] = units[k];
         hdr->units[k] = units[k];
-        gl.grid[k] = units[k];
+        gl.grid[k] = std::min(units[k], group_grid_cap(k));
         gl.begin[k] = (const int64_t *)(t + G.off_begin[k]);
     }
     gl.tab = t + G.off_table;

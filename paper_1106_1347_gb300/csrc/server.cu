@@ -8,11 +8,13 @@
 //     when their device copies of A, B and C plus their split workspace fit
 //     in the arena (first fit) -- so an admitted request can always run;
 //   * whenever one of its K stream slots is free, forms a batch from every
-//     admitted request of the oldest request's slice count (up to max_batch)
-//     and enqueues on that slot's stream: host-to-device copies of A and B, the table upload, one grouped
-//     emulated launch (replayed from a CUDA graph cached per slot, slice count
-//     and power-of-two size bucket, when enabled), device-to-host copies of C,
-//     and an event;
+//     admitted request of the oldest request's slice format and count (up to
+//     max_batch, and, with MM_SERVER_BATCH_MS set, up to that many estimated
+//     milliseconds of work) and enqueues on that slot's stream: host-to-device
+//     copies of A and B, the table upload, one grouped emulated launch
+//     (replayed from a CUDA graph cached per slot, slice format and count, when
+//     enabled -- the grouped kernels run fixed grids), device-to-host copies
+//     of C, and an event;
 //   * retires batches whose event has fired, frees their memory and records
 //     each request's latency (arrival to result in the caller's host buffer).
 // Requests that arrive while batches are on the GPU are admitted and launched
@@ -23,6 +25,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -118,12 +121,6 @@ struct Batch {
     cudaEvent_t done = nullptr;
 };
 
-int64_t bucket(int64_t x) {
-    int64_t b = 1;
-    while (b < x) b <<= 1;
-    return b;
-}
-
 size_t operand_bytes(const mm_request &r) {
     return mm::align_up((size_t)(r.N * r.P) * 8, 1024) + mm::align_up((size_t)(r.P * r.M) * 8, 1024) +
            mm::align_up((size_t)(r.N * r.M) * 8, 1024);
@@ -136,6 +133,17 @@ size_t request_bytes(const mm_request &r, int s, int kind) {
     if (s > 0)
         b += mm::problem_data_bytes(mm_problem{r.N, r.P, r.M, nullptr, r.P, nullptr, r.M, nullptr, r.M}, s, kind);
     return b;
+}
+
+// Rough device time of one request (copies over a ~200 GB/s host link plus
+// the slice products at ~1.2 (BF16) or ~2.4 (FP8) PFLOP/s per pair), used only
+// to bound how much work one batch takes on.
+double request_ms(const Req &q) {
+    const mm_request &r = q.r;
+    const double bytes = 8.0 * ((double)r.N * r.P + (double)r.P * r.M + (double)r.N * r.M);
+    const double pairs = q.s * (q.s + 1) / 2.0;
+    const double rate = q.kind == MM_SLICE_FP8E4M3 ? 2.4e15 : 1.2e15;
+    return 1e3 * (bytes / 200e9 + 2.0 * r.N * r.P * r.M * pairs / rate);
 }
 
 // The slice format and count for a tier.  Method 2 takes FP8-E4M3 slices when
@@ -158,6 +166,7 @@ struct mm_server {
     int device = 0;
     ArenaAlloc arena;
     int max_batch = 64, method = 0;
+    double batch_ms_cap = 0.0;  // estimated device time per batch (0: no cap; MM_SERVER_BATCH_MS)
     bool use_graphs = true;
     std::vector<Slot> slots;
 
@@ -299,7 +308,9 @@ struct mm_server {
             cudaError_t e = cudaMemcpyAsync(sl.table_dev, sl.staging, image.size(), cudaMemcpyHostToDevice, st);
             if (e != cudaSuccess) return give_back(mm::cuda_fail(e, "server: table upload"));
             if (use_graphs) {
-                for (int k = 0; k < 5; ++k) gl.grid[k] = bucket(gl.grid[k]);
+                // Fixed grids (the kernels stride over their units): one graph per
+                // slice format and count serves every batch.
+                for (int k = 0; k < 5; ++k) gl.grid[k] = mm::group_grid_cap(k);
                 const GraphKey key{s + 16 * kind, gl.grid[0], gl.grid[1], gl.grid[2], gl.grid[3], gl.grid[4]};
                 auto it = sl.graphs.find(key);
                 if (it == sl.graphs.end()) {
@@ -355,8 +366,12 @@ struct mm_server {
             const int s = admitted.front()->s, kind = admitted.front()->kind;
             const int cap = method == 1 ? 1 : max_batch;
             std::vector<Req *> take;
+            double est_ms = 0.0;
             for (auto it = admitted.begin(); it != admitted.end() && (int)take.size() < cap;) {
                 if ((*it)->s == s && (*it)->kind == kind) {
+                    const double t = request_ms(**it);
+                    if (!take.empty() && batch_ms_cap > 0.0 && est_ms + t > batch_ms_cap) break;
+                    est_ms += t;
                     take.push_back(*it);
                     it = admitted.erase(it);
                 } else {
@@ -422,6 +437,7 @@ int mm_server_create(void *arena, size_t arena_bytes, int32_t max_batch, int32_t
     mm_server *s = new mm_server();
     cudaGetDevice(&s->device);
     s->max_batch = method == 1 ? 1 : max_batch;
+    if (const char *cap = getenv("MM_SERVER_BATCH_MS")) s->batch_ms_cap = atof(cap);
     s->method = method;
     s->use_graphs = use_graphs != 0 && method != 1;
     const size_t table_cap = mm::group_table_bytes(s->max_batch);
