@@ -313,6 +313,33 @@ def tall_inner_shape(dev):
             "rel_inf_err_sampled": sampled_error(c, a, b, norm_a, norm_b, rows)}
 
 
+def grouped_vs_single(dev, count=256):
+    """`count` products with the serving stream's shapes (N, P, M log-uniform on
+    [32, 4096]), 8 BF16 slices: one grouped launch per kernel against one
+    mm_emulated call per product, device-resident operands."""
+    import torch
+
+    import paper_1106_1347_gb300 as mm
+    import synthetic as S
+
+    trace = S.serving_trace(count, S.stream_seed(4, 7), mean_gap_s=0.0)
+    a_pool = torch.from_numpy(S.uniform(4096, 4096, S.stream_seed(4, 0))).to(dev)
+    b_pool = torch.from_numpy(S.uniform(4096, 4096, S.stream_seed(4, 1))).to(dev)
+    pairs = [(a_pool[:r["N"], :r["P"]], b_pool[:r["P"], :r["M"]]) for r in trace]
+    outs = [torch.empty((r["N"], r["M"]), dtype=torch.float64, device=dev) for r in trace]
+    flop = sum(2.0 * r["N"] * r["P"] * r["M"] for r in trace)
+    ms_group = timed(lambda: mm.emulated_group(pairs, nslices=8, outs=outs), 3)
+
+    def singles():
+        for (ta, tb), c in zip(pairs, outs):
+            mm.emulated(ta, tb, nslices=8, out=c)
+
+    ms_single = timed(singles, 3)
+    return {"problems": count, "dims": "N, P, M log-uniform [32, 4096]", "slices": 8, "gflop": flop / 1e9,
+            "grouped": {"ms": ms_group, "tflops": flop / (ms_group * 1e-3) / 1e12},
+            "one_call_each": {"ms": ms_single, "tflops": flop / (ms_single * 1e-3) / 1e12}}
+
+
 def badly_scaled_errors(dev, n=2048, nrows=64):
     """Rows of A times 10^u, columns of B times 10^v (u, v uniform [-6, 6]):
     normwise error ||C - T||/(||A|| ||B||) and componentwise
@@ -658,6 +685,7 @@ def run_ours(args):
             out["slice_sweep"] = slice_sweep(ta, tb, a, b, norm_a, norm_b, rows, truth)
             out["shape_4096x16384x4096"] = tall_inner_shape(dev)
             out["badly_scaled_2048"] = badly_scaled_errors(dev)
+            out["grouped_vs_single"] = grouped_vs_single(dev)
             torch.cuda.empty_cache()
         if not args.no_serve:
             del ha, hb, hc

@@ -140,9 +140,9 @@ __device__ __forceinline__ void store_digit(unsigned char *dst, int d, int kind)
 struct SplitA {
     int64_t N, P, lda, Nr, Pp;
     const double *A;
-    int s, kind;
+    int s;
     int32_t *ea;
-    unsigned char *slices;  // [s][Nr][Pp] elements of the slice format
+    unsigned char *slices;  // [s][Nr][Pp] elements of the slice format (the kernels' template parameter)
 };
 
 // One warp per row of A: max |A_ik| by integer max on the bit patterns, then
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const SplitA p) {
 struct SplitB {
     int64_t P, M, ldb, Mr, Pp;
     const double *B;
-    int s, kind;
+    int s;
     unsigned long long *colmax;  // zeroed before col_max runs
     int32_t *fb;
     unsigned char *slices;  // [s][Mr][Pp] elements of the slice format
@@ -265,7 +265,6 @@ __global__ void __launch_bounds__(256) split_cols_kernel(const SplitB p) {
 struct EmuParams {
     int64_t N, P, M;
     int s, stages, chunk_blocks, hsplit, tmem_cols;
-    int kind, beta, bke, pair_blocks;  // slice format, K-block in elements, exact K-blocks of one pair
     int tiles_m, tiles_n;
     const int32_t *ea, *fb;
     double *C;
@@ -759,12 +758,8 @@ int encode_slices(CUtensorMap *map, void *base, int64_t rows, int64_t Pp, int s,
 void fill_common(EmuParams &prm, int s, int kind) {
     const uint32_t stage_bytes = (uint32_t)s * (BM + BN) * KB_BYTES;
     prm.s = s;
-    prm.kind = kind;
-    prm.beta = fmt_beta(kind);
-    prm.bke = fmt_bke(kind);
-    prm.pair_blocks = fmt_pair_blocks(kind);
     prm.stages = std::min(4, (int)((kSmemLimit - 2048) / stage_bytes));
-    prm.chunk_blocks = std::max(1, prm.pair_blocks / s);  // the exact length of diagonal s - 1
+    prm.chunk_blocks = std::max(1, fmt_pair_blocks(kind) / s);  // the exact length of diagonal s - 1
     prm.hsplit = (s + 1) / 2;
     int cols = 32;
     while (cols < s * BN) cols <<= 1;
@@ -831,7 +826,7 @@ int split_b(const EmuWork &w, int64_t P, int64_t M, const double *B, int64_t ldb
             cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(w.colmax, 0, (size_t)M * 8, st);
     if (e != cudaSuccess) return mm::cuda_fail(e, "mm_emulated");
-    const SplitB spb{P, M, ldb, w.L.Mr, w.L.Pp, B, s, kind, w.colmax, w.fb, w.sb};
+    const SplitB spb{P, M, ldb, w.L.Mr, w.L.Pp, B, s, w.colmax, w.fb, w.sb};
     int rc = mm::launch("emu_col_max", st, [&] {
         dim3 g((unsigned)mm::ceil_div(M, 128), (unsigned)mm::ceil_div(P, 256));
         col_max_kernel<<<g, 128, 0, st>>>(spb);
@@ -849,7 +844,7 @@ int split_b(const EmuWork &w, int64_t P, int64_t M, const double *B, int64_t ldb
 // Rows [r0, r0 + n) of A (A points at row r0): exponents and slices.
 int split_a_rows(const EmuWork &w, int64_t r0, int64_t n, int64_t P, const double *A, int64_t lda, int s, int kind,
                  cudaStream_t st) {
-    const SplitA spa{n, P, lda, w.L.Nr, w.L.Pp, A, s, kind, w.ea + r0,
+    const SplitA spa{n, P, lda, w.L.Nr, w.L.Pp, A, s, w.ea + r0,
                      w.sa + (size_t)r0 * w.L.Pp * fmt_esize(kind)};
     return mm::launch("emu_split_rows", st, [&] {
         if (kind == MM_SLICE_FP8E4M3)
@@ -1169,8 +1164,8 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
         unsigned char *sa = (unsigned char *)w;
         w += slices_bytes(L.Nr, L.Pp, s, kind);
         unsigned char *sb = (unsigned char *)w;
-        e.spa = SplitA{q.N, q.P, q.lda, L.Nr, L.Pp, q.A, s, kind, ea, sa};
-        e.spb = SplitB{q.P, q.M, q.ldb, L.Mr, L.Pp, q.B, s, kind, cm, fb, sb};
+        e.spa = SplitA{q.N, q.P, q.lda, L.Nr, L.Pp, q.A, s, ea, sa};
+        e.spb = SplitB{q.P, q.M, q.ldb, L.Mr, L.Pp, q.B, s, cm, fb, sb};
         fill_common(e.prm, s, kind);
         e.prm.N = q.N;
         e.prm.P = q.P;
