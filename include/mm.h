@@ -1,8 +1,9 @@
 /*
  * mm.h -- C ABI of libmm, a GB300 (sm_103a) library for the dense product
- * C = A B of an N x P by a P x M double matrix in the methods surveyed by
+ * C = A B of an N x P by a P x M double matrix in the methods described in
  * I. Hedtke, "Methods of Matrix Multiplication" (arXiv:1106.1347), plus an
- * FP64-accurate product emulated from BF16 slices on the tcgen05 tensor cores.
+ * FP64-accurate product emulated from BF16 or FP8-E4M3 slices on the tcgen05
+ * tensor cores.
  *
  * Common conventions (every entry point below):
  *  - Matrices are row-major double with leading dimensions in elements:
