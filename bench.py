@@ -395,10 +395,21 @@ def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000
     b_pool = torch.from_numpy(S.uniform(4096, 4096, S.stream_seed(4, 1))).pin_memory()
     c_pool = torch.empty((8192, 8192), dtype=torch.float64).pin_memory()
     budget = int(budget_gb * (1 << 30))
+    # The host link the requests' operands cross: pinned copies of 512 MiB each way.
+    probe_h = torch.empty(1 << 26, dtype=torch.float64).pin_memory()
+    probe_d = torch.empty(1 << 26, dtype=torch.float64, device=dev)
+    up_ms = timed(lambda: probe_d.copy_(probe_h, non_blocking=True), 3)
+    down_ms = timed(lambda: probe_h.copy_(probe_d, non_blocking=True), 3)
+    link = {"h2d_gbs": probe_h.nbytes / (up_ms * 1e-3) / 1e9, "d2h_gbs": probe_h.nbytes / (down_ms * 1e-3) / 1e9}
+    del probe_h, probe_d
     sat_trace = S.serving_trace(requests, S.stream_seed(4, 2), mean_gap_s=0.0)
     with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True) as srv:
         st_sat, _, rc_sat = serving.replay(srv, sat_trace, a_pool, b_pool, c_pool)
     rate = st_sat["completed"] / max(st_sat["busy_s"], 1e-9)
+    up_bytes = sum(8.0 * (r["N"] * r["P"] + r["P"] * r["M"]) for r in sat_trace)
+    down_bytes = sum(8.0 * r["N"] * r["M"] for r in sat_trace)
+    # Time the copies alone would take, one direction after the other, at the measured link rates.
+    copy_s = up_bytes / (link["h2d_gbs"] * 1e9) + down_bytes / (link["d2h_gbs"] * 1e9)
     paced = S.serving_trace(requests, S.stream_seed(4, 2), mean_gap_s=1.0 / (0.7 * rate))
     with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True) as srv:
         st, comps, rc = serving.replay(srv, paced, a_pool, b_pool, c_pool)
@@ -436,8 +447,13 @@ def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000
     return {
         "requests": requests, "budget_gb": budget_gb, "dims": "N, P, M log-uniform [32, 4096]",
         "tiers": "1e-14 (8 slices) / 1e-6 (5 slices), 50/50",
+        "host_link": link,
         "saturated": {"requests_per_s": rate, "tflops": st_sat["flops"] / max(st_sat["busy_s"], 1e-9) / 1e12,
-                      "batches": st_sat["batches"], "status": rc_sat},
+                      "batches": st_sat["batches"], "graph_replays": st_sat["graph_replays"], "status": rc_sat,
+                      "h2d_gb": up_bytes / 1e9, "d2h_gb": down_bytes / 1e9, "busy_s": st_sat["busy_s"],
+                      "copy_bound_s": copy_s,
+                      "note": "copy_bound_s: the operand and result copies alone at the measured link rates, one "
+                              "direction after the other"},
         "paced": {"arrival_rate_rps": 0.7 * rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                   "mean_ms": st["mean_ms"], "max_ms": st["max_ms"], "completed": st["completed"],
                   "tflops": flop_all / max(st["busy_s"], 1e-9) / 1e12, "batches": st["batches"],
