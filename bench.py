@@ -728,7 +728,10 @@ def run_ours(args):
                       + ("" if KIND == 1 else " (FP64-accurate)")),
         "config": {"workload": WORKLOAD, "N": N, "P": P, "M": M, "slices": SLICES, "beta": 5 if KIND == 1 else 7,
                    "parallelism": "replicas" if world > 1 else "single", "l2": "inputs (1 GiB) larger than L2"},
-        "roofline": roofline, "kernel_ms_per_launch": kernel_ms, "gpu_launches": gpu_launches,
+        "roofline": roofline,
+        "vs_fp64_peak": {"fp64_peak_tflops": FP64_PEAK_TFLOPS, "ratio": value / world / FP64_PEAK_TFLOPS,
+                         "note": "2NPM/t per GPU against the FP64 rate (DFMA, DMMA) measured on this part"},
+        "kernel_ms_per_launch": kernel_ms, "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
     }
     line.update(out)
