@@ -58,6 +58,31 @@ __global__ void __launch_bounds__(256) unrolled_kernel(int64_t N, int64_t P, int
         __syncthreads();
         if (k0 + TK < P) fetch(k0 + TK);
         const int kn = (int)min((int64_t)TK, P - k0);
+        if (U != 3 && k0 + TK <= full) {
+            // A whole tile of complete groups (U divides TK and k0): the position in
+            // the group is known at compile time, so no selects are issued.
+#pragma unroll
+            for (int kk = 0; kk < TK; ++kk) {
+                double a[4], b[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) a[r] = As[ty + 16 * r][kk];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const double x = __dmul_rn(a[r], b[c]);
+                        if (U == 1) {
+                            aux[r][c] = __dadd_rn(aux[r][c], x);
+                        } else {
+                            grp[r][c] = kk % U == 0 ? x : __dadd_rn(grp[r][c], x);
+                            if (kk % U == U - 1) aux[r][c] = __dadd_rn(aux[r][c], grp[r][c]);
+                        }
+                    }
+            }
+            continue;  // t stays 0: the tile ended on a group boundary
+        }
         for (int kk = 0; kk < kn; ++kk) {
             double a[4], b[4];
 #pragma unroll
