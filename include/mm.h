@@ -305,7 +305,9 @@ int mm_emulated_group(const mm_problem *probs, int32_t count, int32_t kind, int3
  *   - continuous batching: whenever a stream is free, all admitted requests of
  *     the oldest request's slice format and count (up to max_batch; the
  *     environment variable MM_SERVER_BATCH_MS, read at creation, also caps a
- *     batch's estimated milliseconds of work) run as one grouped emulated
+ *     batch's estimated milliseconds of work, and MM_SERVER_CLASS_RATIO keeps
+ *     to requests within that factor of the oldest one's estimated time) run
+ *     as one grouped emulated
  *     launch, replayed from a CUDA graph cached per stream, slice format and
  *     count when use_graphs != 0;
  *   - method 0: BF16 slices, the tier's count (mm_emulated_slices);

@@ -167,6 +167,7 @@ struct mm_server {
     ArenaAlloc arena;
     int max_batch = 64, method = 0;
     double batch_ms_cap = 0.0;  // estimated device time per batch (0: no cap; MM_SERVER_BATCH_MS)
+    double class_ratio = 0.0;   // batch only requests within this factor of the oldest one's time (0: off)
     bool use_graphs = true;
     std::vector<Slot> slots;
 
@@ -365,11 +366,14 @@ struct mm_server {
             if (slots[k].busy) continue;
             const int s = admitted.front()->s, kind = admitted.front()->kind;
             const int cap = method == 1 ? 1 : max_batch;
+            const double front_ms = request_ms(*admitted.front());
             std::vector<Req *> take;
             double est_ms = 0.0;
             for (auto it = admitted.begin(); it != admitted.end() && (int)take.size() < cap;) {
-                if ((*it)->s == s && (*it)->kind == kind) {
-                    const double t = request_ms(**it);
+                const double t = request_ms(**it);
+                const bool same_class = class_ratio <= 0.0 ||
+                                        (t <= class_ratio * front_ms && front_ms <= class_ratio * t);
+                if ((*it)->s == s && (*it)->kind == kind && same_class) {
                     if (!take.empty() && batch_ms_cap > 0.0 && est_ms + t > batch_ms_cap) break;
                     est_ms += t;
                     take.push_back(*it);
@@ -438,6 +442,7 @@ int mm_server_create(void *arena, size_t arena_bytes, int32_t max_batch, int32_t
     cudaGetDevice(&s->device);
     s->max_batch = method == 1 ? 1 : max_batch;
     if (const char *cap = getenv("MM_SERVER_BATCH_MS")) s->batch_ms_cap = atof(cap);
+    if (const char *ratio = getenv("MM_SERVER_CLASS_RATIO")) s->class_ratio = atof(ratio);
     s->method = method;
     s->use_graphs = use_graphs != 0 && method != 1;
     const size_t table_cap = mm::group_table_bytes(s->max_batch);
