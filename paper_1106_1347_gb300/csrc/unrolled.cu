@@ -14,6 +14,8 @@
 // Same tiling as the Kahan kernel: 64x64 output tile, 256 threads, each owning
 // 4x4 outputs strided by 16, (aux, group) pairs in registers; FP64-pipe bound at
 // 1 DMUL + 1 DADD per k per output plus 1 DADD per group.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace {
@@ -58,30 +60,42 @@ __global__ void __launch_bounds__(256) unrolled_kernel(int64_t N, int64_t P, int
         __syncthreads();
         if (k0 + TK < P) fetch(k0 + TK);
         const int kn = (int)min((int64_t)TK, P - k0);
-        if (U != 3 && k0 + TK <= full) {
-            // A whole tile of complete groups (U divides TK and k0): the position in
-            // the group is known at compile time, so no selects are issued.
+        if (k0 + TK <= full) {
+            // A whole tile inside the complete groups: the position of each k in
+            // its group is (t + kk) mod U with t the tile's starting phase, fixed
+            // per phase at compile time, so no selects are issued.
+            auto tile = [&](auto phase) {
+                constexpr int T0 = decltype(phase)::value;
 #pragma unroll
-            for (int kk = 0; kk < TK; ++kk) {
-                double a[4], b[4];
+                for (int kk = 0; kk < TK; ++kk) {
+                    double a[4], b[4];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) a[r] = As[ty + 16 * r][kk];
+                    for (int r = 0; r < 4; ++r) a[r] = As[ty + 16 * r][kk];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+                    for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+                    const int pos = (T0 + kk) % U;
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
+                    for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const double x = __dmul_rn(a[r], b[c]);
-                        if (U == 1) {
-                            aux[r][c] = __dadd_rn(aux[r][c], x);
-                        } else {
-                            grp[r][c] = kk % U == 0 ? x : __dadd_rn(grp[r][c], x);
-                            if (kk % U == U - 1) aux[r][c] = __dadd_rn(aux[r][c], grp[r][c]);
+                        for (int c = 0; c < 4; ++c) {
+                            const double x = __dmul_rn(a[r], b[c]);
+                            if (U == 1) {
+                                aux[r][c] = __dadd_rn(aux[r][c], x);
+                            } else {
+                                grp[r][c] = pos == 0 ? x : __dadd_rn(grp[r][c], x);
+                                if (pos == U - 1) aux[r][c] = __dadd_rn(aux[r][c], grp[r][c]);
+                            }
                         }
-                    }
-            }
-            continue;  // t stays 0: the tile ended on a group boundary
+                }
+            };
+            if (U == 3 && t == 1)
+                tile(std::integral_constant<int, 1>{});
+            else if (U == 3 && t == 2)
+                tile(std::integral_constant<int, 2>{});
+            else
+                tile(std::integral_constant<int, 0>{});
+            t = (t + TK) % U;
+            continue;
         }
         for (int kk = 0; kk < kn; ++kk) {
             double a[4], b[4];
