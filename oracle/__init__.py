@@ -70,6 +70,8 @@ def _load():
             lib.oracle_split_digits.restype = ctypes.c_int
             lib.oracle_split_product.argtypes = gemm + [ctypes.c_int, ctypes.c_int]
             lib.oracle_split_product.restype = ctypes.c_int
+            lib.oracle_strassen_emulated.argtypes = [ctypes.c_int] + gemm + [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            lib.oracle_strassen_emulated.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -209,6 +211,22 @@ def strassen_naiv(a, b, depth: int = -1, padded=None):
 
 def strassen_winograd(a, b, depth: int = -1, padded=None):
     return _strassen("oracle_strassen_winograd", a, b, depth, padded)
+
+
+def strassen_emulated(a, b, variant: int, depth: int, beta: int, s: int):
+    """Strassen (variant 0) or Strassen-Winograd (variant 1), `depth` levels, over
+    the split product (beta, s); operands zero-padded to multiples of 2^depth."""
+    a, b = _f64(a), _f64(b)
+    n, p = a.shape
+    if b.shape[0] != p:
+        raise ValueError("inner dimensions differ")
+    m = b.shape[1]
+    c = np.zeros((n, m), dtype=np.float64)
+    rc = _load().oracle_strassen_emulated(int(variant), n, p, m, _ptr(a), _ld(a), _ptr(b), _ld(b), _ptr(c), _ld(c),
+                                          int(depth), int(beta), int(s))
+    if rc != 0:
+        raise ValueError(f"oracle_strassen_emulated: bad arguments ({variant}, {depth}, {beta}, {s})")
+    return c
 
 
 def dot2_product(a, b):

@@ -22,7 +22,10 @@
  *    1/2 <= 4^lambda ||A|| / ||B|| <= 2 (two integers qualify when
  *    log2(||B||/||A||) is odd, as for the paper's own test B = 8A).
  *  - Strassen: X = max{N,P,M}, k = max(0, floor(log2 X) - 4), m = floor(X/2^k) + 1,
- *    Y = m 2^k; sums of several terms are evaluated left to right.
+ *    Y = m 2^k; sums of several terms are evaluated left to right.  The same
+ *    recursion also runs over the split product as its base (not in the paper:
+ *    its Strassen levels above the emulated product), padded to multiples of
+ *    2^depth.
  *  - Kahan: the paper's update is used as printed and the final err is not
  *    folded back into the sum.
  *  - Per-row/column scaled Winograd (not in the paper; its scaling taken from
@@ -309,12 +312,30 @@ void oracle_strassen_paper_rule(int64_t N, int64_t P, int64_t M, int *k_out, int
 
 static double *zalloc(int64_t n) { return (double *)calloc((size_t)imax(n, 1), sizeof(double)); }
 
+/* The product at the bottom of the recursion: the paper's NaivStandard
+ * (beta == 0), or the split product of the given beta and slice count. */
+struct strassen_base {
+    int beta, s;
+};
+static const struct strassen_base naive_base = {0, 0};
+
+int oracle_split_product(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
+                         int64_t ldb, double *C, int64_t ldc, int beta, int s);
+
+static void base_product(const struct strassen_base *base, int64_t n, int64_t p, int64_t m, const double *A,
+                         int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc) {
+    if (base->beta == 0)
+        oracle_naiv_standard(n, p, m, A, lda, B, ldb, C, ldc);
+    else
+        (void)oracle_split_product(n, p, m, A, lda, B, ldb, C, ldc, base->beta, base->s);
+}
+
 /* alpha_{m,k}: one level of the recursion on an n x p times p x m product whose
  * dimensions are all divisible by 2^depth. */
 static void strassen_rec(int64_t n, int64_t p, int64_t m, const double *A, int64_t lda, const double *B,
-                         int64_t ldb, double *C, int64_t ldc, int depth) {
+                         int64_t ldb, double *C, int64_t ldc, int depth, const struct strassen_base *base) {
     if (depth == 0) {
-        oracle_naiv_standard(n, p, m, A, lda, B, ldb, C, ldc);
+        base_product(base, n, p, m, A, lda, B, ldb, C, ldc);
         return;
     }
     int64_t n2 = n / 2, p2 = p / 2, m2 = m / 2;
@@ -327,27 +348,27 @@ static void strassen_rec(int64_t n, int64_t p, int64_t m, const double *A, int64
     /* H1 = (A11 + A22)(B11 + B22) */
     plus(n2, p2, A11, lda, A22, lda, S, p2);
     plus(p2, m2, B11, ldb, B22, ldb, T, m2);
-    strassen_rec(n2, p2, m2, S, p2, T, m2, H[1], m2, depth - 1);
+    strassen_rec(n2, p2, m2, S, p2, T, m2, H[1], m2, depth - 1, base);
     /* H2 = (A21 + A22) B11 */
     plus(n2, p2, A21, lda, A22, lda, S, p2);
-    strassen_rec(n2, p2, m2, S, p2, B11, ldb, H[2], m2, depth - 1);
+    strassen_rec(n2, p2, m2, S, p2, B11, ldb, H[2], m2, depth - 1, base);
     /* H3 = A11 (B12 - B22) */
     minus(p2, m2, B12, ldb, B22, ldb, T, m2);
-    strassen_rec(n2, p2, m2, A11, lda, T, m2, H[3], m2, depth - 1);
+    strassen_rec(n2, p2, m2, A11, lda, T, m2, H[3], m2, depth - 1, base);
     /* H4 = A22 (B21 - B11) */
     minus(p2, m2, B21, ldb, B11, ldb, T, m2);
-    strassen_rec(n2, p2, m2, A22, lda, T, m2, H[4], m2, depth - 1);
+    strassen_rec(n2, p2, m2, A22, lda, T, m2, H[4], m2, depth - 1, base);
     /* H5 = (A11 + A12) B22 */
     plus(n2, p2, A11, lda, A12, lda, S, p2);
-    strassen_rec(n2, p2, m2, S, p2, B22, ldb, H[5], m2, depth - 1);
+    strassen_rec(n2, p2, m2, S, p2, B22, ldb, H[5], m2, depth - 1, base);
     /* H6 = (A21 - A11)(B11 + B12) */
     minus(n2, p2, A21, lda, A11, lda, S, p2);
     plus(p2, m2, B11, ldb, B12, ldb, T, m2);
-    strassen_rec(n2, p2, m2, S, p2, T, m2, H[6], m2, depth - 1);
+    strassen_rec(n2, p2, m2, S, p2, T, m2, H[6], m2, depth - 1, base);
     /* H7 = (A12 - A22)(B21 + B22) */
     minus(n2, p2, A12, lda, A22, lda, S, p2);
     plus(p2, m2, B21, ldb, B22, ldb, T, m2);
-    strassen_rec(n2, p2, m2, S, p2, T, m2, H[7], m2, depth - 1);
+    strassen_rec(n2, p2, m2, S, p2, T, m2, H[7], m2, depth - 1, base);
     /* C11 = H1 + H4 - H5 + H7, C12 = H3 + H5, C21 = H2 + H4, C22 = H1 + H3 - H2 + H6 (left to right) */
     plus(n2, m2, H[1], m2, H[4], m2, C11, ldc);
     minus(n2, m2, C11, ldc, H[5], m2, C11, ldc);
@@ -365,9 +386,10 @@ static void strassen_rec(int64_t n, int64_t p, int64_t m, const double *A, int64
 /* Section "StrassenWinograd": the Winograd variant (after Fischer and Probert)
  * with 15 additions, in the printed order. */
 static void strassen_winograd_rec(int64_t n, int64_t p, int64_t m, const double *A, int64_t lda, const double *B,
-                                  int64_t ldb, double *C, int64_t ldc, int depth) {
+                                  int64_t ldb, double *C, int64_t ldc, int depth,
+                                  const struct strassen_base *base) {
     if (depth == 0) {
-        oracle_naiv_standard(n, p, m, A, lda, B, ldb, C, ldc);
+        base_product(base, n, p, m, A, lda, B, ldb, C, ldc);
         return;
     }
     int64_t n2 = n / 2, p2 = p / 2, m2 = m / 2;
@@ -384,18 +406,18 @@ static void strassen_winograd_rec(int64_t n, int64_t p, int64_t m, const double 
     minus(p2, m2, B22, ldb, B12, ldb, B1, m2);
     plus(p2, m2, B1, m2, B11, ldb, B2, m2);
     /* H1 = A11 B11, H2 = A12 B21, H3 = A2 B2, H4 = (A21 + A22)(B12 - B11) */
-    strassen_winograd_rec(n2, p2, m2, A11, lda, B11, ldb, H[1], m2, depth - 1);
-    strassen_winograd_rec(n2, p2, m2, A12, lda, B21, ldb, H[2], m2, depth - 1);
-    strassen_winograd_rec(n2, p2, m2, A2, p2, B2, m2, H[3], m2, depth - 1);
+    strassen_winograd_rec(n2, p2, m2, A11, lda, B11, ldb, H[1], m2, depth - 1, base);
+    strassen_winograd_rec(n2, p2, m2, A12, lda, B21, ldb, H[2], m2, depth - 1, base);
+    strassen_winograd_rec(n2, p2, m2, A2, p2, B2, m2, H[3], m2, depth - 1, base);
     plus(n2, p2, A21, lda, A22, lda, S, p2);
     minus(p2, m2, B12, ldb, B11, ldb, T, m2);
-    strassen_winograd_rec(n2, p2, m2, S, p2, T, m2, H[4], m2, depth - 1);
+    strassen_winograd_rec(n2, p2, m2, S, p2, T, m2, H[4], m2, depth - 1, base);
     /* H5 = A1 B1, H6 = (A12 - A2) B22, H7 = A22 (B21 - B2) */
-    strassen_winograd_rec(n2, p2, m2, A1, p2, B1, m2, H[5], m2, depth - 1);
+    strassen_winograd_rec(n2, p2, m2, A1, p2, B1, m2, H[5], m2, depth - 1, base);
     minus(n2, p2, A12, lda, A2, p2, S, p2);
-    strassen_winograd_rec(n2, p2, m2, S, p2, B22, ldb, H[6], m2, depth - 1);
+    strassen_winograd_rec(n2, p2, m2, S, p2, B22, ldb, H[6], m2, depth - 1, base);
     minus(p2, m2, B21, ldb, B2, m2, T, m2);
-    strassen_winograd_rec(n2, p2, m2, A22, lda, T, m2, H[7], m2, depth - 1);
+    strassen_winograd_rec(n2, p2, m2, A22, lda, T, m2, H[7], m2, depth - 1, base);
     /* H8 = H1 + H3, H9 = H8 + H4 */
     plus(n2, m2, H[1], m2, H[3], m2, H[8], m2);
     plus(n2, m2, H[8], m2, H[4], m2, H[9], m2);
@@ -419,7 +441,7 @@ static void strassen_winograd_rec(int64_t n, int64_t p, int64_t m, const double 
  * "StrassenNaiv", last paragraph).  variant 0 = StrassenNaiv, 1 = StrassenWinograd. */
 static int strassen_embedded(int variant, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda,
                              const double *B, int64_t ldb, double *C, int64_t ldc, int depth, int64_t Np,
-                             int64_t Pp, int64_t Mp) {
+                             int64_t Pp, int64_t Mp, const struct strassen_base *base) {
     if (N == 0 || M == 0) return 0;
     if (depth < 0 || Np < N || Pp < P || Mp < M) return -1;
     int64_t q = (int64_t)1 << depth;
@@ -430,9 +452,9 @@ static int strassen_embedded(int variant, int64_t N, int64_t P, int64_t M, const
     for (int64_t i = 0; i < P; ++i)
         for (int64_t j = 0; j < M; ++j) AT(Bt, Mp, i, j) = AT(B, ldb, i, j);
     if (variant == 0)
-        strassen_rec(Np, Pp, Mp, At, Pp, Bt, Mp, Ct, Mp, depth);
+        strassen_rec(Np, Pp, Mp, At, Pp, Bt, Mp, Ct, Mp, depth, base);
     else
-        strassen_winograd_rec(Np, Pp, Mp, At, Pp, Bt, Mp, Ct, Mp, depth);
+        strassen_winograd_rec(Np, Pp, Mp, At, Pp, Bt, Mp, Ct, Mp, depth, base);
     for (int64_t i = 0; i < N; ++i)
         for (int64_t j = 0; j < M; ++j) AT(C, ldc, i, j) = AT(Ct, Mp, i, j);
     free(At);
@@ -450,7 +472,7 @@ int oracle_strassen_naiv(int64_t N, int64_t P, int64_t M, const double *A, int64
         oracle_strassen_paper_rule(N, P, M, &depth, &Y);
         Np = Pp = Mp = Y;
     }
-    return strassen_embedded(0, N, P, M, A, lda, B, ldb, C, ldc, depth, Np, Pp, Mp);
+    return strassen_embedded(0, N, P, M, A, lda, B, ldb, C, ldc, depth, Np, Pp, Mp, &naive_base);
 }
 
 int oracle_strassen_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
@@ -460,7 +482,23 @@ int oracle_strassen_winograd(int64_t N, int64_t P, int64_t M, const double *A, i
         oracle_strassen_paper_rule(N, P, M, &depth, &Y);
         Np = Pp = Mp = Y;
     }
-    return strassen_embedded(1, N, P, M, A, lda, B, ldb, C, ldc, depth, Np, Pp, Mp);
+    return strassen_embedded(1, N, P, M, A, lda, B, ldb, C, ldc, depth, Np, Pp, Mp, &naive_base);
+}
+
+/* Strassen (variant 0, section "StrassenNaiv") or Strassen-Winograd (variant 1,
+ * section "StrassenWinograd") recursion of `depth` levels whose base product is
+ * the split product (beta, s) instead of NaivStandard: the operand sums and the
+ * combinations of H1..H7 are the same FP64 additions, in the printed order.  A
+ * and B are embedded in zero matrices whose sizes are the smallest multiples of
+ * 2^depth >= N, P, M. */
+int oracle_strassen_emulated(int variant, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda,
+                             const double *B, int64_t ldb, double *C, int64_t ldc, int depth, int beta, int s) {
+    if (variant < 0 || variant > 1 || depth < 0 || depth > 6) return -1;
+    if (beta < 2 || beta > 12 || s < 1 || beta * s > 62) return -1;
+    const struct strassen_base base = {beta, s};
+    const int64_t q = (int64_t)1 << depth;
+    const int64_t Np = (N + q - 1) / q * q, Pp = (P + q - 1) / q * q, Mp = (M + q - 1) / q * q;
+    return strassen_embedded(variant, N, P, M, A, lda, B, ldb, C, ldc, depth, Np, Pp, Mp, &base);
 }
 
 /* ------------------------------------------------------------- the truth */

@@ -8,6 +8,7 @@ completions and statistics.  `replay` drives a trace with Poisson arrivals.
 from __future__ import annotations
 
 import ctypes
+import gc
 import time
 
 from ._native import Completion, Request, ServerStats, check, lib
@@ -119,23 +120,31 @@ def replay(server: Server, trace, a_pool, b_pool, c_pool, time_scale: float = 1.
     Each request writes its own region of c_pool (rows of width M, starting at
     row (id * 1117) mod capacity), so concurrent requests rarely alias.
     Returns (stats, completions)."""
-    import torch
-
-    t0 = time.perf_counter()
     rows_c = c_pool.shape[0] * c_pool.shape[1]
     flat_c = c_pool.view(-1)
-    for req in trace:
-        due = t0 + req["arrival_s"] * time_scale
-        while True:
-            now = time.perf_counter()
-            if now >= due:
-                break
-            if due - now > 2e-3:
-                time.sleep(due - now - 1e-3)
-        n, p, m = req["N"], req["P"], req["M"]
-        start = (req["id"] * 1117 * 4096) % max(1, rows_c - n * m)
-        c = flat_c[start: start + n * m].view(n, m)
-        server.submit(a_pool[:n, :p], b_pool[:p, :m], c, tier=req["tier"], tag=req["id"])
+    # A full collection of a large Python heap stalls the submitting thread for
+    # tens of milliseconds, which would arrive as a burst of late requests: the
+    # collector stays off while the trace is submitted.
+    gc.collect()
+    was_enabled = gc.isenabled()
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        for req in trace:
+            due = t0 + req["arrival_s"] * time_scale
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                if due - now > 2e-3:
+                    time.sleep(due - now - 1e-3)
+            n, p, m = req["N"], req["P"], req["M"]
+            start = (req["id"] * 1117 * 4096) % max(1, rows_c - n * m)
+            c = flat_c[start: start + n * m].view(n, m)
+            server.submit(a_pool[:n, :p], b_pool[:p, :m], c, tier=req["tier"], tag=req["id"])
+    finally:
+        if was_enabled:
+            gc.enable()
     rc = server.wait()
     comps = server.poll(len(trace) + 16)
     if rc != 0:

@@ -417,3 +417,59 @@ def test_unrolled_grouping_by_exact_rationals(orc, u):
         for k in range(full, p):
             aux = rn(aux + prods[k])
         assert orc.naiv_unrolled(a, b, u)[0, 0] == float(aux)
+
+
+# ------------------------------------- Strassen levels over the split product
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("shape", [(17, 33, 12), (40, 31, 23), (8, 8, 8), (5, 3, 9)])
+def test_strassen_emulated_exact_on_integers(orc, variant, depth, shape):
+    """Integer entries in [-8, 8]: after at most 3 levels every operand sum is an
+    integer below 2^7 * 8, which 3 BF16-width digits (beta = 7) hold exactly, and
+    every H and C combination is an exact integer sum -- so the recursion must
+    reproduce the exact product.  A dropped H, a wrong sign or a crossed
+    quadrant changes some entry."""
+    n, p, m = shape
+    a = S.integers(n, p, S.stream_seed(0, 300 + n + depth))
+    b = S.integers(p, m, S.stream_seed(0, 400 + m + depth))
+    ref = (a.astype(np.int64) @ b.astype(np.int64)).astype(np.float64)
+    assert np.array_equal(orc.strassen_emulated(a, b, variant, depth, 7, 3), ref)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_strassen_emulated_depth_zero_is_the_split_product(orc, variant):
+    a = S.loguniform(23, 41, 131)
+    b = S.loguniform(41, 19, 132)
+    for beta, s in ((7, 8), (5, 6)):
+        assert np.array_equal(orc.strassen_emulated(a, b, variant, 0, beta, s), orc.split_product(a, b, beta, s))
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_strassen_emulated_one_level_structure(orc, variant):
+    """On a 2x2 block matrix whose blocks are single entries, one level with a base
+    that is exact for these integers gives the 2x2 product: each of the 8 sign
+    patterns of a single nonzero in A against all-ones B isolates one quadrant term."""
+    ones = np.ones((2, 2))
+    for i in range(2):
+        for k in range(2):
+            a = np.zeros((2, 2))
+            a[i, k] = 3.0
+            got = orc.strassen_emulated(a, ones * 5.0, variant, 1, 7, 2)
+            assert np.array_equal(got, a @ (ones * 5.0))
+            got = orc.strassen_emulated(ones * 5.0, a, variant, 1, 7, 2)
+            assert np.array_equal(got, (ones * 5.0) @ a)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("depth", [1, 2])
+def test_strassen_emulated_error_tier(orc, variant, depth):
+    """Reals: the FP64 operand sums and H combinations add a few ulps of
+    ||A|| ||B|| per level, far inside the 1e-14 tier 8 BF16 slices serve."""
+    a = S.uniform(48, 40, 141)
+    b = S.uniform(40, 36, 142)
+    truth = orc.dot2_product(a, b)
+    err = orc.rel_inf_error(orc.strassen_emulated(a, b, variant, depth, 7, 8), truth, a, b)
+    assert err <= 1e-14
+    # and the recursion is not the base product under another name
+    assert not np.array_equal(orc.strassen_emulated(a, b, variant, depth, 7, 8), orc.split_product(a, b, 7, 8))
