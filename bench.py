@@ -313,6 +313,47 @@ def tall_inner_shape(dev):
             "rel_inf_err_sampled": sampled_error(c, a, b, norm_a, norm_b, rows)}
 
 
+def strassen_over_emulated(ta, tb, a, b, norm_a, norm_b, rows, truth):
+    """Strassen / Strassen-Winograd levels over the emulated product (8 BF16
+    slices): 8192^3 on the bench inputs with 0..2 levels (sampled error), and
+    16384^3 with 0..2 levels on the bench inputs tiled 2 x 2 (time only).
+    TFLOP/s is 2NPM / t throughout."""
+    import torch
+
+    import paper_1106_1347_gb300 as mm
+
+    res = {}
+    n = a.shape[0]
+    c = torch.empty((n, n), dtype=torch.float64, device=ta.device)
+    for variant, label in ((0, "strassen"), (1, "strassen_winograd")):
+        for levels in (0, 1, 2):
+            if variant == 1 and levels == 0:
+                continue
+            name = "emulated" if levels == 0 else f"{label}_{levels}"
+            ms = timed(lambda: mm.strassen_emulated(ta, tb, variant=variant, levels=levels, nslices=8, out=c), 3)
+            res.setdefault("8192", {})[name] = {
+                "ms": ms, "tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+                "rel_inf_err_sampled": sampled_error(c, a, b, norm_a, norm_b, rows, truth)}
+    del c
+    torch.cuda.empty_cache()
+    big = 2 * n
+    ta2 = ta.repeat(2, 2)
+    tb2 = tb.flip(0).repeat(2, 2)
+    c2 = torch.empty((big, big), dtype=torch.float64, device=ta.device)
+    for variant, label in ((0, "strassen"), (1, "strassen_winograd")):
+        for levels in (0, 1, 2):
+            if variant == 1 and levels == 0:
+                continue
+            name = "emulated" if levels == 0 else f"{label}_{levels}"
+            ms = timed(lambda: mm.strassen_emulated(ta2, tb2, variant=variant, levels=levels, nslices=8, out=c2), 2)
+            res.setdefault(str(big), {})[name] = {"ms": ms, "tflops": 2.0 * big ** 3 / (ms * 1e-3) / 1e12}
+            torch.cuda.empty_cache()
+    del ta2, tb2, c2
+    torch.cuda.empty_cache()
+    res["inputs"] = "8192: the bench's log-uniform A, B; 16384: A tiled 2x2, B row-reversed and tiled 2x2"
+    return res
+
+
 def grouped_vs_single(dev, count=256):
     """`count` products with the serving stream's shapes (N, P, M log-uniform on
     [32, 4096]), 8 BF16 slices: one grouped launch per kernel against one
@@ -714,6 +755,7 @@ def run_ours(args):
             out["shape_4096x16384x4096"] = tall_inner_shape(dev)
             out["badly_scaled_2048"] = badly_scaled_errors(dev)
             out["grouped_vs_single"] = grouped_vs_single(dev)
+            out["strassen_over_emulated"] = strassen_over_emulated(ta, tb, a, b, norm_a, norm_b, rows, truth)
             torch.cuda.empty_cache()
         if not args.no_serve:
             del ha, hb, hc

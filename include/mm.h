@@ -292,6 +292,34 @@ int mm_emulated_group(const mm_problem *probs, int32_t count, int32_t kind, int3
                       size_t ws_bytes, void *stream);
 
 /*
+ * Strassen levels over the FP64-accurate emulated product (no counterpart in
+ * the paper as such: the recursion of sections "StrassenNaiv" (variant 0) and
+ * "StrassenWinograd" (variant 1) with mm_emulated's split product as the base
+ * case instead of NaivStandard).  C = A B with
+ *   - A and B embedded in zero matrices whose sizes Np, Pp, Mp are the
+ *     smallest multiples of 2^levels >= N, P, M;
+ *   - at each of `levels` levels (0..4) the operands of H1..H7 formed by the
+ *     FP64 additions of the section's formulas, in the printed order, and
+ *     the C quadrants by its printed sums of the H's, left to right;
+ *   - the 7^levels products at the bottom computed as mm_emulated does (slice
+ *     format `kind`, slice count from nslices / tier as for mm_emulated), all
+ *     in one grouped launch.
+ * levels = 0 is mm_emulated itself.  The result is bit-identical to the CPU
+ * oracle's restatement of this definition.  Normwise error: the base
+ * product's plus a few units of 2^-53 ||A|| ||B|| per level from the FP64
+ * sums.  Workspace (device, caller-owned): the padded copies when padding is
+ * needed, every level's operand sums and H blocks, and the grouped product's
+ * workspace, as mm_strassen_emulated_workspace_bytes reports (0 for invalid
+ * arguments).  Argument rules and errors as mm_emulated; MM_ERR_ARG for a
+ * variant other than 0 or 1 or levels outside 0..4.
+ */
+size_t mm_strassen_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t variant, int32_t levels,
+                                            int32_t kind, int32_t nslices, double tier);
+int mm_strassen_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                         double *C, int64_t ldc, int32_t variant, int32_t levels, int32_t kind, int32_t nslices,
+                         double tier, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Serving loop (spec serving; no counterpart in the paper).  A server
  * owns a worker thread and K streams and serves requests C = A B with host
  * operands and a requested accuracy tier:

@@ -13,7 +13,7 @@ import ctypes
 
 from ._native import KernelStat, MMError, check, lib
 
-__all__ = ["naive", "naive_unrolled", "kahan", "winograd", "winograd_scaled", "winograd_rowcol_scaled", "strassen", "strassen_winograd", "tune_strassen", "norm_inf",
+__all__ = ["naive", "naive_unrolled", "kahan", "winograd", "winograd_scaled", "winograd_rowcol_scaled", "strassen", "strassen_winograd", "strassen_emulated", "tune_strassen", "norm_inf",
            "emulated", "emulated_host", "emulated_group", "emulated_noalloc", "emulated_slices", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
            "SLICE_FP8E4M3"]
 
@@ -183,6 +183,18 @@ def emulated(a, b, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
     ws = _ws(need, a.device)
     check("mm_emulated", lib().mm_emulated(*_gemm_args(a, b, c, n, p, m), kind, nslices, float(tier), _ptr(ws), need,
                                            _stream(a.device)))
+    return c
+
+
+def strassen_emulated(a, b, variant=0, levels=1, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
+    """Strassen (variant 0) or Strassen-Winograd (1) levels over the emulated
+    product: mm_strassen_emulated (see include/mm.h)."""
+    a, b, c, n, p, m = _prep(a, b, out)
+    need = lib().mm_strassen_emulated_workspace_bytes(n, p, m, int(variant), int(levels), kind, nslices, tier)
+    ws = _ws(need, a.device)
+    check("mm_strassen_emulated", lib().mm_strassen_emulated(*_gemm_args(a, b, c, n, p, m), int(variant), int(levels),
+                                                             kind, nslices, float(tier), _ptr(ws), need,
+                                                             _stream(a.device)))
     return c
 
 

@@ -62,6 +62,8 @@ SIGNATURES = {
     "mm_strassen": (ctypes.c_int, GEMM + [i32, vp, sz, vp]),
     "mm_strassen_winograd_workspace_bytes": (sz, [i64, i64, i64, i32]),
     "mm_strassen_winograd": (ctypes.c_int, GEMM + [i32, vp, sz, vp]),
+    "mm_strassen_emulated_workspace_bytes": (sz, [i64, i64, i64, i32, i32, i32, i32, dbl]),
+    "mm_strassen_emulated": (ctypes.c_int, GEMM + [i32, i32, i32, i32, dbl, vp, sz, vp]),
     "mm_emulated_workspace_bytes": (sz, [i64, i64, i64, i32, i32, dbl]),
     "mm_emulated_host_workspace_bytes": (sz, [i64, i64, i64, i32, i32, dbl]),
     "mm_emulated_host": (ctypes.c_int, GEMM + [i32, i32, dbl, vp, sz, vp]),

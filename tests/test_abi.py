@@ -78,6 +78,17 @@ def test_host_side_queries_and_checks(native):
     bf = lib.mm_emulated_workspace_bytes(1024, 1024, 1024, 0, 6, 1e-14)
     f8 = lib.mm_emulated_workspace_bytes(1024, 1024, 1024, 1, 6, 1e-14)
     assert 0 < f8 < bf
+    # Strassen levels over the emulated product: variant 0/1, levels 0..4
+    assert lib.mm_strassen_emulated_workspace_bytes(512, 512, 512, 0, 1, 0, 8, 1e-14) > \
+        lib.mm_emulated_workspace_bytes(256, 256, 256, 0, 8, 1e-14) * 7
+    assert lib.mm_strassen_emulated_workspace_bytes(512, 512, 512, 2, 1, 0, 8, 1e-14) == 0
+    assert lib.mm_strassen_emulated_workspace_bytes(512, 512, 512, 0, 5, 0, 8, 1e-14) == 0
+    assert lib.mm_strassen_emulated(8, 8, 8, fake, 8, ctypes.c_void_p(0x30000), 8, ctypes.c_void_p(0x50000), 8, 2, 1, 0,
+                                    8, 1e-14, None, 0, None) == -1
+    assert lib.mm_strassen_emulated(8, 8, 8, fake, 8, ctypes.c_void_p(0x30000), 8, ctypes.c_void_p(0x50000), 8, 0, 5, 0,
+                                    8, 1e-14, None, 0, None) == -1
+    assert lib.mm_strassen_emulated(8, 8, 8, fake, 8, ctypes.c_void_p(0x30000), 8, ctypes.c_void_p(0x50000), 8, 0, 1, 0,
+                                    8, 1e-14, None, 0, None) == -6  # no workspace
     # the paper's Strassen rule beyond 2401 innermost launches is refused
     assert lib.mm_strassen_workspace_bytes(4096, 4096, 4096, 0) == 0
     assert lib.mm_strassen(4096, 4096, 4096, fake, 4096, ctypes.c_void_p(0x30000), 4096, ctypes.c_void_p(0x10000000000),

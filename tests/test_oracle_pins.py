@@ -473,3 +473,16 @@ def test_strassen_emulated_error_tier(orc, variant, depth):
     assert err <= 1e-14
     # and the recursion is not the base product under another name
     assert not np.array_equal(orc.strassen_emulated(a, b, variant, depth, 7, 8), orc.split_product(a, b, 7, 8))
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_sampled_one_level_helper_matches_the_oracle(orc, variant):
+    """The sampled-entry helper the full-size GPU parity test uses agrees bit for
+    bit with the oracle's full recursion (one level, log-uniform inputs)."""
+    from strassen_sampled import one_level_sampled
+
+    a = S.loguniform(36, 44, 151)
+    b = S.loguniform(44, 30, 152)
+    full = orc.strassen_emulated(a, b, variant, 1, 7, 8)
+    rows, cols = [0, 5, 17, 18, 35], [0, 3, 14, 15, 29]
+    assert np.array_equal(one_level_sampled(orc, a, b, variant, rows, cols, 7, 8), full[np.ix_(rows, cols)])
