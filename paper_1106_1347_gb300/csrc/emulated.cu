@@ -13,11 +13,13 @@
 //
 // Kernels (all integer work on the FP64 bit patterns; FP64 arithmetic on this
 // part runs at ~1/100 of the BF16 tensor rate, so none is spent per slice):
-//   split_rows  -- one warp per row of A: max |A_ik| by integer max on the bit
-//                  patterns, then the digits, written as BF16 slices [s][N][P]
-//                  (K-major, coalesced).
-//   col_max / split_cols -- per-column maxima of B, then digits transposed
-//                  through shared memory into slices [s][M][P] (K-major).
+//   split_rows  -- one CTA per row of A: max |A_ik| by integer max on the bit
+//                  patterns (the row held in registers), then the digits,
+//                  written as slices [s][N][P] (K-major, 16-byte stores).
+//   col_max / split_cols -- per-column maxima of B, then each thread turns
+//                  32 consecutive k of one column into digits and stores them
+//                  as K-major slice rows [s][M][P] (the transpose happens in
+//                  registers).
 //   slice_gemm  -- (slice_gemm.cuh, instantiated per format and slice count)
 //                  persistent, one CTA per SM looping over 128x64 output
 //                  tiles.  Warp 0 issues TMA loads of all s slices of a
@@ -92,77 +94,145 @@ __device__ __forceinline__ int64_t round_scaled(double x, int sh) {
     return neg ? -(int64_t)q : (int64_t)q;
 }
 
-// Balanced base-2^beta digits, most significant first: dig[0] is the top digit.
-__device__ __forceinline__ void balanced_digits(int64_t V, int s, int beta, int (&dig)[8]) {
-    const int base = 1 << beta, half = base >> 1;
+// Eight consecutive elements of one slice row at a time.  V[u] holds
+// RN(x_u 2^sh) on entry; its balanced base-2^beta digits are peeled off from
+// the least significant one (low digits in [-2^(beta-1), 2^(beta-1)), the
+// rest is the top digit), and digit t of all eight goes to slice s-1-t as one
+// vector store: 16 bytes of BF16 or 8 bytes of E4M3 at dst0 + (s-1-t) * stride
+// (dst0: slice 0 at this row and column, 16-byte aligned for BF16, 8 for E4M3).
+// Every index is a compile-time constant, so nothing leaves registers.
+template <int KIND>
+__device__ __forceinline__ void store_digits8(int64_t (&V)[8], int s, unsigned char *dst0, int64_t stride) {
+    constexpr int beta = fmt_beta(KIND), base = 1 << beta, half = base >> 1;
 #pragma unroll
-    for (int t = 0; t < 7; ++t) {
-        if (t < s - 1) {
-            int d = (int)(V & (base - 1));
-            if (d >= half) d -= base;
-            dig[s - 1 - t] = d;
-            V = (V - d) >> beta;
+    for (int t = 0; t < 8; ++t) {
+        if (t < s) {
+            int d[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (t < s - 1) {
+                    int x = (int)(V[u] & (base - 1));
+                    if (x >= half) x -= base;
+                    d[u] = x;
+                    V[u] = (V[u] - x) >> beta;
+                } else {
+                    d[u] = (int)V[u];
+                }
+            }
+            unsigned char *dst = dst0 + (int64_t)(s - 1 - t) * stride;
+            if (KIND == MM_SLICE_FP8E4M3) {
+                uint32_t w[2] = {0u, 0u};
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    w[u >> 2] |= (uint32_t)__nv_cvt_float_to_fp8((float)d[u], __NV_SATFINITE, __NV_E4M3)
+                                 << (8 * (u & 3));
+                *reinterpret_cast<uint2 *>(dst) = make_uint2(w[0], w[1]);
+            } else {
+                uint32_t w[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn((float)d[2 * u], (float)d[2 * u + 1]);
+                    w[u] = *reinterpret_cast<const uint32_t *>(&h2);
+                }
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
         }
     }
-    dig[0] = (int)V;
 }
 
-// Two digits stored side by side in a slice row (element size 2 or 1 bytes).
-__device__ __forceinline__ void store_digit_pair(unsigned char *dst, int d0, int d1, int kind) {
-    if (kind == MM_SLICE_FP8E4M3) {
-        const uint16_t lo = __nv_cvt_float_to_fp8((float)d0, __NV_SATFINITE, __NV_E4M3);
-        const uint16_t hi = __nv_cvt_float_to_fp8((float)d1, __NV_SATFINITE, __NV_E4M3);
-        *reinterpret_cast<uint16_t *>(dst) = (uint16_t)(lo | (hi << 8));
+// x[c .. c+8) of a row (zeros at and past P), with 16-byte loads when the row
+// start is 16-byte aligned and all eight lie before P.
+__device__ __forceinline__ void load8(const double *__restrict__ a, int64_t c, int64_t P, bool vec, double (&v)[8]) {
+    if (vec && c + 8 <= P) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double2 x = __ldg(reinterpret_cast<const double2 *>(a + c) + u);
+            v[2 * u] = x.x;
+            v[2 * u + 1] = x.y;
+        }
     } else {
-        *reinterpret_cast<__nv_bfloat162 *>(dst) = __floats2bfloat162_rn((float)d0, (float)d1);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = (c + u < P) ? __ldg(a + c + u) : 0.0;
     }
 }
-__device__ __forceinline__ void store_digit(unsigned char *dst, int d, int kind) {
-    if (kind == MM_SLICE_FP8E4M3)
-        *dst = (unsigned char)__nv_cvt_float_to_fp8((float)d, __NV_SATFINITE, __NV_E4M3);
-    else
-        *reinterpret_cast<__nv_bfloat16 *>(dst) = __float2bfloat16_rn((float)d);
-}
 
+constexpr int kRowThreads = 256;
+constexpr int64_t kRowResident = 4 * 8 * kRowThreads;  // row elements one CTA holds in registers
 
-// One warp per row of A: max |A_ik| by integer max on the bit patterns, then
-// the digits, written as slices [s][Nr][Pp] (BF16 or FP8-E4M3).
+// One CTA per row of A: max |A_ik| by integer max on the bit patterns (block
+// reduction), then the digits, written as slices [s][Nr][Pp] (BF16 or
+// FP8-E4M3); columns [P, Pp) get zero digits so every K-block read is defined.
+// Rows of up to 8192 elements stay in registers between the two passes, so A
+// is read from memory once; longer rows are read twice (the second time
+// mostly from L2: one row per CTA keeps few rows in flight).  `red` is 8
+// words of shared memory.
 template <int KIND>
-__device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int lane) {
-    const double *a = p.A + row * p.lda;
+__device__ __forceinline__ void split_row(const SplitA &p, int64_t row, unsigned long long *red) {
+    const double *__restrict__ a = p.A + row * p.lda;
     const int64_t P = p.P, Pp = p.Pp;
-    const int s = p.s;
+    const int s = p.s, tid = threadIdx.x;
+    const bool vec = (((uintptr_t)a) & 15) == 0;
+    const bool resident = Pp <= kRowResident;
+    double v[4][8];
     unsigned long long mx = 0;
-    for (int64_t c = lane; c < P; c += 32) mx = umax64(mx, absbits(a[c]));
+    if (resident) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            load8(a, (int64_t)q * 8 * kRowThreads + 8 * tid, P, vec, v[q]);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mx = umax64(mx, absbits(v[q][u]));
+        }
+    } else {
+        for (int64_t c = 8 * tid; c < P; c += 8 * kRowThreads) {
+            double x[8];
+            load8(a, c, P, vec, x);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mx = umax64(mx, absbits(x[u]));
+        }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         mx = umax64(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mx, o));
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < kRowThreads / 32; ++w) mx = umax64(mx, red[w]);
+    __syncthreads();  // `red` is reused by the next row
     const int e = frexp_exp_bits(mx);
-    if (lane == 0) p.ea[row] = e;
+    if (tid == 0) p.ea[row] = e;
     constexpr int beta = fmt_beta(KIND), es = fmt_esize(KIND);
     const int sh = beta * s - 1 - e;
-    // Columns [P, Pp) are written as zero digits so every K-block read stays defined.
-    for (int64_t c0 = 0; c0 < Pp; c0 += 64) {
-        const int64_t c = c0 + 2 * lane;
-        if (c >= Pp) break;
-        int d0[8], d1[8];
-        balanced_digits(c < P ? round_scaled(a[c], sh) : 0, s, beta, d0);
-        const bool two = c + 1 < Pp;
-        balanced_digits((two && c + 1 < P) ? round_scaled(a[c + 1], sh) : 0, s, beta, d1);
-        for (int t = 0; t < s; ++t) {
-            unsigned char *dst = p.slices + (((int64_t)t * p.Nr + row) * Pp + c) * es;
-            if (two)
-                store_digit_pair(dst, d0[t], d1[t], KIND);
-            else
-                store_digit(dst, d0[t], KIND);
+    const int64_t stride = (int64_t)p.Nr * Pp * es;
+    unsigned char *row0 = p.slices + row * Pp * es;
+    // Pp is a multiple of 8 (BF16) or 16 (E4M3) elements: a group of eight
+    // starting before Pp ends by Pp.
+    if (resident) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t c = (int64_t)q * 8 * kRowThreads + 8 * tid;
+            if (c < Pp) {
+                int64_t V[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) V[u] = round_scaled(v[q][u], sh);
+                store_digits8<KIND>(V, s, row0 + c * es, stride);
+            }
+        }
+    } else {
+        for (int64_t c = 8 * tid; c < Pp; c += 8 * kRowThreads) {
+            double x[8];
+            load8(a, c, P, vec, x);
+            int64_t V[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) V[u] = round_scaled(x[u], sh);
+            store_digits8<KIND>(V, s, row0 + c * es, stride);
         }
     }
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(256) split_rows_kernel(const SplitA p) {
-    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (row < p.N) split_row<KIND>(p, row, threadIdx.x & 31);
+__global__ void __launch_bounds__(kRowThreads, 2) split_rows_kernel(const SplitA p) {
+    __shared__ unsigned long long red[kRowThreads / 32];
+    split_row<KIND>(p, blockIdx.x, red);
 }
 
 
@@ -179,60 +249,45 @@ __global__ void __launch_bounds__(128) col_max_kernel(const SplitB p) {
     col_max_part(p, (int64_t)blockIdx.x * 128 + threadIdx.x, (int64_t)blockIdx.y * 256);
 }
 
-constexpr int SC_K = 32, SC_J = 64;
+// Column split tiles: 64 columns of B by 128 k.  Lane l of warp w owns column
+// j = j0 + 8 w + l / 4 and the k-groups of eight g = l % 4 + 4 r (r < 4): it
+// reads them down its column and writes each group's digits straight into
+// the K-major slice row j as one vector store per slice -- the transpose
+// happens in registers.  Four adjacent lanes cover 32 consecutive k of one
+// column, so each load instruction reads 64-byte runs of four rows of B and
+// each store fills whole 32-byte sectors (64 bytes of BF16 or 32 of E4M3 per
+// slice row).
+constexpr int SC_J = 64, SC_K = 128;
 
-// A 32 (k) x 64 (j) tile of B: digits, transposed through shared memory into
-// the K-major slices [s][Mr][Pp] (each slice row is one column of B).
 template <int KIND>
-__device__ __forceinline__ void split_cols_tile(const SplitB &p, int64_t jt, int64_t kt, unsigned char *sm) {
-    constexpr int LD = SC_K + 2;
-    const int tid = threadIdx.x;
-    const int64_t j0 = jt * SC_J, k0 = kt * SC_K;
-    const int64_t P = p.P, M = p.M, Pp = p.Pp;
+__device__ __forceinline__ void split_cols_tile(const SplitB &p, int64_t jt, int64_t kt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, kg = lane & 3;
+    const int64_t j = jt * SC_J + 8 * warp + (lane >> 2);
+    if (j >= p.M) return;
+    const int64_t P = p.P, Pp = p.Pp, ldb = p.ldb;
     const int s = p.s;
-    const int jj = tid & 63;
-    const int64_t j = j0 + jj;
-    const int f = (j < M) ? frexp_exp_bits(p.colmax[j]) : 0;
-    if (kt == 0 && tid < 64 && j < M) p.fb[j] = f;
+    const int f = frexp_exp_bits(p.colmax[j]);
+    if (kt == 0 && kg == 0) p.fb[j] = f;
     constexpr int beta = fmt_beta(KIND), es = fmt_esize(KIND);
     const int sh = beta * s - 1 - f;
+    const double *__restrict__ bj = p.B + j;
+    unsigned char *row0 = p.slices + j * Pp * es;
+    const int64_t stride = (int64_t)p.Mr * Pp * es;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int kk = (tid >> 6) + 4 * r;
-        const int64_t k = k0 + kk;
-        int dig[8];
-        balanced_digits((k < P && j < M) ? round_scaled(p.B[k * p.ldb + j], sh) : 0, s, beta, dig);
-        for (int t = 0; t < s; ++t) store_digit(sm + ((t * SC_J + jj) * LD + kk) * es, dig[t], KIND);
-    }
-    __syncthreads();
-    // Write each slice's 64 columns x 32 k as K-major rows (16 threads per row, two digits each).
-    for (int t = 0; t < s; ++t) {
+    for (int r = 0; r < 4; ++r) {
+        const int64_t k0 = kt * SC_K + 8 * (kg + 4 * r);
+        if (k0 >= Pp) break;  // Pp is a multiple of 8 (BF16) or 16 (E4M3)
+        int64_t V[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int w = tid + 256 * q;
-            const int jr = w >> 4, kp = (w & 15) * 2;
-            const int64_t gj = j0 + jr, gk = k0 + kp;
-            if (gj >= M || gk >= Pp) continue;  // [P, Pp) receives zero digits
-            const unsigned char *src = sm + ((t * SC_J + jr) * LD + kp) * es;
-            unsigned char *dst = p.slices + (((int64_t)t * p.Mr + gj) * Pp + gk) * es;
-            if (gk + 1 < Pp) {
-                if (es == 2)
-                    *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(src);
-                else
-                    *reinterpret_cast<uint16_t *>(dst) = *reinterpret_cast<const uint16_t *>(src);
-            } else {
-                for (int b = 0; b < es; ++b) dst[b] = src[b];
-            }
-        }
+        for (int u = 0; u < 8; ++u) V[u] = (k0 + u < P) ? round_scaled(__ldg(bj + (k0 + u) * ldb), sh) : 0;
+        store_digits8<KIND>(V, s, row0 + k0 * es, stride);
     }
 }
 
 template <int KIND>
 __global__ void __launch_bounds__(256) split_cols_kernel(const SplitB p) {
-    extern __shared__ __align__(16) unsigned char sm[];  // [s][SC_J][SC_K + 2] elements
-    split_cols_tile<KIND>(p, blockIdx.x, blockIdx.y, sm);
+    split_cols_tile<KIND>(p, blockIdx.x, blockIdx.y);
 }
-
 
 
 // The grouped split kernels stride over their units (grid-stride loops), so
@@ -250,14 +305,14 @@ __global__ void __launch_bounds__(256) group_zero_colmax_kernel(const EmuProblem
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(256) group_split_rows_kernel(const EmuProblem *tab, const int64_t *begin,
-                                                               const GroupHeader *hdr) {
+__global__ void __launch_bounds__(kRowThreads, 2) group_split_rows_kernel(const EmuProblem *tab,
+                                                                          const int64_t *begin,
+                                                                          const GroupHeader *hdr) {
+    __shared__ unsigned long long red[kRowThreads / 32];
     const int64_t units = hdr->units[U_ROWS];
-    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {  // one row per unit
         const int g = find_problem(begin, hdr->count, u);
-        const SplitA &p = tab[g].spa;
-        const int64_t row = (u - begin[g]) * 8 + (threadIdx.x >> 5);
-        if (row < p.N) split_row<KIND>(p, row, threadIdx.x & 31);
+        split_row<KIND>(tab[g].spa, u - begin[g], red);
     }
 }
 
@@ -275,14 +330,12 @@ __global__ void __launch_bounds__(128) group_col_max_kernel(const EmuProblem *ta
 template <int KIND>
 __global__ void __launch_bounds__(256) group_split_cols_kernel(const EmuProblem *tab, const int64_t *begin,
                                                                const GroupHeader *hdr) {
-    extern __shared__ __align__(16) unsigned char sm[];
     const int64_t units = hdr->units[U_SPLITCOLS];
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const int g = find_problem(begin, hdr->count, u);
         const SplitB &p = tab[g].spb;
         const int64_t local = u - begin[g], nj = (p.M + SC_J - 1) / SC_J;
-        split_cols_tile<KIND>(p, local % nj, local / nj, sm);
-        __syncthreads();  // the next unit rewrites the shared tile
+        split_cols_tile<KIND>(p, local % nj, local / nj);
     }
 }
 
@@ -359,7 +412,6 @@ size_t slice_smem_bytes(int s) {
     return (size_t)stages * stage_bytes + 1024;
 }
 
-size_t split_cols_smem_bytes(int s, int kind) { return (size_t)s * SC_J * (SC_K + 2) * fmt_esize(kind); }
 
 }  // namespace
 
@@ -422,9 +474,9 @@ int split_b(const EmuWork &w, int64_t P, int64_t M, const double *B, int64_t ldb
     return mm::launch("emu_split_cols", st, [&] {
         dim3 g((unsigned)mm::ceil_div(M, SC_J), (unsigned)mm::ceil_div(w.L.Pp, SC_K));
         if (kind == MM_SLICE_FP8E4M3)
-            split_cols_kernel<MM_SLICE_FP8E4M3><<<g, 256, split_cols_smem_bytes(s, kind), st>>>(spb);
+            split_cols_kernel<MM_SLICE_FP8E4M3><<<g, 256, 0, st>>>(spb);
         else
-            split_cols_kernel<MM_SLICE_BF16><<<g, 256, split_cols_smem_bytes(s, kind), st>>>(spb);
+            split_cols_kernel<MM_SLICE_BF16><<<g, 256, 0, st>>>(spb);
     });
 }
 
@@ -435,9 +487,9 @@ int split_a_rows(const EmuWork &w, int64_t r0, int64_t n, int64_t P, const doubl
                      w.sa + (size_t)r0 * w.L.Pp * fmt_esize(kind)};
     return mm::launch("emu_split_rows", st, [&] {
         if (kind == MM_SLICE_FP8E4M3)
-            split_rows_kernel<MM_SLICE_FP8E4M3><<<(unsigned)mm::ceil_div(n, 8), 256, 0, st>>>(spa);
+            split_rows_kernel<MM_SLICE_FP8E4M3><<<(unsigned)n, kRowThreads, 0, st>>>(spa);
         else
-            split_rows_kernel<MM_SLICE_BF16><<<(unsigned)mm::ceil_div(n, 8), 256, 0, st>>>(spa);
+            split_rows_kernel<MM_SLICE_BF16><<<(unsigned)n, kRowThreads, 0, st>>>(spa);
     });
 }
 
@@ -702,7 +754,7 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
         rc = launch("emu_group_split_cols", st, [&] {
             const auto k = gl.kind == MM_SLICE_FP8E4M3 ? group_split_cols_kernel<MM_SLICE_FP8E4M3>
                                                        : group_split_cols_kernel<MM_SLICE_BF16>;
-            k<<<(unsigned)gl.grid[U_SPLITCOLS], 256, split_cols_smem_bytes(gl.s, gl.kind), st>>>(
+            k<<<(unsigned)gl.grid[U_SPLITCOLS], 256, 0, st>>>(
                 (const EmuProblem *)gl.tab, gl.begin[U_SPLITCOLS], (const GroupHeader *)gl.hdr);
         });
     if (rc) return rc;
@@ -769,7 +821,7 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
         if (!rc) rc = encode_slices(&e.tmB, sb, L.Mr, L.Pp, s, BN, kind);
         if (rc) return rc;
         for (int k = 0; k < 5; ++k) begin[k][i] = units[k];
-        units[U_ROWS] += ceil_div(q.N, 8);
+        units[U_ROWS] += q.N;
         units[U_COLMAX] += ceil_div(q.M, 128) * ceil_div(q.P, 256);
         units[U_SPLITCOLS] += ceil_div(q.M, SC_J) * ceil_div(L.Pp, SC_K);
         units[U_TILES] += (int64_t)e.prm.tiles_m * e.prm.tiles_n;
