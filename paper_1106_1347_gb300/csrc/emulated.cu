@@ -14,7 +14,7 @@
 // Kernels (all integer work on the FP64 bit patterns; FP64 arithmetic on this
 // part runs at ~1/100 of the BF16 tensor rate, so none is spent per slice):
 //   split_rows  -- one CTA per row of A: max |A_ik| by integer max on the bit
-//                  patterns (the row held in registers), then the digits,
+//                  patterns, then the digits (the row re-read from L2),
 //                  written as slices [s][N][P] (K-major, 16-byte stores).
 //   col_max / split_cols -- per-column maxima of B, then each thread turns
 //                  32 consecutive k of one column into digits and stores them
@@ -157,38 +157,25 @@ __device__ __forceinline__ void load8(const double *__restrict__ a, int64_t c, i
 }
 
 constexpr int kRowThreads = 256;
-constexpr int64_t kRowResident = 4 * 8 * kRowThreads;  // row elements one CTA holds in registers
 
 // One CTA per row of A: max |A_ik| by integer max on the bit patterns (block
 // reduction), then the digits, written as slices [s][Nr][Pp] (BF16 or
 // FP8-E4M3); columns [P, Pp) get zero digits so every K-block read is defined.
-// Rows of up to 8192 elements stay in registers between the two passes, so A
-// is read from memory once; longer rows are read twice (the second time
-// mostly from L2: one row per CTA keeps few rows in flight).  `red` is 8
-// words of shared memory.
+// The digit pass reads the row again, from L2: with one row per CTA only a
+// few rows per SM are in flight (about 40 MB over the GPU at 8192 columns),
+// so A crosses HBM once.  `red` is 8 words of shared memory.
 template <int KIND>
 __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, unsigned long long *red) {
     const double *__restrict__ a = p.A + row * p.lda;
     const int64_t P = p.P, Pp = p.Pp;
     const int s = p.s, tid = threadIdx.x;
     const bool vec = (((uintptr_t)a) & 15) == 0;
-    const bool resident = Pp <= kRowResident;
-    double v[4][8];
     unsigned long long mx = 0;
-    if (resident) {
+    for (int64_t c = 8 * tid; c < P; c += 8 * kRowThreads) {
+        double x[8];
+        load8(a, c, P, vec, x);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            load8(a, (int64_t)q * 8 * kRowThreads + 8 * tid, P, vec, v[q]);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) mx = umax64(mx, absbits(v[q][u]));
-        }
-    } else {
-        for (int64_t c = 8 * tid; c < P; c += 8 * kRowThreads) {
-            double x[8];
-            load8(a, c, P, vec, x);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) mx = umax64(mx, absbits(x[u]));
-        }
+        for (int u = 0; u < 8; ++u) mx = umax64(mx, absbits(x[u]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -206,31 +193,18 @@ __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, unsigned
     unsigned char *row0 = p.slices + row * Pp * es;
     // Pp is a multiple of 8 (BF16) or 16 (E4M3) elements: a group of eight
     // starting before Pp ends by Pp.
-    if (resident) {
+    for (int64_t c = 8 * tid; c < Pp; c += 8 * kRowThreads) {
+        double x[8];
+        load8(a, c, P, vec, x);
+        int64_t V[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int64_t c = (int64_t)q * 8 * kRowThreads + 8 * tid;
-            if (c < Pp) {
-                int64_t V[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) V[u] = round_scaled(v[q][u], sh);
-                store_digits8<KIND>(V, s, row0 + c * es, stride);
-            }
-        }
-    } else {
-        for (int64_t c = 8 * tid; c < Pp; c += 8 * kRowThreads) {
-            double x[8];
-            load8(a, c, P, vec, x);
-            int64_t V[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) V[u] = round_scaled(x[u], sh);
-            store_digits8<KIND>(V, s, row0 + c * es, stride);
-        }
+        for (int u = 0; u < 8; ++u) V[u] = round_scaled(x[u], sh);
+        store_digits8<KIND>(V, s, row0 + c * es, stride);
     }
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kRowThreads, 2) split_rows_kernel(const SplitA p) {
+__global__ void __launch_bounds__(kRowThreads, 4) split_rows_kernel(const SplitA p) {
     __shared__ unsigned long long red[kRowThreads / 32];
     split_row<KIND>(p, blockIdx.x, red);
 }
@@ -305,7 +279,7 @@ __global__ void __launch_bounds__(256) group_zero_colmax_kernel(const EmuProblem
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kRowThreads, 2) group_split_rows_kernel(const EmuProblem *tab,
+__global__ void __launch_bounds__(kRowThreads, 4) group_split_rows_kernel(const EmuProblem *tab,
                                                                           const int64_t *begin,
                                                                           const GroupHeader *hdr) {
     __shared__ unsigned long long red[kRowThreads / 32];
@@ -591,8 +565,9 @@ int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t 
     double *dC = (double *)w8;
     w8 += align_up((size_t)N * M * 8, 1024);
     const EmuWork w = emu_work(N, P, M, s, kind, w8);
-    // Up to 4 row blocks of whole tiles.
-    const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(4, ceil_div(N, 512)));
+    // Up to 8 row blocks of whole tiles: the first product waits for B and one
+    // block of A, and the last block's copy back trails the products.
+    const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(8, ceil_div(N, 512)));
     const int64_t R = ceil_div(ceil_div(N, nb), BM) * BM;
     std::vector<cudaEvent_t> ev;
     auto event = [&](cudaEvent_t *e) {
@@ -604,13 +579,19 @@ int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t 
         for (cudaEvent_t e : ev) cudaEventDestroy(e);  // released once their work completes
         return r;
     };
-    cudaEvent_t e0, eA, eC, eEnd;
+    // All uploads go through one copy stream in the order they are needed: B
+    // first (every product needs all of it), then the row blocks of A, so the
+    // link is not shared between B and A blocks that cannot start yet.
+    cudaEvent_t e0, eB, eA, eC, eEnd;
     cudaError_t e = event(&e0);
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.up, e0, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.down, e0, 0);
     if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(dB, (size_t)M * 8, B, (size_t)ldb * 8, (size_t)M * 8, P, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpy2DAsync(dB, (size_t)M * 8, B, (size_t)ldb * 8, (size_t)M * 8, P, cudaMemcpyHostToDevice, cs.up);
+    if (e == cudaSuccess) e = event(&eB);
+    if (e == cudaSuccess) e = cudaEventRecord(eB, cs.up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, eB, 0);
     if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
     rc = split_b(w, P, M, dB, M, s, kind, st);
     if (rc) return done(rc);
@@ -739,7 +720,7 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
         rc = launch("emu_group_split_rows", st, [&] {
             const auto k = gl.kind == MM_SLICE_FP8E4M3 ? group_split_rows_kernel<MM_SLICE_FP8E4M3>
                                                        : group_split_rows_kernel<MM_SLICE_BF16>;
-            k<<<(unsigned)gl.grid[U_ROWS], 256, 0, st>>>((const EmuProblem *)gl.tab, gl.begin[U_ROWS],
+            k<<<(unsigned)gl.grid[U_ROWS], kRowThreads, 0, st>>>((const EmuProblem *)gl.tab, gl.begin[U_ROWS],
                                                          (const GroupHeader *)gl.hdr);
         });
     if (rc) return rc;

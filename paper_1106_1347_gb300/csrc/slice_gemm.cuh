@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // kernel strides over its units, so its grid is a fixed size independent of
 // the batch: the serving loop captures the five launches once per slice
 // format and count in a CUDA graph and replays it for any batch.
-struct __align__(64) EmuProblem {
+struct EmuProblem {  // 128-byte aligned through its tensor maps
     CUtensorMap tmA, tmB;
     EmuParams prm;
     SplitA spa;
