@@ -742,11 +742,12 @@ def run_ours(args):
             e2e_step()
         torch.cuda.synchronize()
         gm = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps + 1)]
-        gm[0].record(stream)
-        for i in range(e2e_steps):
-            e2e_step()
-            gm[i + 1].record(stream)
-        torch.cuda.synchronize()
+        with ClockSampler(local) as clk_e2e:
+            gm[0].record(stream)
+            for i in range(e2e_steps):
+                e2e_step()
+                gm[i + 1].record(stream)
+            torch.cuda.synchronize()
         e2e_each = [gm[i].elapsed_time(gm[i + 1]) for i in range(e2e_steps)]
         e2e_ms = statistics.median(e2e_each)
         if not np.array_equal(hc[rows].numpy(), c[rows].cpu().numpy()):
@@ -754,6 +755,7 @@ def run_ours(args):
         out["e2e"] = {"value": flop / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                       "steps": e2e_steps, "statistic": "median of per-step CUDA-event times",
                       "ms_mean": statistics.mean(e2e_each), "ms_min": min(e2e_each), "ms_max": max(e2e_each),
+                      "ms_each": [round(x, 3) for x in e2e_each], "clocks": clk_e2e.summary(),
                       "h2d_bytes_per_step": int(a.nbytes + b.nbytes), "d2h_bytes_per_step": int(N * M * 8),
                       "call": "mm_emulated_host (pinned host A, B, C; copies overlapped with row-block products)"}
         del hws

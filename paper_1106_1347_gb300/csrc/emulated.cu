@@ -374,7 +374,6 @@ void fill_common(EmuParams &prm, int s, int kind) {
     prm.s = s;
     prm.stages = std::min(4, (int)((kSmemLimit - 2048) / stage_bytes));
     prm.chunk_blocks = std::max(1, fmt_pair_blocks(kind) / s);  // the exact length of diagonal s - 1
-    prm.hsplit = (s + 1) / 2;
     int cols = 32;
     while (cols < s * BN) cols <<= 1;
     prm.tmem_cols = cols;

@@ -52,7 +52,7 @@ struct SplitB {
 
 struct EmuParams {
     int64_t N, P, M;
-    int s, stages, chunk_blocks, hsplit, tmem_cols;
+    int s, stages, chunk_blocks, tmem_cols;
     int tiles_m, tiles_n;
     const int32_t *ea, *fb;
     double *C;
@@ -125,6 +125,13 @@ __device__ __forceinline__ uint32_t drain_due(uint32_t &cnt, uint32_t R, bool la
     }
     cnt = nc;
     return due;
+}
+
+// d = a * b + c with a 64-bit c (one multiply-add of the integer pipe).
+__device__ __forceinline__ int64_t mad_wide(int32_t a, int32_t b, int64_t c) {
+    int64_t d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
 }
 
 // One output tile of one problem: its slice tensor maps (kernel parameters or
@@ -283,7 +290,7 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
         const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h);
         uint32_t ev = 0;
         bool ok = true;
-        const int hsplit = c.hsplit;
+        constexpr int hsplit = (s + 1) / 2;  // diagonals [0, hsplit) sum into whi, the rest into wlo
         constexpr int beta = fmt_beta(KIND);
         const uint32_t R = drain_periods(CB, pair_blocks);
         for (int64_t id = blockIdx.x; id < total && ok; id += gridDim.x) {
@@ -305,20 +312,20 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                 }
                 mmdev::tc_fence_after();
                 const uint32_t due = drain_due(cnt, R, ch == nchunks - 1);
+                // Unrolled over the diagonals, so each one's weight is a constant and
+                // its accumulator array is known: one exact conversion and one
+                // 32 x 32 -> 64-bit multiply-add per value.
+#pragma unroll
                 for (int d = 0; d < s; ++d) {
                     if (!((due >> d) & 1u)) continue;
                     uint32_t v[32];
                     mmdev::tmem_ld_32x32b_x32(tbase + (uint32_t)(d * BN), v);
                     mmdev::tmem_wait_ld();
-                    if (d < hsplit) {
-                        const int sh = beta * (hsplit - 1 - d);
+                    const int32_t weight = 1 << (d < hsplit ? beta * (hsplit - 1 - d) : beta * (s - 1 - d));
+                    int64_t *acc = d < hsplit ? whi : wlo;
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) whi[k] += (int64_t)__float2int_rn(__uint_as_float(v[k])) << sh;
-                    } else {
-                        const int sh = beta * (s - 1 - d);
-#pragma unroll
-                        for (int k = 0; k < 32; ++k) wlo[k] += (int64_t)__float2int_rn(__uint_as_float(v[k])) << sh;
-                    }
+                    for (int k = 0; k < 32; ++k)
+                        acc[k] = mad_wide(__float2int_rn(__uint_as_float(v[k])), weight, acc[k]);
                 }
                 mmdev::tc_fence_before();
                 __syncwarp();
