@@ -247,13 +247,21 @@ __device__ __forceinline__ void split_cols_tile(const SplitB &p, int64_t jt, int
     const double *__restrict__ bj = p.B + j;
     unsigned char *row0 = p.slices + j * Pp * es;
     const int64_t stride = (int64_t)p.Mr * Pp * es;
+    // All 32 loads first, so they are in flight together.
+    double x[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t k0 = kt * SC_K + 8 * (kg + 4 * r);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[r][u] = (k0 + u < P) ? __ldg(bj + (k0 + u) * ldb) : 0.0;
+    }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int64_t k0 = kt * SC_K + 8 * (kg + 4 * r);
         if (k0 >= Pp) break;  // Pp is a multiple of 8 (BF16) or 16 (E4M3)
         int64_t V[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) V[u] = (k0 + u < P) ? round_scaled(__ldg(bj + (k0 + u) * ldb), sh) : 0;
+        for (int u = 0; u < 8; ++u) V[u] = round_scaled(x[r][u], sh);
         store_digits8<KIND>(V, s, row0 + k0 * es, stride);
     }
 }
@@ -367,23 +375,14 @@ int encode_slices(CUtensorMap *map, void *base, int64_t rows, int64_t Pp, int s,
     return MM_OK;
 }
 
-// Per-launch constants shared by every problem of one slice format and count.
-// A stage holds one K-block (64 bytes per slice row) of all s slices of A and B.
+// Per-launch constants shared by every problem of one slice format and count
+// (the rest -- stages, exact chunk, TMEM columns -- follow from s at compile time).
 void fill_common(EmuParams &prm, int s, int kind) {
-    const uint32_t stage_bytes = (uint32_t)s * (BM + BN) * KB_BYTES;
+    (void)kind;
     prm.s = s;
-    prm.stages = std::min(4, (int)((kSmemLimit - 2048) / stage_bytes));
-    prm.chunk_blocks = std::max(1, fmt_pair_blocks(kind) / s);  // the exact length of diagonal s - 1
-    int cols = 32;
-    while (cols < s * BN) cols <<= 1;
-    prm.tmem_cols = cols;
 }
 
-size_t slice_smem_bytes(int s) {
-    const uint32_t stage_bytes = (uint32_t)s * (BM + BN) * KB_BYTES;
-    const int stages = std::min(4, (int)((kSmemLimit - 2048) / stage_bytes));
-    return (size_t)stages * stage_bytes + 1024;
-}
+size_t slice_smem_bytes(int s) { return (size_t)slice_stages(s) * slice_stage_bytes(s) + 1024; }
 
 
 }  // namespace

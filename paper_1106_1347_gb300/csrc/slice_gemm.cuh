@@ -27,9 +27,24 @@ __host__ __device__ constexpr int fmt_bke(int kind) { return KB_BYTES / fmt_esiz
 __host__ __device__ constexpr int fmt_pair_blocks(int kind) {
     return (1 << (26 - 2 * fmt_beta(kind))) / fmt_bke(kind);
 }
+// Launch-wide constants of the slice product, functions of the slice format
+// and count only (so the kernel, templated on both, has them at compile time):
+// a stage holds one K-block (64 bytes per slice row) of all s slices of A and
+// B; up to 4 stages fit the shared memory; an exact chunk is the exact length
+// of diagonal s - 1; TMEM is allocated in powers of two >= 32 columns.
+constexpr int kSmemLimit = 232448;  // opt-in dynamic shared memory per block on sm_103
+__host__ __device__ constexpr uint32_t slice_stage_bytes(int s) { return (uint32_t)s * (BM + BN) * KB_BYTES; }
+__host__ __device__ constexpr int slice_stages(int s) {
+    return (int)((kSmemLimit - 2048) / slice_stage_bytes(s)) < 4 ? (int)((kSmemLimit - 2048) / slice_stage_bytes(s)) : 4;
+}
+__host__ __device__ constexpr int slice_chunk_blocks(int kind, int s) {
+    return fmt_pair_blocks(kind) / s > 1 ? fmt_pair_blocks(kind) / s : 1;
+}
+__host__ __device__ constexpr uint32_t slice_tmem_cols(int s) {
+    return (uint32_t)(s * BN <= 32 ? 32 : s * BN <= 64 ? 64 : s * BN <= 128 ? 128 : s * BN <= 256 ? 256 : 512);
+}
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kSmemLimit = 232448;  // opt-in dynamic shared memory per block on sm_103
 
 // Everything one split of A needs (one problem).
 struct SplitA {
@@ -52,7 +67,7 @@ struct SplitB {
 
 struct EmuParams {
     int64_t N, P, M;
-    int s, stages, chunk_blocks, tmem_cols;
+    int s;
     int tiles_m, tiles_n;
     const int32_t *ea, *fb;
     double *C;
@@ -148,8 +163,8 @@ struct TileJob {
 // phases run on across tiles, so the loads of the next tile start while the
 // last chunk of the current one is in the tensor pipe, and its MMAs start as
 // soon as the epilogue has read the accumulators out -- the final rounding and
-// the stores of C overlap them.  `c` holds the launch-wide constants (stages,
-// chunk, TMEM columns); the slice count kS is a template parameter.
+// the stores of C overlap them.  The slice count kS is a template parameter,
+// and with it the stage count, the exact chunk and the TMEM columns.
 template <bool kFP8, int kS, class Tiles>
 __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, const EmuParams &c,
                                             bool maps_in_global) {
@@ -162,9 +177,10 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
     constexpr int bke = fmt_bke(KIND), pair_blocks = fmt_pair_blocks(KIND);
     static_assert(kS >= 1 && kS <= 8, "1 to 8 slices");
     constexpr int s = kS;
-    const int S = c.stages, CB = c.chunk_blocks;
-    const uint32_t a_bytes = (uint32_t)s * BM * KB_BYTES, b_bytes = (uint32_t)s * BN * KB_BYTES;
-    const uint32_t stage_bytes = a_bytes + b_bytes;
+    constexpr int S = slice_stages(s), CB = slice_chunk_blocks(KIND, s);
+    constexpr uint32_t a_bytes = (uint32_t)s * BM * KB_BYTES, b_bytes = (uint32_t)s * BN * KB_BYTES;
+    constexpr uint32_t stage_bytes = slice_stage_bytes(s), tmem_cols = slice_tmem_cols(s);
+    static_assert(a_bytes + b_bytes == stage_bytes, "stage layout");
     uint64_t *full = bars, *empty = bars + 8, *acc_full = bars + 16, *acc_empty = bars + 17, *mma_done = bars + 18;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -179,7 +195,7 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
         mmdev::fence_mbar_init();
     }
     if (warp == 1) {
-        mmdev::tmem_alloc(&tmem_slot, (uint32_t)c.tmem_cols);
+        mmdev::tmem_alloc(&tmem_slot, tmem_cols);
         mmdev::tmem_relinquish();
     }
     mmdev::tc_fence_before();
@@ -375,7 +391,7 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
     if (warp == 1) {
         __syncwarp();
         mmdev::tc_fence_after();
-        mmdev::tmem_dealloc(tmem, (uint32_t)c.tmem_cols);
+        mmdev::tmem_dealloc(tmem, tmem_cols);
     }
 }
 
