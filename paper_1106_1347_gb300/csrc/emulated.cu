@@ -516,10 +516,10 @@ int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
 }
 
 // Host operands: device copies of A, B and C and the split workspace are carved
-// from ws.  B is copied and split on the caller's stream while the row blocks
-// of A go up on a copy stream; each block's split and slice product follow its
-// copy, and its rows of C come back on a second copy stream as soon as they
-// are done, so transfers overlap the products of other blocks.  The caller's
+// from ws.  One copy stream carries B and then the row blocks of A; B is split
+// on the caller's stream as soon as it lands, each block's split and slice
+// product follow its copy, and its rows of C come back on a second copy stream
+// as soon as they are done, so transfers overlap the products of other blocks.  The caller's
 // stream waits for the last copy back, and the copy streams wait for the
 // caller's earlier work, so consecutive calls on one stream stay ordered.
 size_t emulated_host_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind) {
