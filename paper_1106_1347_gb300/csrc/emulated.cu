@@ -377,10 +377,7 @@ int encode_slices(CUtensorMap *map, void *base, int64_t rows, int64_t Pp, int s,
 
 // Per-launch constants shared by every problem of one slice format and count
 // (the rest -- stages, exact chunk, TMEM columns -- follow from s at compile time).
-void fill_common(EmuParams &prm, int s, int kind) {
-    (void)kind;
-    prm.s = s;
-}
+void fill_common(EmuParams &prm, int s) { prm.s = s; }
 
 size_t slice_smem_bytes(int s) { return (size_t)slice_stages(s) * slice_stage_bytes(s) + 1024; }
 
@@ -476,7 +473,7 @@ int slice_product(const EmuWork &w, int64_t r0, int64_t n, int64_t P, int64_t M,
     if (!rc) rc = encode_slices(&tmB, w.sb, w.L.Mr, w.L.Pp, s, BN, kind);
     if (rc) return rc;
     EmuParams prm{};
-    fill_common(prm, s, kind);
+    fill_common(prm, s);
     prm.N = n;
     prm.P = P;
     prm.M = M;
@@ -785,7 +782,7 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
         unsigned char *sb = (unsigned char *)w;
         e.spa = SplitA{q.N, q.P, q.lda, L.Nr, L.Pp, q.A, s, ea, sa};
         e.spb = SplitB{q.P, q.M, q.ldb, L.Mr, L.Pp, q.B, s, cm, fb, sb};
-        fill_common(e.prm, s, kind);
+        fill_common(e.prm, s);
         e.prm.N = q.N;
         e.prm.P = q.P;
         e.prm.M = q.M;
