@@ -39,7 +39,7 @@ typedef enum {
     MM_ERR_ARG = -1,         /* bad argument; nothing was enqueued */
     MM_ERR_CUDA = -2,        /* a CUDA call or launch failed */
     MM_ERR_NOMEM = -3,       /* a fixed capacity was exceeded */
-    MM_ERR_UNSUPPORTED = -4, /* valid request this build does not implement */
+    MM_ERR_UNSUPPORTED = -4, /* valid request the library does not implement */
     MM_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
     MM_ERR_WORKSPACE = -6    /* ws_bytes smaller than the *_workspace_bytes query */
 } mm_status;
@@ -175,8 +175,8 @@ int mm_strassen_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64
                          void *stream);
 
 /*
- * Autotuner for the Strassen depth used by cutoff == -1 (north-star
- * autotuning; the paper fixes the depth by its padding rule).
+ * Autotuner for the Strassen depth used by cutoff == -1 (not in the paper,
+ * which fixes the depth by its padding rule).
  * mm_tune_strassen times the recursion at depths 0..3 (each dimension padded
  * to a multiple of 2^depth) on the given operands, writing C each time, and
  * records the fastest depth for (variant, floor(log2 max(N, P, M))); it
@@ -267,7 +267,7 @@ int mm_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_
 size_t mm_emulated_noalloc_capacity(void);
 
 /*
- * Grouped FP64-accurate products (spec batching; no counterpart in the
+ * Grouped FP64-accurate products (batching; no counterpart in the
  * paper): `count` independent products C_g = A_g B_g of uneven shapes, each
  * with the mm_emulated definition and one common slice count, in one launch
  * of each of the four kernels (split of A, column maxima and split of B, slice
@@ -320,7 +320,7 @@ int mm_strassen_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64
                          double tier, void *ws, size_t ws_bytes, void *stream);
 
 /*
- * Serving loop (spec serving; no counterpart in the paper).  A server
+ * Serving loop (no counterpart in the paper).  A server
  * owns a worker thread and K streams and serves requests C = A B with host
  * operands and a requested accuracy tier:
  *   - `arena` (device, caller-owned, arena_bytes) is the server's entire HBM

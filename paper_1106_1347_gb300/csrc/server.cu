@@ -1,6 +1,6 @@
 // Serving runtime: a request loop for products of uneven shapes with a
 // requested accuracy tier, continuous batching, admission by an HBM budget,
-// and latency statistics.  No counterpart in the paper (spec serving).
+// and latency statistics.  No counterpart in the paper.
 //
 // The caller hands the server one device arena (its HBM budget) at creation;
 // the server never allocates device memory.  A worker thread:
