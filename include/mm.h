@@ -304,14 +304,16 @@ int mm_emulated_group(const mm_problem *probs, int32_t count, int32_t kind, int3
  *   - the 7^levels products at the bottom computed as mm_emulated does (slice
  *     format `kind`, slice count from nslices / tier as for mm_emulated), all
  *     in one grouped launch.
- * levels = 0 is mm_emulated itself.  The result is bit-identical to the CPU
+ * levels = 0 is mm_emulated itself; levels = -1 picks the count by the
+ * smallest of N, P, M (0 below 5120, 1 below 12288, else 2: the measured
+ * crossovers on GB300 with 8 BF16 slices).  The result is bit-identical to the CPU
  * oracle's restatement of this definition.  Normwise error: the base
  * product's plus a few units of 2^-53 ||A|| ||B|| per level from the FP64
  * sums.  Workspace (device, caller-owned): the padded copies when padding is
  * needed, every level's operand sums and H blocks, and the grouped product's
  * workspace, as mm_strassen_emulated_workspace_bytes reports (0 for invalid
  * arguments).  Argument rules and errors as mm_emulated; MM_ERR_ARG for a
- * variant other than 0 or 1 or levels outside 0..4.
+ * variant other than 0 or 1 or levels outside -1..4.
  */
 size_t mm_strassen_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t variant, int32_t levels,
                                             int32_t kind, int32_t nslices, double tier);

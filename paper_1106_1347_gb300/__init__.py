@@ -188,7 +188,8 @@ def emulated(a, b, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
 
 def strassen_emulated(a, b, variant=0, levels=1, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
     """Strassen (variant 0) or Strassen-Winograd (1) levels over the emulated
-    product: mm_strassen_emulated (see include/mm.h)."""
+    product: mm_strassen_emulated (see include/mm.h); levels=-1 picks the
+    count from the size."""
     a, b, c, n, p, m = _prep(a, b, out)
     need = lib().mm_strassen_emulated_workspace_bytes(n, p, m, int(variant), int(levels), kind, nslices, tier)
     ws = _ws(need, a.device)

@@ -428,9 +428,9 @@ int mm_emulated_group(const mm_problem *probs, int32_t count, int32_t kind, int3
 size_t mm_strassen_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t variant, int32_t levels,
                                             int32_t kind, int32_t nslices, double tier) {
     const int s = emulated_slices(kind, nslices, tier);
-    if (s <= 0 || N < 0 || P < 0 || M < 0 || variant < 0 || variant > 1 || levels < 0 || levels > 4) return 0;
+    if (s <= 0 || N < 0 || P < 0 || M < 0 || variant < 0 || variant > 1 || levels < -1 || levels > 4) return 0;
     if (N == 0 || M == 0 || P == 0) return 0;
-    return strassen_emulated_ws_bytes(variant, levels, N, P, M, s, kind);
+    return strassen_emulated_ws_bytes(variant, strassen_emulated_levels(levels, N, P, M), N, P, M, s, kind);
 }
 
 int mm_strassen_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
@@ -440,12 +440,13 @@ int mm_strassen_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64
     int rc = check_gemm_args(fn, N, P, M, A, lda, B, ldb, C, ldc);
     if (rc) return rc;
     if (variant < 0 || variant > 1) return fail(MM_ERR_ARG, "%s: variant must be 0 or 1", fn);
-    if (levels < 0 || levels > 4) return fail(MM_ERR_ARG, "%s: levels must be 0..4", fn);
+    if (levels < -1 || levels > 4) return fail(MM_ERR_ARG, "%s: levels must be -1 (automatic) or 0..4", fn);
     const int s = slices_or_fail(fn, kind, nslices, tier);
     if (s < 0) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if (N == 0 || M == 0) return MM_OK;
     if (P == 0) return run_zero(N, M, C, ldc, st);
+    levels = strassen_emulated_levels(levels, N, P, M);
     const size_t need = strassen_emulated_ws_bytes(variant, levels, N, P, M, s, kind);
     if (ws_bytes < need || !ws)
         return fail(MM_ERR_WORKSPACE, "%s: workspace %zu bytes < %zu required", fn, ws_bytes, need);

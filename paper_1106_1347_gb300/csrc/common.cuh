@@ -115,6 +115,7 @@ int64_t group_grid_cap(int kernel);  // fixed grid of grouped kernel `kernel` (0
 void prof_suspend(bool on);  // skip kernel timing while a stream is being captured
 int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void *ws, cudaStream_t st);
 // Strassen (variant 0) / Strassen-Winograd (1) levels over the emulated product.
+int strassen_emulated_levels(int levels, int64_t N, int64_t P, int64_t M);  // resolves levels == -1
 size_t strassen_emulated_ws_bytes(int variant, int levels, int64_t N, int64_t P, int64_t M, int s, int kind);
 int run_strassen_emulated(int variant, int levels, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda,
                           const double *B, int64_t ldb, double *C, int64_t ldc, int s, int kind, void *ws,

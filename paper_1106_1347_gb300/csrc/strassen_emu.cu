@@ -18,6 +18,7 @@
 // kernel per internal node reads its seven H blocks once and writes its four
 // C quadrants.  Operands that are plain quadrants are passed as views (the
 // parent's leading dimension), never copied.
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -258,6 +259,15 @@ int strassen_emulated_walk(bool dry, int variant, int levels, int64_t N, int64_t
 }  // namespace
 
 namespace mm {
+
+// levels == -1: the level count that measured fastest on GB300 for 8 BF16
+// slices, by the smallest dimension: none below 5120 (at 4096 one level ties),
+// one up to 12288, two from there (5% faster than one at 16384).
+int strassen_emulated_levels(int levels, int64_t N, int64_t P, int64_t M) {
+    if (levels != -1) return levels;
+    const int64_t n = std::min(N, std::min(P, M));
+    return n < 5120 ? 0 : n < 12288 ? 1 : 2;
+}
 
 size_t strassen_emulated_ws_bytes(int variant, int levels, int64_t N, int64_t P, int64_t M, int s, int kind) {
     Arena ar{nullptr};

@@ -83,6 +83,11 @@ def test_host_side_queries_and_checks(native):
         lib.mm_emulated_workspace_bytes(256, 256, 256, 0, 8, 1e-14) * 7
     assert lib.mm_strassen_emulated_workspace_bytes(512, 512, 512, 2, 1, 0, 8, 1e-14) == 0
     assert lib.mm_strassen_emulated_workspace_bytes(512, 512, 512, 0, 5, 0, 8, 1e-14) == 0
+    assert lib.mm_strassen_emulated_workspace_bytes(512, 512, 512, 0, -2, 0, 8, 1e-14) == 0
+    # levels = -1: none below 5120, one up to 12288, two from there
+    for n, lv in ((4096, 0), (8192, 1), (16384, 2)):
+        assert lib.mm_strassen_emulated_workspace_bytes(n, n, n, 1, -1, 0, 8, 1e-14) == \
+            lib.mm_strassen_emulated_workspace_bytes(n, n, n, 1, lv, 0, 8, 1e-14)
     assert lib.mm_strassen_emulated(8, 8, 8, fake, 8, ctypes.c_void_p(0x30000), 8, ctypes.c_void_p(0x50000), 8, 2, 1, 0,
                                     8, 1e-14, None, 0, None) == -1
     assert lib.mm_strassen_emulated(8, 8, 8, fake, 8, ctypes.c_void_p(0x30000), 8, ctypes.c_void_p(0x50000), 8, 0, 5, 0,

@@ -61,6 +61,13 @@ def test_three_and_four_levels_bit_exact(mm, orc, variant):
         assert np.array_equal(got, orc.strassen_emulated(a, b, variant, levels, 7, 4))
 
 
+def test_automatic_levels_below_the_crossover_is_the_emulated_product(mm):
+    a, b = pair(120, 90, 100, tag=41)
+    ta, tb = dev(a), dev(b)
+    got = mm.strassen_emulated(ta, tb, variant=1, levels=-1, nslices=8)
+    assert bool((got == mm.emulated(ta, tb, nslices=8)).all())
+
+
 def test_zero_levels_is_the_emulated_product(mm):
     a, b = pair(150, 97, 130, tag=40)
     ta, tb = dev(a), dev(b)
