@@ -422,7 +422,8 @@ def test_emulated_group_rejects_overlapping_outputs(mm):
 # ------------------------------------------------------------ edge cases
 
 @pytest.mark.parametrize("name", ["naive", "naive_unrolled", "kahan", "winograd", "winograd_scaled",
-                                  "winograd_rowcol_scaled", "strassen", "strassen_winograd", "emulated"])
+                                  "winograd_rowcol_scaled", "strassen", "strassen_winograd", "emulated",
+                                  "strassen_emulated"])
 def test_degenerate_shapes(mm, name):
     import torch
 
