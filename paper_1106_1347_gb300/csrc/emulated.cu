@@ -94,48 +94,84 @@ __device__ __forceinline__ int64_t round_scaled(double x, int sh) {
     return neg ? -(int64_t)q : (int64_t)q;
 }
 
+// One slice's eight digits as one vector store: 16 bytes of BF16 or 8 bytes of
+// E4M3 at dst (16-byte aligned for BF16, 8 for E4M3).
+template <int KIND>
+__device__ __forceinline__ void store_slice8(const int (&d)[8], unsigned char *dst) {
+    if (KIND == MM_SLICE_FP8E4M3) {
+        uint32_t w[2] = {0u, 0u};
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            w[u >> 2] |= (uint32_t)__nv_cvt_float_to_fp8((float)d[u], __NV_SATFINITE, __NV_E4M3) << (8 * (u & 3));
+        *reinterpret_cast<uint2 *>(dst) = make_uint2(w[0], w[1]);
+    } else {
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn((float)d[2 * u], (float)d[2 * u + 1]);
+            w[u] = *reinterpret_cast<const uint32_t *>(&h2);
+        }
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// The balanced low digit of x, d = ((x + 2^(beta-1)) mod 2^beta) - 2^(beta-1)
+// (in [-2^(beta-1), 2^(beta-1))), and x <- (x - d) / 2^beta, exactly.
+template <int beta, class I>
+__device__ __forceinline__ int peel_digit(I &x) {
+    constexpr int base = 1 << beta, half = base >> 1;
+    const int d = (int)((x + half) & (base - 1)) - half;
+    x = (x - d) >> beta;
+    return d;
+}
+
 // Eight consecutive elements of one slice row at a time.  V[u] holds
 // RN(x_u 2^sh) on entry; its balanced base-2^beta digits are peeled off from
 // the least significant one (low digits in [-2^(beta-1), 2^(beta-1)), the
 // rest is the top digit), and digit t of all eight goes to slice s-1-t as one
-// vector store: 16 bytes of BF16 or 8 bytes of E4M3 at dst0 + (s-1-t) * stride
-// (dst0: slice 0 at this row and column, 16-byte aligned for BF16, 8 for E4M3).
-// Every index is a compile-time constant, so nothing leaves registers.
+// vector store at dst0 + (s-1-t) * stride (dst0: slice 0 at this row and
+// column).  With more than LO = floor(28 / beta) slices, V = hi 2^(LO beta) +
+// lo is split first: the LO low digits come from lo and the rest from hi +
+// the carry lo leaves, all in 32-bit arithmetic (|V| < 2^55, so |hi| < 2^27);
+// the digits are the same as those of V itself.  Every index is a
+// compile-time constant, so nothing leaves registers.
 template <int KIND>
 __device__ __forceinline__ void store_digits8(int64_t (&V)[8], int s, unsigned char *dst0, int64_t stride) {
-    constexpr int beta = fmt_beta(KIND), base = 1 << beta, half = base >> 1;
+    constexpr int beta = fmt_beta(KIND), LO = 28 / beta, LOBITS = LO * beta;
+    if (s > LO) {
+        int32_t lo[8], hi[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            lo[u] = (int32_t)(V[u] & ((1ll << LOBITS) - 1));
+            hi[u] = (int32_t)(V[u] >> LOBITS);
+        }
+#pragma unroll
+        for (int t = 0; t < LO; ++t) {
+            int d[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) d[u] = peel_digit<beta>(lo[u]);
+            store_slice8<KIND>(d, dst0 + (int64_t)(s - 1 - t) * stride);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) hi[u] += lo[u];  // the carry, 0 or 1
+#pragma unroll
+        for (int t = LO; t < 8; ++t) {
+            if (t < s) {
+                int d[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) d[u] = t < s - 1 ? peel_digit<beta>(hi[u]) : hi[u];
+                store_slice8<KIND>(d, dst0 + (int64_t)(s - 1 - t) * stride);
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         if (t < s) {
             int d[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (t < s - 1) {
-                    int x = (int)(V[u] & (base - 1));
-                    if (x >= half) x -= base;
-                    d[u] = x;
-                    V[u] = (V[u] - x) >> beta;
-                } else {
-                    d[u] = (int)V[u];
-                }
-            }
-            unsigned char *dst = dst0 + (int64_t)(s - 1 - t) * stride;
-            if (KIND == MM_SLICE_FP8E4M3) {
-                uint32_t w[2] = {0u, 0u};
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    w[u >> 2] |= (uint32_t)__nv_cvt_float_to_fp8((float)d[u], __NV_SATFINITE, __NV_E4M3)
-                                 << (8 * (u & 3));
-                *reinterpret_cast<uint2 *>(dst) = make_uint2(w[0], w[1]);
-            } else {
-                uint32_t w[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const __nv_bfloat162 h2 = __floats2bfloat162_rn((float)d[2 * u], (float)d[2 * u + 1]);
-                    w[u] = *reinterpret_cast<const uint32_t *>(&h2);
-                }
-                *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-            }
+            for (int u = 0; u < 8; ++u) d[u] = t < s - 1 ? peel_digit<beta>(V[u]) : (int)V[u];
+            store_slice8<KIND>(d, dst0 + (int64_t)(s - 1 - t) * stride);
         }
     }
 }
