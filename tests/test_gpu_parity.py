@@ -259,7 +259,7 @@ def test_emulated_bit_exact_vs_oracle(mm, orc, shape, s):
     assert np.array_equal(got, orc.split_product(a, b, 7, s))
 
 
-@pytest.mark.parametrize("s", [1, 2, 5, 6, 7])
+@pytest.mark.parametrize("s", [1, 2, 4, 5, 6, 7])
 def test_emulated_other_slice_counts(mm, orc, s):
     a, b = pair(130, 200, 70, "uni", 13)
     assert np.array_equal(host(mm.emulated(dev(a), dev(b), nslices=s)), orc.split_product(a, b, 7, s))
@@ -319,6 +319,14 @@ def test_emulated_extreme_digit_sums(mm, orc):
 def test_emulated_fp8_bit_exact_vs_oracle(mm, orc, shape, s):
     """FP8-E4M3 slices hold balanced base-2^5 digits: the same definition with beta = 5."""
     a, b = pair(*shape, "log", 40 + s)
+    got = host(mm.emulated(dev(a), dev(b), nslices=s, kind=mm.SLICE_FP8E4M3))
+    assert np.array_equal(got, orc.split_product(a, b, 5, s))
+
+
+@pytest.mark.parametrize("s", [2, 4, 5, 7])
+def test_emulated_fp8_other_slice_counts(mm, orc, s):
+    """Every E4M3 slice count (the split peels up to 5 digits from the low 25 bits, the rest from the high part)."""
+    a, b = pair(130, 200, 70, "log", 60 + s)
     got = host(mm.emulated(dev(a), dev(b), nslices=s, kind=mm.SLICE_FP8E4M3))
     assert np.array_equal(got, orc.split_product(a, b, 5, s))
 
