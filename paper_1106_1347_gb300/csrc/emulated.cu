@@ -193,21 +193,26 @@ __device__ __forceinline__ void load8(const double *__restrict__ a, int64_t c, i
 }
 
 constexpr int kRowThreads = 256;
+// Rows of at most this many (padded) elements are split by one warp each, 8
+// rows per CTA; longer ones by a whole CTA.
+constexpr int64_t kWarpRowMax = 1024;
 
-// One CTA per row of A: max |A_ik| by integer max on the bit patterns (block
-// reduction), then the digits, written as slices [s][Nr][Pp] (BF16 or
-// FP8-E4M3); columns [P, Pp) get zero digits so every K-block read is defined.
-// The digit pass reads the row again, from L2: with one row per CTA only a
-// few rows per SM are in flight (about 40 MB over the GPU at 8192 columns),
-// so A crosses HBM once.  `red` is 8 words of shared memory.
-template <int KIND>
-__device__ __forceinline__ void split_row(const SplitA &p, int64_t row, unsigned long long *red) {
+// One row of A by T threads (a whole CTA of 256, or one warp): max |A_ik| by
+// integer max on the bit patterns, then the digits, written as slices
+// [s][Nr][Pp] (BF16 or FP8-E4M3); columns [P, Pp) get zero digits so every
+// K-block read is defined.  The digit pass reads the row again, from L2: with
+// one row per CTA only a few rows per SM are in flight (about 40 MB over the
+// GPU at 8192 columns), so A crosses HBM once.  `tid` is the thread's index
+// among the T; with T = 256 `red` is 8 words of shared memory (unused for a
+// warp).
+template <int KIND, int T>
+__device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int tid, unsigned long long *red) {
     const double *__restrict__ a = p.A + row * p.lda;
     const int64_t P = p.P, Pp = p.Pp;
-    const int s = p.s, tid = threadIdx.x;
+    const int s = p.s;
     const bool vec = (((uintptr_t)a) & 15) == 0;
     unsigned long long mx = 0;
-    for (int64_t c = 8 * tid; c < P; c += 8 * kRowThreads) {
+    for (int64_t c = 8 * tid; c < P; c += 8 * T) {
         double x[8];
         load8(a, c, P, vec, x);
 #pragma unroll
@@ -216,11 +221,13 @@ __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, unsigned
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         mx = umax64(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mx, o));
-    if ((tid & 31) == 0) red[tid >> 5] = mx;
-    __syncthreads();
+    if (T > 32) {
+        if ((tid & 31) == 0) red[tid >> 5] = mx;
+        __syncthreads();
 #pragma unroll
-    for (int w = 0; w < kRowThreads / 32; ++w) mx = umax64(mx, red[w]);
-    __syncthreads();  // `red` is reused by the next row
+        for (int w = 0; w < T / 32; ++w) mx = umax64(mx, red[w]);
+        __syncthreads();  // `red` is reused by the next row
+    }
     const int e = frexp_exp_bits(mx);
     if (tid == 0) p.ea[row] = e;
     constexpr int beta = fmt_beta(KIND), es = fmt_esize(KIND);
@@ -229,7 +236,7 @@ __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, unsigned
     unsigned char *row0 = p.slices + row * Pp * es;
     // Pp is a multiple of 8 (BF16) or 16 (E4M3) elements: a group of eight
     // starting before Pp ends by Pp.
-    for (int64_t c = 8 * tid; c < Pp; c += 8 * kRowThreads) {
+    for (int64_t c = 8 * tid; c < Pp; c += 8 * T) {
         double x[8];
         load8(a, c, P, vec, x);
         int64_t V[8];
@@ -242,7 +249,14 @@ __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, unsigned
 template <int KIND>
 __global__ void __launch_bounds__(kRowThreads, 4) split_rows_kernel(const SplitA p) {
     __shared__ unsigned long long red[kRowThreads / 32];
-    split_row<KIND>(p, blockIdx.x, red);
+    split_row<KIND, kRowThreads>(p, blockIdx.x, threadIdx.x, red);
+}
+
+// Short rows (Pp <= kWarpRowMax): one warp per row, 8 rows per CTA.
+template <int KIND>
+__global__ void __launch_bounds__(kRowThreads, 4) split_rows_warp_kernel(const SplitA p) {
+    const int64_t row = (int64_t)blockIdx.x * (kRowThreads / 32) + (threadIdx.x >> 5);
+    if (row < p.N) split_row<KIND, 32>(p, row, threadIdx.x & 31, nullptr);
 }
 
 
@@ -328,9 +342,15 @@ __global__ void __launch_bounds__(kRowThreads, 4) group_split_rows_kernel(const 
                                                                           const GroupHeader *hdr) {
     __shared__ unsigned long long red[kRowThreads / 32];
     const int64_t units = hdr->units[U_ROWS];
-    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {  // one row per unit
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const int g = find_problem(begin, hdr->count, u);
-        split_row<KIND>(tab[g].spa, u - begin[g], red);
+        const SplitA &p = tab[g].spa;
+        if (p.Pp <= kWarpRowMax) {  // 8 rows per unit, one per warp (the whole CTA takes this branch)
+            const int64_t row = (u - begin[g]) * (kRowThreads / 32) + (threadIdx.x >> 5);
+            if (row < p.N) split_row<KIND, 32>(p, row, threadIdx.x & 31, nullptr);
+        } else {  // one row per unit
+            split_row<KIND, kRowThreads>(p, u - begin[g], threadIdx.x, red);
+        }
     }
 }
 
@@ -491,10 +511,18 @@ int split_a_rows(const EmuWork &w, int64_t r0, int64_t n, int64_t P, const doubl
     const SplitA spa{n, P, lda, w.L.Nr, w.L.Pp, A, s, w.ea + r0,
                      w.sa + (size_t)r0 * w.L.Pp * fmt_esize(kind)};
     return mm::launch("emu_split_rows", st, [&] {
-        if (kind == MM_SLICE_FP8E4M3)
+        const bool fp8 = kind == MM_SLICE_FP8E4M3;
+        if (w.L.Pp <= kWarpRowMax) {
+            const unsigned g = (unsigned)mm::ceil_div(n, kRowThreads / 32);
+            if (fp8)
+                split_rows_warp_kernel<MM_SLICE_FP8E4M3><<<g, kRowThreads, 0, st>>>(spa);
+            else
+                split_rows_warp_kernel<MM_SLICE_BF16><<<g, kRowThreads, 0, st>>>(spa);
+        } else if (fp8) {
             split_rows_kernel<MM_SLICE_FP8E4M3><<<(unsigned)n, kRowThreads, 0, st>>>(spa);
-        else
+        } else {
             split_rows_kernel<MM_SLICE_BF16><<<(unsigned)n, kRowThreads, 0, st>>>(spa);
+        }
     });
 }
 
@@ -833,7 +861,7 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
         if (!rc) rc = encode_slices(&e.tmB, sb, L.Mr, L.Pp, s, BN, kind);
         if (rc) return rc;
         for (int k = 0; k < 5; ++k) begin[k][i] = units[k];
-        units[U_ROWS] += q.N;
+        units[U_ROWS] += L.Pp <= kWarpRowMax ? ceil_div(q.N, kRowThreads / 32) : q.N;
         units[U_COLMAX] += ceil_div(q.M, 128) * ceil_div(q.P, 256);
         units[U_SPLITCOLS] += ceil_div(q.M, SC_J) * ceil_div(L.Pp, SC_K);
         units[U_TILES] += (int64_t)e.prm.tiles_m * e.prm.tiles_n;
