@@ -692,12 +692,62 @@ def run_ours(args):
     gpu_launches = sum(v[0] for v in prof.stats.values())
     kernel_ms = {k: round(v[1] / max(v[0], 1), 4) for k, v in prof.stats.items()}
 
-    # Accuracy of this run (sampled rows) and the plain FP64 product on the same inputs.
     out = {}
-    if rank == 0 and not args.quick:
+    rows = np.arange(0, N, N // 4)[:4]
+    if not args.quick:
+        # End to end through the C ABI with host buffers (mm_emulated_host), on
+        # every rank with its own pinned A, B, C: the copies of A and B up and of
+        # C back run inside the call, overlapped with the products of other row
+        # blocks.  Per-step events; each rank's value is its median step (the
+        # paper's statistic: the host link sees sporadic stalls of several ms that
+        # a mean of ten steps would carry), and the whole job's is the slowest
+        # rank's.
+        ha = torch.from_numpy(a).pin_memory()
+        hb = torch.from_numpy(b).pin_memory()
+        hc = torch.empty((N, M), dtype=torch.float64).pin_memory()
+        hws_bytes = lib.mm_emulated_host_workspace_bytes(N, P, M, 0, SLICES, 1e-14)
+        hws = torch.empty(hws_bytes, dtype=torch.uint8, device=dev)
+
+        def e2e_step():
+            rc = lib.mm_emulated_host(N, P, M, ctypes.c_void_p(ha.data_ptr()), P, ctypes.c_void_p(hb.data_ptr()), M,
+                                      ctypes.c_void_p(hc.data_ptr()), M, 0, SLICES, 1e-14,
+                                      ctypes.c_void_p(hws.data_ptr()), hws_bytes, ctypes.c_void_p(stream.cuda_stream))
+            if rc != 0:
+                raise RuntimeError(lib.mm_last_error().decode())
+
+        e2e_steps = max(10, min(20, args.steps))
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        gm = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps + 1)]
+        with ClockSampler(local) as clk_e2e:
+            gm[0].record(stream)
+            for i in range(e2e_steps):
+                e2e_step()
+                gm[i + 1].record(stream)
+            torch.cuda.synchronize()
+        e2e_each = [gm[i].elapsed_time(gm[i + 1]) for i in range(e2e_steps)]
+        e2e_ms = max_over_ranks(statistics.median(e2e_each), dev)
+        if not np.array_equal(hc[rows].numpy(), c[rows].cpu().numpy()):
+            raise RuntimeError("host-operand product differs from the device call")
+        out["e2e"] = {"value": whole_job_tflops(flop, 1, world, e2e_ms), "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                      "steps": e2e_steps,
+                      "statistic": "median of per-step CUDA-event times" + (", slowest rank" if world > 1 else ""),
+                      "ms_mean": statistics.mean(e2e_each), "ms_min": min(e2e_each), "ms_max": max(e2e_each),
+                      "ms_each": [round(x, 3) for x in e2e_each], "clocks": clk_e2e.summary(),
+                      "h2d_bytes_per_step": int(world * (a.nbytes + b.nbytes)),
+                      "d2h_bytes_per_step": int(world * N * M * 8),
+                      "call": "mm_emulated_host (pinned host A, B, C; copies overlapped with row-block products)"}
+        del hws, ha, hb, hc
+        torch.cuda.empty_cache()
+
+    # Single-GPU sections (rank 0 of a one-rank run): accuracy, the plain FP64
+    # product, the other configurations, serving and the CPU baseline.
+    if rank == 0 and world == 1 and not args.quick:
         norm_a = float(mm.norm_inf(ta).item())
         norm_b = float(mm.norm_inf(tb).item())
-        rows = np.arange(0, N, N // 4)[:4]
         import oracle
 
         truth = oracle.dot2_product(a[rows], b)
@@ -719,48 +769,6 @@ def run_ours(args):
                            "target": 1e-14, "reference": "oracle Dot2 product on the sampled rows"}
         del cn
 
-        # End to end through the C ABI with host buffers (mm_emulated_host): the
-        # copies of A and B up and of C back run inside the call, overlapped with
-        # the products of other row blocks; pinned host memory.
-        ha = torch.from_numpy(a).pin_memory()
-        hb = torch.from_numpy(b).pin_memory()
-        hc = torch.empty((N, M), dtype=torch.float64).pin_memory()
-        hws_bytes = lib.mm_emulated_host_workspace_bytes(N, P, M, 0, SLICES, 1e-14)
-        hws = torch.empty(hws_bytes, dtype=torch.uint8, device=dev)
-
-        def e2e_step():
-            rc = lib.mm_emulated_host(N, P, M, ctypes.c_void_p(ha.data_ptr()), P, ctypes.c_void_p(hb.data_ptr()), M,
-                                      ctypes.c_void_p(hc.data_ptr()), M, 0, SLICES, 1e-14,
-                                      ctypes.c_void_p(hws.data_ptr()), hws_bytes, ctypes.c_void_p(stream.cuda_stream))
-            if rc != 0:
-                raise RuntimeError(lib.mm_last_error().decode())
-
-        # Per-step events; the value is the median step (the paper's statistic:
-        # the host link sees sporadic stalls of several ms that a mean of ten
-        # steps would carry), with the mean, min and max beside it.
-        e2e_steps = max(10, min(20, args.steps))
-        for _ in range(3):
-            e2e_step()
-        torch.cuda.synchronize()
-        gm = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps + 1)]
-        with ClockSampler(local) as clk_e2e:
-            gm[0].record(stream)
-            for i in range(e2e_steps):
-                e2e_step()
-                gm[i + 1].record(stream)
-            torch.cuda.synchronize()
-        e2e_each = [gm[i].elapsed_time(gm[i + 1]) for i in range(e2e_steps)]
-        e2e_ms = statistics.median(e2e_each)
-        if not np.array_equal(hc[rows].numpy(), c[rows].cpu().numpy()):
-            raise RuntimeError("host-operand product differs from the device call")
-        out["e2e"] = {"value": flop / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
-                      "steps": e2e_steps, "statistic": "median of per-step CUDA-event times",
-                      "ms_mean": statistics.mean(e2e_each), "ms_min": min(e2e_each), "ms_max": max(e2e_each),
-                      "ms_each": [round(x, 3) for x in e2e_each], "clocks": clk_e2e.summary(),
-                      "h2d_bytes_per_step": int(a.nbytes + b.nbytes), "d2h_bytes_per_step": int(N * M * 8),
-                      "call": "mm_emulated_host (pinned host A, B, C; copies overlapped with row-block products)"}
-        del hws
-
         if args.variants_n > 0:
             out["fp64_methods"] = variants_bench(dev)
             out["paper_table"] = paper_table(dev)
@@ -772,7 +780,6 @@ def run_ours(args):
             out["strassen_over_emulated"] = strassen_over_emulated(ta, tb, a, b, norm_a, norm_b, rows, truth)
             torch.cuda.empty_cache()
         if not args.no_serve:
-            del ha, hb, hc
             out["serving"] = serve_in_own_process(local, args)
 
         cores = host_cores()
