@@ -333,11 +333,12 @@ int mm_strassen_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64
  *     not fit yet) once their A, B and C fit; a request that can never fit
  *     completes with MM_ERR_NOMEM;
  *   - continuous batching: whenever a stream is free, all admitted requests of
- *     the oldest request's slice format and count (up to max_batch; the
- *     environment variable MM_SERVER_BATCH_MS, read at creation, also caps a
- *     batch's estimated milliseconds of work, and MM_SERVER_CLASS_RATIO keeps
- *     to requests within that factor of the oldest one's estimated time) run
- *     as one grouped emulated
+ *     the oldest request's slice format and count (up to max_batch and, past
+ *     the first request, up to 4 ms of estimated work -- copies at 200 GB/s,
+ *     slice pairs at 1.2 (BF16) or 2.4 (FP8) PFLOP/s; the environment variable
+ *     MM_SERVER_BATCH_MS, read at creation, sets that cap, 0 lifts it, and
+ *     MM_SERVER_CLASS_RATIO keeps to requests within that factor of the
+ *     oldest one's estimated time) run as one grouped emulated
  *     launch, replayed from a CUDA graph cached per stream, slice format and
  *     count when use_graphs != 0;
  *   - method 0: BF16 slices, the tier's count (mm_emulated_slices);

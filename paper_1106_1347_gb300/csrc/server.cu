@@ -9,8 +9,8 @@
 //     in the arena (first fit) -- so an admitted request can always run;
 //   * whenever one of its K stream slots is free, forms a batch from every
 //     admitted request of the oldest request's slice format and count (up to
-//     max_batch, and, with MM_SERVER_BATCH_MS set, up to that many estimated
-//     milliseconds of work) and enqueues on that slot's stream: host-to-device
+//     max_batch and past the first request up to 4 ms of estimated work, a cap
+//     MM_SERVER_BATCH_MS changes) and enqueues on that slot's stream: host-to-device
 //     copies of A and B, the table upload, one grouped emulated launch
 //     (replayed from a CUDA graph cached per slot, slice format and count, when
 //     enabled -- the grouped kernels run fixed grids), device-to-host copies
@@ -166,7 +166,7 @@ struct mm_server {
     int device = 0;
     ArenaAlloc arena;
     int max_batch = 64, method = 0;
-    double batch_ms_cap = 0.0;  // estimated device time per batch (0: no cap; MM_SERVER_BATCH_MS)
+    double batch_ms_cap = 4.0;  // estimated device time per batch (MM_SERVER_BATCH_MS; 0: no cap)
     double class_ratio = 0.0;   // batch only requests within this factor of the oldest one's time (0: off)
     bool use_graphs = true;
     std::vector<Slot> slots;
