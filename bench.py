@@ -769,6 +769,9 @@ def run_ours(args):
                            "target": 1e-14, "reference": "oracle Dot2 product on the sampled rows"}
         del cn
 
+        # Serving first, in its own process, before the long sections below.
+        if not args.no_serve:
+            out["serving"] = serve_in_own_process(local, args)
         if args.variants_n > 0:
             out["fp64_methods"] = variants_bench(dev)
             out["paper_table"] = paper_table(dev)
@@ -779,8 +782,6 @@ def run_ours(args):
             out["grouped_vs_single"] = grouped_vs_single(dev)
             out["strassen_over_emulated"] = strassen_over_emulated(ta, tb, a, b, norm_a, norm_b, rows, truth)
             torch.cuda.empty_cache()
-        if not args.no_serve:
-            out["serving"] = serve_in_own_process(local, args)
 
         cores = host_cores()
         v, rows_used, thr, el = cpu_oracle_tflops(a, b, args.cpu_seconds, cores)
