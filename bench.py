@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--variants-n", type=int, default=1, help="0: skip the per-method FP64 sweep and the paper's table")
     ap.add_argument("--fp64-only", action="store_true",
                     help="only the per-method FP64 timings at n = --n, one run each (profiling runs)")
+    ap.add_argument("--detail", default=os.path.join(ROOT, "bench_detail.json"),
+                    help="file that receives every section of the run (the printed line carries summaries)")
+    ap.add_argument("--no-cpu-table", action="store_true", help="skip the CPU oracle's run of the paper's test")
+    ap.add_argument("--cpu-table-repeats", type=int, default=10)
     args = ap.parse_args()
     global N, P, M, WORKLOAD, SLICES, KIND, DOMINANT
     if args.fp8:
@@ -426,8 +430,11 @@ def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000
     [32, 4096], entries uniform [-1, 1], tiers 1e-14 / 1e-6 half and half.
     1) saturated: every request submitted at t = 0 -> throughput;
     2) Poisson arrivals at 0.7x that rate -> p50 / p99 latency;
-    3) the same arrivals (first `baseline_requests`) served one at a time by
-       the plain FP64 kernel."""
+    3) like for like at one accuracy (every request at the 1e-14 tier): the
+       plain FP64 kernel one request at a time and the emulated server, each
+       paced at 0.7x its own saturated rate over the whole trace (the FP64
+       arm's rate from its first `baseline_requests`), and the emulated server
+       at the FP64 arm's arrival rate."""
     import torch
 
     import synthetic as S
@@ -464,9 +471,40 @@ def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000
     with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True,
                         method=serving.METHOD_EMULATED_AUTO) as srv:
         st_a, _, rc_a = serving.replay(srv, paced_a, a_pool, b_pool, c_pool)
-    base_trace = paced[:baseline_requests]
+    # Like for like at one accuracy: every request at the 1e-14 tier, each arm paced at 0.7x the rate
+    # it sustains itself (the FP64 arm's rate measured on a prefix of the trace), plus the emulated
+    # arm at the FP64 arm's arrival rate.
+    strict = lambda gap: S.serving_trace(requests, S.stream_seed(4, 5), mean_gap_s=gap, tiers=(1e-14, 1e-14))
     with serving.Server(budget, method=serving.METHOD_FP64) as srv:
-        st_b, _, rc_b = serving.replay(srv, base_trace, a_pool, b_pool, c_pool)
+        st_fs, _, rc_fs = serving.replay(srv, strict(0.0)[:baseline_requests], a_pool, b_pool, c_pool)
+    rate_f = st_fs["completed"] / max(st_fs["busy_s"], 1e-9)
+    with serving.Server(budget, method=serving.METHOD_FP64) as srv:
+        st_fp, _, rc_fp = serving.replay(srv, strict(1.0 / (0.7 * rate_f)), a_pool, b_pool, c_pool)
+    with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True) as srv:
+        st_es, _, rc_es = serving.replay(srv, strict(0.0), a_pool, b_pool, c_pool)
+    rate_e = st_es["completed"] / max(st_es["busy_s"], 1e-9)
+    with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True) as srv:
+        st_ep, _, rc_ep = serving.replay(srv, strict(1.0 / (0.7 * rate_e)), a_pool, b_pool, c_pool)
+    with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True) as srv:
+        st_ef, _, rc_ef = serving.replay(srv, strict(1.0 / (0.7 * rate_f)), a_pool, b_pool, c_pool)
+
+    def arm(st_sat_x, st_paced_x, rate_x, rc_x):
+        return {"saturated_requests_per_s": rate_x,
+                "saturated_tflops": st_sat_x["flops"] / max(st_sat_x["busy_s"], 1e-9) / 1e12,
+                "paced": {"arrival_rate_rps": 0.7 * rate_x, "requests": st_paced_x["completed"],
+                          "p50_ms": st_paced_x["p50_ms"], "p99_ms": st_paced_x["p99_ms"],
+                          "mean_ms": st_paced_x["mean_ms"], "max_ms": st_paced_x["max_ms"],
+                          "requests_per_s": st_paced_x["completed"] / max(st_paced_x["busy_s"], 1e-9),
+                          "status": rc_x}}
+
+    like_for_like = {
+        "tier": 1e-14, "requests": requests,
+        "fp64_one_at_a_time": dict(arm(st_fs, st_fp, rate_f, rc_fp), saturated_on=f"first {baseline_requests}"),
+        "emulated": arm(st_es, st_ep, rate_e, rc_ep),
+        "emulated_at_fp64_rate": {"arrival_rate_rps": 0.7 * rate_f, "p50_ms": st_ef["p50_ms"],
+                                  "p99_ms": st_ef["p99_ms"], "mean_ms": st_ef["mean_ms"],
+                                  "max_ms": st_ef["max_ms"], "completed": st_ef["completed"], "status": rc_ef},
+    }
     flop_all = st["flops"]
     # Latency against load: shorter Poisson streams at other fractions of the saturated rate.
     sweep = {}
@@ -501,9 +539,7 @@ def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000
                   "tflops": flop_all / max(st["busy_s"], 1e-9) / 1e12, "batches": st["batches"],
                   "graph_replays": st["graph_replays"], "peak_arena_gb": st["peak_arena_bytes"] / 2 ** 30,
                   "status": rc},
-        "fp64_one_at_a_time": {"requests": len(base_trace), "arrival_rate_rps": 0.7 * rate,
-                               "p50_ms": st_b["p50_ms"], "p99_ms": st_b["p99_ms"], "mean_ms": st_b["mean_ms"],
-                               "tflops": st_b["flops"] / max(st_b["busy_s"], 1e-9) / 1e12, "status": rc_b},
+        "like_for_like_1e-14": like_for_like,
         "auto_format": {"formats": "1e-14: 8 BF16 slices; 1e-6: 6 FP8-E4M3 slices",
                         "saturated": {"requests_per_s": rate_a,
                                       "tflops": st_sat_a["flops"] / max(st_sat_a["busy_s"], 1e-9) / 1e12,
@@ -515,28 +551,40 @@ def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000
     }
 
 
-FP64_PEAK_TFLOPS = 1.056  # DFMA and mma.sync f64 on GB300, measured by the library's own probe
+def fp64_peak(local, target_ms=150.0):
+    """The FP64 pipe's rate measured on this GPU by the library's probe
+    (mm_probe_fp64_peak: independent DFMA chains, and independent mma.sync f64
+    accumulators), with the SM clock sampled while it runs."""
+    import paper_1106_1347_gb300 as mm
+
+    with ClockSampler(local) as clk:
+        dfma, dmma = mm.probe_fp64_peak(target_ms)
+    return {"dfma_tflops": dfma, "dmma_tflops": dmma, "clocks": clk.summary(),
+            "how": f"mm_probe_fp64_peak, each kernel timed over >= {target_ms:.0f} ms with CUDA events"}
 
 
 FP64_SWEEP = (256, 1024, 2047, 2048, 4095, 4096, 8192)
 
 
-def variants_bench(dev, sizes=FP64_SWEEP, reps=None):
+def variants_bench(dev, peak, sizes=FP64_SWEEP, reps=None):
     """Each FP64 method at n^3 for n in `sizes` (uniform [-1, 1] inputs; odd n
     exercise Winograd's odd-P term): TFLOP/s as 2n^3/t and, for the methods
-    with a fixed operation count, the fraction of the FP64 pipe kept busy."""
+    with a fixed operation count, the fraction of the FP64 pipe kept busy
+    against the probe's rate for the instruction the kernel issues (`peak`,
+    from fp64_peak)."""
     import torch
 
     import paper_1106_1347_gb300 as mm
     import synthetic as S
 
     # FP64-pipe operations (an FMA, DADD or DMUL each, or 1/256 of an m8n8k4 MMA)
-    # issued per reported flop (2n^3 per product): naive 1 FMA per 2 flop; the
-    # ordered naive sum 1 DMUL + 1 DADD per k (plus 1 DADD per group of 4 when
-    # unrolled); Kahan 1 DMUL + 4 DADD per k; Winograd 2 DADD + 1 FMA per pair of k.
-    pipe = {"naive": 0.5, "naive_ordered": 1.0, "naive_unrolled_4": 1.125, "kahan": 2.5, "winograd": 0.75,
+    # issued per reported flop (2n^3 per product): naive 1 MMA-FMA per 2 flop; the
+    # ordered naive sum 1 DMUL + 1 DADD per k; unrolled by 4, per group of four k
+    # 4 DMUL + 3 DADD inside the group + 1 DADD into aux (2 per k); Kahan 1 DMUL +
+    # 4 DADD per k; Winograd 2 DADD + 1 FMA per pair of k.
+    pipe = {"naive": 0.5, "naive_ordered": 1.0, "naive_unrolled_4": 1.0, "kahan": 2.5, "winograd": 0.75,
             "winograd_scaled": 0.75, "winograd_rowcol_scaled": 0.75}
-    peak_ops = FP64_PEAK_TFLOPS / 2.0  # FP64-pipe ops per second (1e12)
+    ops_rate = {"dmma": peak["dmma_tflops"] / 2.0, "dfma": peak["dfma_tflops"] / 2.0}  # 1e12 FP64-pipe ops/s
     by_size = {}
     for n in sizes:
         a = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 0))).to(dev)
@@ -552,20 +600,26 @@ def variants_bench(dev, sizes=FP64_SWEEP, reps=None):
             "winograd_rowcol_scaled": lambda: mm.winograd_rowcol_scaled(a, b, out=c),
             "strassen": lambda: mm.strassen(a, b, out=c),
             "strassen_winograd": lambda: mm.strassen_winograd(a, b, out=c),
+            "strassen_paper_rule": lambda: mm.strassen(a, b, cutoff=0, out=c),
+            "strassen_winograd_paper_rule": lambda: mm.strassen_winograd(a, b, cutoff=0, out=c),
             "emulated_8_slices": lambda: mm.emulated(a, b, nslices=8, out=c),
         }
         out = {}
         for name, fn in runs.items():
-            ms = timed(fn, reps or (1 if n >= 4095 else 3))
+            try:
+                ms = timed(fn, reps or (1 if n >= 4095 else 3))
+            except mm.MMError as exc:  # a depth the library refuses (reported, not hidden)
+                out[name] = {"status": exc.status}
+                continue
             tf = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
             entry = {"ms": ms, "tflops": tf}
             if name in pipe:  # fraction of the FP64 pipe kept busy
-                entry["fp64_pipe_frac"] = tf * pipe[name] / peak_ops
+                entry["fp64_pipe_frac"] = tf * pipe[name] / ops_rate["dmma" if name == "naive" else "dfma"]
             out[name] = entry
         by_size[str(n)] = out
         del a, b, c
-    return {"inputs": "uniform [-1, 1]", "fp64_peak_tflops": FP64_PEAK_TFLOPS,
-            "fp64_peak_source": "own probe: DFMA and mma.sync m8n8k4 f64 both ~1.06 TFLOP/s", "by_size": by_size}
+    return {"inputs": "uniform [-1, 1]", "fp64_peak": peak,
+            "pipe_frac_against": "naive: the mma.sync f64 probe; the others: the DFMA probe", "by_size": by_size}
 
 
 def paper_table(dev, sizes=(200, 400, 800), repeats=10):
@@ -607,6 +661,133 @@ def paper_table(dev, sizes=(200, 400, 800), repeats=10):
             rows[name] = {"time_s": ms * 1e-3, "gflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e9, "norm_inf_N_minus_C": err}
         table[str(n)] = rows
     return {"workload": "C = A (8A), A uniform [-1, 1]", "repeats": repeats, "time": "mean of one product", "n": table}
+
+
+def paper_table_cpu(sizes=(200, 400, 800), repeats=10):
+    """The paper's own test (section 'Tests') on this machine's host cores with
+    the CPU oracle (plain C, -O2, no FMA contraction): C = A (8A) for a random
+    n x n A, each method single-threaded and timed over `repeats` runs, and
+    NormInf(N - C) with N the NaivKahan result.  The ten methods run at the
+    same time, one thread each, each thread pinned to its own core when there
+    are enough; the time is the mean of one product."""
+    import numpy as np
+
+    import oracle
+    import synthetic as S
+
+    oracle.build()
+    methods = {
+        "NaivKahan (N)": oracle.naiv_kahan,
+        "NaivStandard": oracle.naiv_standard,
+        "NaivOnArray": oracle.naiv_on_array,
+        "NaivLoopUnrollingTwo": oracle.naiv_unrolled_2,
+        "NaivLoopUnrollingThree": oracle.naiv_unrolled_3,
+        "NaivLoopUnrollingFour": oracle.naiv_unrolled_4,
+        "StrassenNaiv": lambda x, y: oracle.strassen_naiv(x, y),
+        "StrassenWinograd": lambda x, y: oracle.strassen_winograd(x, y),
+        "WinogradOriginal": oracle.winograd_original,
+        "WinogradScaled": lambda x, y: oracle.winograd_scaled(x, y)[0],
+    }
+    try:
+        cores = sorted(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = []
+    pin = len(cores) >= len(methods)
+    table = {}
+    for n in sizes:
+        a, b = S.paper_pair(n, S.stream_seed(5, n))
+        results, times = {}, {}
+
+        def work(idx, name, fn):
+            if pin:
+                os.sched_setaffinity(0, {cores[idx]})  # the calling thread only
+            t0 = time.perf_counter()
+            for _ in range(repeats):
+                c = fn(a, b)
+            times[name] = (time.perf_counter() - t0) / repeats
+            results[name] = c
+
+        ths = [threading.Thread(target=work, args=(i, nm, fn)) for i, (nm, fn) in enumerate(methods.items())]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        ref = results["NaivKahan (N)"]
+        table[str(n)] = {nm: {"time_s": times[nm], "gflops": 2.0 * n ** 3 / times[nm] / 1e9,
+                              "norm_inf_N_minus_C": oracle.norm_inf(np.asarray(ref) - np.asarray(results[nm]))}
+                         for nm in methods}
+    if pin:
+        os.sched_setaffinity(0, set(cores))
+    return {"workload": "C = A (8A), A uniform [-1, 1]", "repeats": repeats, "time": "mean of one product",
+            "threads": f"{len(methods)} methods at once, one thread each" + (", pinned to own cores" if pin else ""),
+            "host_cores": host_cores(), "n": table}
+
+
+def compact_line(core, sections):
+    """The one JSON line the bench prints: the contract's keys (`core`) plus a
+    short summary of each section; every section in full goes to the detail
+    file.  Stays a few KB whatever the sections hold."""
+    def get(d, *path):
+        for k in path:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+
+    def rnd(x, n=4):
+        return float(f"{x:.{n}g}") if isinstance(x, float) else x
+
+    line = dict(core)
+    e2e = sections.get("e2e")
+    if e2e:
+        line["e2e"] = {k: e2e[k] for k in ("value", "unit", "ms_per_step", "ms_mean", "ms_min", "ms_max", "steps",
+                                          "statistic", "h2d_bytes_per_step", "d2h_bytes_per_step", "call")
+                       if k in e2e}
+    if "cpu_baseline" in sections:
+        cb = sections["cpu_baseline"]
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample") if k in cb}
+    summary = {}
+    if "plain_fp64" in sections:
+        pf = sections["plain_fp64"]
+        summary["plain_fp64"] = {k: rnd(pf[k]) for k in ("value", "unit", "ms", "rel_inf_err_sampled",
+                                                           "fp64_pipe_frac") if k in pf}
+    if "accuracy" in sections:
+        summary["accuracy"] = {k: sections["accuracy"][k] for k in ("rel_inf_err_sampled", "target")}
+    if "fp64_peak" in sections:
+        fp = sections["fp64_peak"]
+        summary["fp64_peak_tflops"] = {"dfma": rnd(fp["dfma_tflops"]), "dmma": rnd(fp["dmma_tflops"]),
+                                       "sm_mhz": get(fp, "clocks", "sm_mhz")}
+    sv = sections.get("serving")
+    if sv:
+        lfl = sv.get("like_for_like_1e-14", {})
+        summary["serving"] = {
+            "requests": sv.get("requests"),
+            "saturated_rps": rnd(get(sv, "saturated", "requests_per_s")),
+            "paced_0.7x": {"p50_ms": rnd(get(sv, "paced", "p50_ms")), "p99_ms": rnd(get(sv, "paced", "p99_ms"))},
+            "1e-14_fp64_one_at_a_time": {"p50_ms": rnd(get(lfl, "fp64_one_at_a_time", "paced", "p50_ms")),
+                                         "p99_ms": rnd(get(lfl, "fp64_one_at_a_time", "paced", "p99_ms")),
+                                         "saturated_rps": rnd(get(lfl, "fp64_one_at_a_time",
+                                                                  "saturated_requests_per_s"))},
+            "1e-14_emulated": {"p50_ms": rnd(get(lfl, "emulated", "paced", "p50_ms")),
+                               "p99_ms": rnd(get(lfl, "emulated", "paced", "p99_ms")),
+                               "saturated_rps": rnd(get(lfl, "emulated", "saturated_requests_per_s"))},
+            "1e-14_emulated_at_fp64_rate": {"p50_ms": rnd(get(lfl, "emulated_at_fp64_rate", "p50_ms")),
+                                            "p99_ms": rnd(get(lfl, "emulated_at_fp64_rate", "p99_ms"))},
+        }
+    gv = sections.get("grouped_vs_single")
+    if gv:
+        summary["grouped_256"] = {"tflops": rnd(get(gv, "grouped", "tflops")),
+                                  "one_call_each_tflops": rnd(get(gv, "one_call_each", "tflops"))}
+    sh = sections.get("shape_4096x16384x4096")
+    if sh:
+        summary["shape_4096x16384x4096_tflops"] = rnd(sh.get("tflops"))
+    se = sections.get("strassen_over_emulated")
+    if se:
+        summary["strassen_winograd_1_over_emulated_8192_tflops"] = rnd(get(se, "8192", "strassen_winograd_1",
+                                                                            "tflops"))
+    if summary:
+        line["summary"] = summary
+    return line
 
 
 def run_ours(args):
@@ -769,11 +950,17 @@ def run_ours(args):
                            "target": 1e-14, "reference": "oracle Dot2 product on the sampled rows"}
         del cn
 
+        # The FP64 pipe's own rate, measured here (denominator of the FP64 fractions).
+        out["fp64_peak"] = fp64_peak(local)
+        pk64 = out["fp64_peak"]["dmma_tflops"]
+        out["plain_fp64"]["fp64_pipe_frac"] = out["plain_fp64"]["value"] / pk64 if pk64 else None
+        out["plain_fp64"]["fp64_pipe_frac_against"] = "mma.sync f64 probe"
+
         # Serving first, in its own process, before the long sections below.
         if not args.no_serve:
             out["serving"] = serve_in_own_process(local, args)
         if args.variants_n > 0:
-            out["fp64_methods"] = variants_bench(dev)
+            out["fp64_methods"] = variants_bench(dev, out["fp64_peak"])
             out["paper_table"] = paper_table(dev)
         if not args.no_configs:
             out["slice_sweep"] = slice_sweep(ta, tb, a, b, norm_a, norm_b, rows, truth)
@@ -790,12 +977,14 @@ def run_ours(args):
                                "sample": f"{rows_used} of {N} rows of C (NaivStandard, plain C), {el:.1f} s",
                                "single_thread": {"value": v1, "unit": "TFLOP/s", "cores": 1,
                                                  "sample": f"{rows1} rows of C, {el1:.1f} s (the paper-like figure)"}}
+        if not args.no_cpu_table and args.variants_n > 0:
+            out["paper_table_cpu"] = paper_table_cpu(repeats=args.cpu_table_repeats)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     if rank != 0:
         return
-    line = {
+    core = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "step_ms": {"median": statistics.median(per_step), "min": min(per_step), "max": max(per_step)},
@@ -806,12 +995,23 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "N": N, "P": P, "M": M, "slices": SLICES, "beta": 5 if KIND == 1 else 7,
                    "parallelism": "replicas" if world > 1 else "single", "l2": "inputs (1 GiB) larger than L2"},
         "roofline": roofline,
-        "vs_fp64_peak": {"fp64_peak_tflops": FP64_PEAK_TFLOPS, "ratio": value / world / FP64_PEAK_TFLOPS,
-                         "note": "2NPM/t per GPU against the FP64 rate (DFMA, DMMA) measured on this part"},
         "kernel_ms_per_launch": kernel_ms, "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
     }
-    line.update(out)
+    if "fp64_peak" in out:
+        pk64 = out["fp64_peak"]["dmma_tflops"]
+        core["vs_fp64_peak"] = {"fp64_peak_tflops": pk64, "ratio": value / world / pk64 if pk64 else None,
+                                "note": "2NPM/t per GPU against the FP64 rate measured in this run (mm_probe_fp64_peak)"}
+    line = compact_line(core, out)
+    detail = dict(line)
+    detail.update(out)
+    detail["step_ms_each"] = [round(x, 4) for x in per_step]
+    try:
+        with open(args.detail, "w") as f:
+            json.dump(detail, f, indent=1)
+        line["detail"] = os.path.relpath(args.detail, ROOT)
+    except OSError as exc:
+        print(f"bench: could not write {args.detail}: {exc}", file=sys.stderr)
     print(json.dumps(line), flush=True)
 
 
@@ -851,7 +1051,7 @@ def main():
 
         mmbuild.build()
         # profiling runs: every FP64 method once (after one warm-up) at n = --n
-        print(json.dumps(variants_bench(torch.device("cuda", 0), (args.n,), reps=1)), flush=True)
+        print(json.dumps(variants_bench(torch.device("cuda", 0), fp64_peak(0), (args.n,), reps=1)), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -338,7 +338,8 @@ int mm_strassen_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64
  *     slice pairs at 1.2 (BF16) or 2.4 (FP8) PFLOP/s; the environment variable
  *     MM_SERVER_BATCH_MS, read at creation, sets that cap, 0 lifts it, and
  *     MM_SERVER_CLASS_RATIO keeps to requests within that factor of the
- *     oldest one's estimated time) run as one grouped emulated
+ *     oldest one's estimated time, a factor in (0, 1) counting as 1; the
+ *     oldest request is always taken) run as one grouped emulated
  *     launch, replayed from a CUDA graph cached per stream, slice format and
  *     count when use_graphs != 0;
  *   - method 0: BF16 slices, the tier's count (mm_emulated_slices);
@@ -394,6 +395,18 @@ const char *mm_server_error(mm_server *server);
 /* Cancels requests that have not started (status MM_ERR_TIMEOUT), waits for
  * running batches, frees the server.  The arena may be reused afterwards. */
 int mm_server_destroy(mm_server *server);
+
+/*
+ * FP64 peak probe (measurement support; the paper has no counterpart): the
+ * rate of this device's FP64 pipe, the denominator of FP64 roofline
+ * fractions.  Runs a kernel of independent DFMA chains and one of independent
+ * mma.sync m8n8k4 f64 accumulators on every SM, each timed with CUDA events
+ * on `stream` after a warm-up and lengthened until one run lasts at least
+ * target_ms (0 < target_ms <= 10000).  Writes the rates in TFLOP/s (2 flop per
+ * FMA, 512 per MMA) to *dfma_tflops and *dmma_tflops (either may be NULL).
+ * Synchronises `stream`; allocates nothing.
+ */
+int mm_probe_fp64_peak(double target_ms, double *dfma_tflops, double *dmma_tflops, void *stream);
 
 /*
  * Kernel-level timing (measurement support).  While enabled, every kernel the

@@ -14,7 +14,7 @@ import ctypes
 from ._native import KernelStat, MMError, check, lib
 
 __all__ = ["naive", "naive_unrolled", "kahan", "winograd", "winograd_scaled", "winograd_rowcol_scaled", "strassen", "strassen_winograd", "strassen_emulated", "tune_strassen", "norm_inf",
-           "emulated", "emulated_host", "emulated_group", "emulated_noalloc", "emulated_slices", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
+           "emulated", "emulated_host", "emulated_group", "emulated_noalloc", "emulated_slices", "probe_fp64_peak", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
            "SLICE_FP8E4M3"]
 
 SLICE_BF16 = 0
@@ -267,6 +267,17 @@ def emulated_noalloc(a, b, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
     check("mm_emulated_noalloc", lib().mm_emulated_noalloc(*_gemm_args(a, b, c, n, p, m), kind, nslices, float(tier),
                                                            _stream(a.device)))
     return c
+
+
+def probe_fp64_peak(target_ms=100.0, device=None):
+    """The FP64 pipe's measured rate on this device (mm_probe_fp64_peak):
+    returns (DFMA TFLOP/s, mma.sync f64 TFLOP/s)."""
+    torch = _torch()
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    dfma, dmma = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check("mm_probe_fp64_peak", lib().mm_probe_fp64_peak(float(target_ms), ctypes.byref(dfma), ctypes.byref(dmma),
+                                                         _stream(dev)))
+    return float(dfma.value), float(dmma.value)
 
 
 class profile:

@@ -85,6 +85,7 @@ SIGNATURES = {
     "mm_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "mm_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "mm_tune_clear": (ctypes.c_int, []),
+    "mm_probe_fp64_peak": (ctypes.c_int, [dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]),
     "mm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mm_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelStat), i32]),
 }

@@ -371,7 +371,8 @@ struct mm_server {
             double est_ms = 0.0;
             for (auto it = admitted.begin(); it != admitted.end() && (int)take.size() < cap;) {
                 const double t = request_ms(**it);
-                const bool same_class = class_ratio <= 0.0 ||
+                // The oldest request always goes; the class filter applies to the others.
+                const bool same_class = take.empty() || class_ratio <= 0.0 ||
                                         (t <= class_ratio * front_ms && front_ms <= class_ratio * t);
                 if ((*it)->s == s && (*it)->kind == kind && same_class) {
                     if (!take.empty() && batch_ms_cap > 0.0 && est_ms + t > batch_ms_cap) break;
@@ -382,6 +383,7 @@ struct mm_server {
                     ++it;
                 }
             }
+            if (take.empty()) break;
             const int rc = launch_batch(slots[k], (int)k, take);
             if (rc == MM_OK) {
                 any = true;
@@ -442,7 +444,11 @@ int mm_server_create(void *arena, size_t arena_bytes, int32_t max_batch, int32_t
     cudaGetDevice(&s->device);
     s->max_batch = method == 1 ? 1 : max_batch;
     if (const char *cap = getenv("MM_SERVER_BATCH_MS")) s->batch_ms_cap = atof(cap);
-    if (const char *ratio = getenv("MM_SERVER_CLASS_RATIO")) s->class_ratio = atof(ratio);
+    if (const char *ratio = getenv("MM_SERVER_CLASS_RATIO")) {
+        // A factor below 1 would exclude every request but the oldest: values in (0, 1) count as 1.
+        const double r = atof(ratio);
+        s->class_ratio = r <= 0.0 ? 0.0 : std::max(1.0, r);
+    }
     s->method = method;
     s->use_graphs = use_graphs != 0 && method != 1;
     const size_t table_cap = mm::group_table_bytes(s->max_batch);
