@@ -63,6 +63,8 @@ def parse():
                     help="only the per-method FP64 timings at n = --n, one run each (profiling runs)")
     ap.add_argument("--detail", default=os.path.join(ROOT, "bench_detail.json"),
                     help="file that receives every section of the run (the printed line carries summaries)")
+    ap.add_argument("--grouped-only", type=int, default=0, metavar="COUNT",
+                    help="profiling runs: only the grouped launch of COUNT serving-shaped products")
     ap.add_argument("--no-cpu-table", action="store_true", help="skip the CPU oracle's run of the paper's test")
     ap.add_argument("--cpu-table-repeats", type=int, default=10)
     args = ap.parse_args()
@@ -1052,6 +1054,14 @@ def main():
         mmbuild.build()
         # profiling runs: every FP64 method once (after one warm-up) at n = --n
         print(json.dumps(variants_bench(torch.device("cuda", 0), fp64_peak(0), (args.n,), reps=1)), flush=True)
+        return
+    if args.grouped_only:
+        import torch
+
+        from paper_1106_1347_gb300 import build as mmbuild
+
+        mmbuild.build()
+        print(json.dumps(grouped_vs_single(torch.device("cuda", 0), args.grouped_only)), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -159,12 +159,25 @@ int mm_winograd_rowcol_scaled(int64_t N, int64_t P, int64_t M, const double *A, 
  *   cutoff == -1: the depth mm_tune_strassen recorded for this shape bucket,
  *                else one level per doubling of max(N, P, M) above 1024 (at
  *                most 3); each dimension padded to a multiple of 2^depth.
- * Padding is virtual (out-of-range elements read as zero).  The innermost
- * level forms the operand sums (Plus/Minus) while staging tiles and adds
- * +-H_i into the C quadrants in the paper's left-to-right order in its
- * epilogue; outer levels keep their operand sums and H_i in the workspace.
- * Depth is limited to 10 levels and 7^(depth-1) <= 2401 innermost launches;
- * deeper requests return MM_ERR_UNSUPPORTED.
+ * Padding is virtual (out-of-range elements read as zero).  Every node of a
+ * recursion level is processed by the same launch (breadth-first):
+ *   - the operand sums (Plus/Minus) of one or two levels are formed in one
+ *     pass over all nodes of a level, each sum rounded as the section's
+ *     Aux matrices are, in the printed order;
+ *   - blocks of at most 32 at the bottom: the last level runs in shared
+ *     memory (operand sums, seven naive FMA block products, C-block sums);
+ *     blocks of at most 64: naive block products in shared memory; larger
+ *     blocks: the last level forms its operand sums while staging tiles for
+ *     the FP64 MMA and adds +-H_i into the C quadrants in its epilogue;
+ *   - the C blocks of one or two levels are formed in one pass, left to
+ *     right as printed.
+ * When a plan's breadth-first arrays would exceed 8 GiB (environment variable
+ * MM_STRASSEN_BREADTH_CAP, in bytes, read at each call and each workspace
+ * query, overrides this), its top levels run depth-first, one child at a
+ * time; the result is the same.  Depth is limited to 16 levels; deeper
+ * requests return MM_ERR_UNSUPPORTED.  On integer inputs whose sums stay
+ * below 2^53 the result is exact; otherwise it differs from a sequential
+ * evaluation only by the FMA rounding of the block products.
  */
 size_t mm_strassen_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t cutoff);
 int mm_strassen(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,

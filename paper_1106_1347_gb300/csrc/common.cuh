@@ -86,6 +86,14 @@ size_t strassen_ws_bytes(int variant, int depth, int64_t Np, int64_t Pp, int64_t
 int run_strassen(int variant, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
                  int64_t ldb, double *C, int64_t ldc, int depth, int64_t Np, int64_t Pp, int64_t Mp, void *ws,
                  cudaStream_t st);
+// One fused recursion level (gemm_f64.cu) for `nodes` equal nodes at fixed
+// element strides za, zb, zc: node z's operands are 2n x 2p (reads past
+// arows x acols are 0) and 2p x 2m, its result 2n x 2m (writes past
+// crows x ccols dropped).
+int run_strassen_level(int variant, int64_t nodes, int64_t n, int64_t p, int64_t m, const double *A, int64_t lda,
+                       int64_t arows, int64_t acols, int64_t za, const double *B, int64_t ldb, int64_t brows,
+                       int64_t bcols, int64_t zb, double *C, int64_t ldc, int64_t crows, int64_t ccols, int64_t zc,
+                       cudaStream_t st);
 int emulated_slices(int32_t kind, int32_t nslices, double tier);
 // kind: MM_SLICE_BF16 or MM_SLICE_FP8E4M3.
 size_t emulated_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind);

@@ -17,10 +17,10 @@
 //   Winograd:  H1..H7 gives C11 = H1+H2, C12 = ((H1+H3)+H4)+H6 = H9+H6,
 //              C21 = ((H1+H3)+H5)+H7 = (H8+H5)+H7, C22 = ((H1+H3)+H4)+H5 = H9+H5.
 // Padding to the recursion's sizes is virtual: reads outside an operand's
-// valid region return zero, writes outside C's region are dropped.
-// Outer recursion levels (depth >= 2) keep their operand sums and H_i in the
-// caller's workspace, like the paper's Aux matrices, and combine them with an
-// elementwise kernel; only the innermost level is fused.
+// valid region return zero, writes outside C's region are dropped.  Grid z
+// walks a batch of equal-size nodes laid out at fixed strides, so one launch
+// runs the fused level of every node of a recursion level (strassen.cu drives
+// the levels above it).
 //
 // Tiling: 64x64 output tile (32x32 when that leaves SMs idle), K-step 16,
 // 4 warps each owning a quarter as 8x8x4 MMA tiles.  The kernel is bound by the FP64 pipe: on GB300 the
@@ -72,6 +72,7 @@ struct LevelArgs {
     double *C;
     int64_t ldc, crows, ccols;
     int64_t n, p, m;  // product size: H is n x m with inner dimension p (quadrant size for a level)
+    int64_t za, zb, zc;  // element offsets from one node to the next (grid z walks nodes)
     int nprod;
     Product prod[7];
 };
@@ -133,6 +134,10 @@ __global__ void __launch_bounds__(128) level_kernel(const __grid_constant__ Leve
     const int g = lane >> 2, t4 = lane & 3;
     const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
     const int64_t n = args.n, p = args.p, m = args.m;
+    View Av = args.A, Bv = args.B;
+    Av.p += (int64_t)blockIdx.z * args.za;
+    Bv.p += (int64_t)blockIdx.z * args.zb;
+    double *const Cz = args.C + (int64_t)blockIdx.z * args.zc;
 
     for (int pi = 0; pi < args.nprod; ++pi) {
         const Product &pr = args.prod[pi];
@@ -150,9 +155,9 @@ __global__ void __launch_bounds__(128) level_kernel(const __grid_constant__ Leve
                 double v = 0.0;
                 if (gi < n && gk < p) {
                     if (kSingle)
-                        v = view_at(args.A, gi, gk);
+                        v = view_at(Av, gi, gk);
                     else
-                        v = eval_expr(pr.a, args.A, gi, gk, n, p);
+                        v = eval_expr(pr.a, Av, gi, gk, n, p);
                 }
                 ra[r] = v;
             }
@@ -163,9 +168,9 @@ __global__ void __launch_bounds__(128) level_kernel(const __grid_constant__ Leve
                 double v = 0.0;
                 if (gk < p && gj < m) {
                     if (kSingle)
-                        v = view_at(args.B, gk, gj);
+                        v = view_at(Bv, gk, gj);
                     else
-                        v = eval_expr(pr.b, args.B, gk, gj, p, m);
+                        v = eval_expr(pr.b, Bv, gk, gj, p, m);
                 }
                 rb[r] = v;
             }
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(128) level_kernel(const __grid_constant__ Leve
                 for (int ni = 0; ni < NI; ++ni) {
                     const int64_t col = j0 + wn * (BN / 2) + ni * 8 + 2 * t4;
                     const int64_t ccol = col + coff;
-                    double *dst = args.C + crow * args.ldc + ccol;
+                    double *dst = Cz + crow * args.ldc + ccol;
                     const double v0 = sgn * acc[mi][ni][0], v1 = sgn * acc[mi][ni][1];
                     const bool ok0 = col < m && ccol < args.ccols;
                     const bool ok1 = col + 1 < m && ccol + 1 < args.ccols;
@@ -233,27 +238,6 @@ __global__ void __launch_bounds__(128) level_kernel(const __grid_constant__ Leve
             }
         }
     }
-}
-
-// Elementwise out(i, j) = expression over up to four term views, for
-// i < rows, j < cols (the outer recursion levels' Plus/Minus passes).
-struct CombineArgs {
-    View term[4];
-    Expr e;
-    double *out;
-    int64_t ldo, rows, cols;
-};
-
-__global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ CombineArgs a) {
-    const int64_t j = (int64_t)blockIdx.x * 64 + (threadIdx.x & 63);
-    const int64_t i = (int64_t)blockIdx.y * 4 + (threadIdx.x >> 6);
-    if (i >= a.rows || j >= a.cols) return;
-    double x[4] = {0.0, 0.0, 0.0, 0.0};
-    const int nt = expr_terms(a.e);
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-        if (t < nt) x[t] = view_at(a.term[a.e.term[t]], i, j);
-    a.out[i * a.ldo + j] = eval_shape(a.e, x);
 }
 
 constexpr int8_t P_ = 1, M_ = -1;  // Plus, Minus
@@ -304,13 +288,13 @@ void strassen_winograd_products(Product (&pr)[7]) {
     pr[6] = Product{E1(T22), E6(T21, M_, T22, M_, T12, P_, T11), 1, {tgt(T21, 1, false)}};
 }
 
-int launch_level(const LevelArgs &a, bool single, cudaStream_t st) {
-    if (a.m <= 0 || a.n <= 0) return MM_OK;
+int launch_level(const LevelArgs &a, bool single, cudaStream_t st, int64_t nodes = 1) {
+    if (a.m <= 0 || a.n <= 0 || nodes <= 0) return MM_OK;
     // 64 x 64 tiles when they give at least four CTAs per SM, else 32 x 32.
-    const bool big = mm::ceil_div(a.m, 64) * mm::ceil_div(a.n, 64) >= 4 * mm::sm_count();
+    const bool big = mm::ceil_div(a.m, 64) * mm::ceil_div(a.n, 64) * nodes >= 4 * mm::sm_count();
     const int tile = big ? 64 : 32;
-    dim3 grid((unsigned)mm::ceil_div(a.m, tile), (unsigned)mm::ceil_div(a.n, tile));
-    if (grid.y > 65535) return mm::fail(MM_ERR_UNSUPPORTED, "product too tall for one launch");
+    dim3 grid((unsigned)mm::ceil_div(a.m, tile), (unsigned)mm::ceil_div(a.n, tile), (unsigned)nodes);
+    if (grid.y > 65535 || nodes > 65535) return mm::fail(MM_ERR_UNSUPPORTED, "product too tall for one launch");
     if (single)
         return mm::launch("gemm_f64_dmma", st, [&] {
             if (big)
@@ -324,195 +308,6 @@ int launch_level(const LevelArgs &a, bool single, cudaStream_t st) {
         else
             level_kernel<false, 32, 32><<<grid, 128, 0, st>>>(a);
     });
-}
-
-int launch_combine(const CombineArgs &a, cudaStream_t st) {
-    if (a.rows <= 0 || a.cols <= 0) return MM_OK;
-    dim3 grid((unsigned)mm::ceil_div(a.cols, 64), (unsigned)mm::ceil_div(a.rows, 4));
-    return mm::launch("strassen_combine", st, [&] { combine_kernel<<<grid, 256, 0, st>>>(a); });
-}
-
-View quadrant(const View &v, int q, int64_t hr, int64_t hc) {
-    const int64_t r0 = (q >> 1) * hr, c0 = (q & 1) * hc;
-    View o;
-    o.p = v.p + r0 * v.ld + c0;
-    o.ld = v.ld;
-    o.rows = std::max<int64_t>(0, std::min<int64_t>(hr, v.rows - r0));
-    o.cols = std::max<int64_t>(0, std::min<int64_t>(hc, v.cols - c0));
-    if (o.rows == 0 || o.cols == 0) o.p = v.p;  // never dereferenced
-    return o;
-}
-
-struct Arena {
-    char *base;
-    size_t used;
-    double *take(int64_t elems) {
-        double *p = (double *)(base + used);
-        used += mm::align_up((size_t)elems * sizeof(double), 256);
-        return p;
-    }
-};
-
-size_t node_bytes(int variant, int64_t n, int64_t p, int64_t m) {
-    auto b = [](int64_t e) { return mm::align_up((size_t)e * sizeof(double), 256); };
-    const int64_t hn = n / 2, hp = p / 2, hm = m / 2;
-    size_t s = b(hn * hp) + b(hp * hm) + 7 * b(hn * hm);
-    if (variant == 1) s += 2 * b(hn * hp) + 2 * b(hp * hm);
-    return s;
-}
-
-// Materialise expression `e` over quadrants of `v` into a dense hr x hc buffer.
-int materialize(const Expr &e, const View &v, int64_t hr, int64_t hc, double *out, cudaStream_t st) {
-    CombineArgs c{};
-    for (int q = 0; q < 4; ++q) c.term[q] = quadrant(v, q, hr, hc);
-    c.e = e;
-    c.out = out;
-    c.ldo = hc;
-    c.rows = hr;
-    c.cols = hc;
-    return launch_combine(c, st);
-}
-
-int node(int variant, int depth, int64_t n, int64_t p, int64_t m, const View &A, const View &B, double *C,
-         int64_t ldc, int64_t crows, int64_t ccols, Arena arena, cudaStream_t st) {
-    if (depth == 1) {
-        LevelArgs a{};
-        a.A = A;
-        a.B = B;
-        a.C = C;
-        a.ldc = ldc;
-        a.crows = crows;
-        a.ccols = ccols;
-        a.n = n / 2;
-        a.p = p / 2;
-        a.m = m / 2;
-        a.nprod = 7;
-        if (variant == 0)
-            strassen_products(a.prod);
-        else
-            strassen_winograd_products(a.prod);
-        return launch_level(a, false, st);
-    }
-    const int64_t hn = n / 2, hp = p / 2, hm = m / 2;
-    double *S = arena.take(hn * hp), *T = arena.take(hp * hm);
-    double *H[8];
-    for (int h = 1; h <= 7; ++h) H[h] = arena.take(hn * hm);
-    auto dense = [](const double *ptr, int64_t r, int64_t c) { return View{ptr, c, r, c}; };
-    auto qa = [&](int q) { return quadrant(A, q, hn, hp); };
-    auto qb = [&](int q) { return quadrant(B, q, hp, hm); };
-    int rc = MM_OK;
-    auto child = [&](const View &a, const View &b, double *h) {
-        if (rc == MM_OK) rc = node(variant, depth - 1, hn, hp, hm, a, b, h, hm, hn, hm, arena, st);
-    };
-    auto mat_a = [&](const Expr &e) {
-        if (rc == MM_OK) rc = materialize(e, A, hn, hp, S, st);
-        return dense(S, hn, hp);
-    };
-    auto mat_b = [&](const Expr &e) {
-        if (rc == MM_OK) rc = materialize(e, B, hp, hm, T, st);
-        return dense(T, hp, hm);
-    };
-    auto combine_into = [&](int q, std::initializer_list<int> hs, const Expr &e) {
-        CombineArgs c{};
-        int i = 0;
-        for (int h : hs) c.term[i++] = dense(H[h], hn, hm);
-        c.e = e;
-        const int64_t r0 = (q >> 1) * hn, c0 = (q & 1) * hm;
-        c.out = C + r0 * ldc + c0;
-        c.ldo = ldc;
-        c.rows = std::max<int64_t>(0, std::min<int64_t>(hn, crows - r0));
-        c.cols = std::max<int64_t>(0, std::min<int64_t>(hm, ccols - c0));
-        if (rc == MM_OK) rc = launch_combine(c, st);
-    };
-    if (variant == 0) {
-        child(mat_a(E2(T11, P_, T22)), mat_b(E2(T11, P_, T22)), H[1]);
-        child(mat_a(E2(T21, P_, T22)), qb(T11), H[2]);
-        child(qa(T11), mat_b(E2(T12, M_, T22)), H[3]);
-        child(qa(T22), mat_b(E2(T21, M_, T11)), H[4]);
-        child(mat_a(E2(T11, P_, T12)), qb(T22), H[5]);
-        {
-            View sa = mat_a(E2(T21, M_, T11));
-            View tb = mat_b(E2(T11, P_, T12));
-            child(sa, tb, H[6]);
-        }
-        {
-            View sa = mat_a(E2(T12, M_, T22));
-            View tb = mat_b(E2(T21, P_, T22));
-            child(sa, tb, H[7]);
-        }
-        // C11 = ((H1+H4)-H5)+H7, C12 = H3+H5, C21 = H2+H4, C22 = ((H1+H3)-H2)+H6
-        combine_into(T11, {1, 4, 5, 7}, E7(0, P_, 1, M_, 2, P_, 3));
-        combine_into(T12, {3, 5}, E2(0, P_, 1));
-        combine_into(T21, {2, 4}, E2(0, P_, 1));
-        combine_into(T22, {1, 3, 2, 6}, E7(0, P_, 1, M_, 2, P_, 3));
-    } else {
-        double *A1 = arena.take(hn * hp), *A2 = arena.take(hn * hp);
-        double *B1 = arena.take(hp * hm), *B2 = arena.take(hp * hm);
-        // A1 = A11 - A21, A2 = A22 - A1, B1 = B22 - B12, B2 = B1 + B11
-        if (rc == MM_OK) rc = materialize(E2(T11, M_, T21), A, hn, hp, A1, st);
-        if (rc == MM_OK) {
-            CombineArgs c{};
-            c.term[0] = qa(T22);
-            c.term[1] = dense(A1, hn, hp);
-            c.e = E2(0, M_, 1);
-            c.out = A2;
-            c.ldo = hp;
-            c.rows = hn;
-            c.cols = hp;
-            rc = launch_combine(c, st);
-        }
-        if (rc == MM_OK) rc = materialize(E2(T22, M_, T12), B, hp, hm, B1, st);
-        if (rc == MM_OK) {
-            CombineArgs c{};
-            c.term[0] = dense(B1, hp, hm);
-            c.term[1] = qb(T11);
-            c.e = E2(0, P_, 1);
-            c.out = B2;
-            c.ldo = hm;
-            c.rows = hp;
-            c.cols = hm;
-            rc = launch_combine(c, st);
-        }
-        child(qa(T11), qb(T11), H[1]);
-        child(qa(T12), qb(T21), H[2]);
-        child(dense(A2, hn, hp), dense(B2, hp, hm), H[3]);
-        {
-            View sa = mat_a(E2(T21, P_, T22));
-            View tb = mat_b(E2(T12, M_, T11));
-            child(sa, tb, H[4]);
-        }
-        child(dense(A1, hn, hp), dense(B1, hp, hm), H[5]);
-        if (rc == MM_OK) {  // S = A12 - A2
-            CombineArgs c{};
-            c.term[0] = qa(T12);
-            c.term[1] = dense(A2, hn, hp);
-            c.e = E2(0, M_, 1);
-            c.out = S;
-            c.ldo = hp;
-            c.rows = hn;
-            c.cols = hp;
-            rc = launch_combine(c, st);
-        }
-        child(dense(S, hn, hp), qb(T22), H[6]);
-        if (rc == MM_OK) {  // T = B21 - B2
-            CombineArgs c{};
-            c.term[0] = qb(T21);
-            c.term[1] = dense(B2, hp, hm);
-            c.e = E2(0, M_, 1);
-            c.out = T;
-            c.ldo = hm;
-            c.rows = hp;
-            c.cols = hm;
-            rc = launch_combine(c, st);
-        }
-        child(qa(T22), dense(T, hp, hm), H[7]);
-        // C11 = H1+H2, C12 = ((H1+H3)+H4)+H6, C21 = ((H1+H3)+H5)+H7, C22 = ((H1+H3)+H4)+H5
-        combine_into(T11, {1, 2}, E2(0, P_, 1));
-        combine_into(T12, {1, 3, 4, 6}, E7(0, P_, 1, P_, 2, P_, 3));
-        combine_into(T21, {1, 3, 5, 7}, E7(0, P_, 1, P_, 2, P_, 3));
-        combine_into(T22, {1, 3, 4, 5}, E7(0, P_, 1, P_, 2, P_, 3));
-    }
-    return rc;
 }
 
 }  // namespace
@@ -536,51 +331,41 @@ int run_naive(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, con
     return launch_level(a, true, st);
 }
 
-// Depth and padded sizes of the recursion (see mm_strassen in mm.h).
-int strassen_plan(int variant, int64_t N, int64_t P, int64_t M, int32_t cutoff, int *depth, int64_t *Np,
-                  int64_t *Pp, int64_t *Mp) {
-    const int64_t X = std::max(N, std::max(P, M));
-    int d = 0;
-    if (cutoff == 0) {  // the paper's rule, square embedding
-        int lg = -1;
-        for (int64_t t = X; t > 0; t >>= 1) ++lg;
-        d = std::max(0, lg - 4);
-        const int64_t Y = ((X >> d) + 1) << d;
-        *depth = d;
-        *Np = *Pp = *Mp = Y;
-    } else {
-        if (cutoff > 0) {
-            while (ceil_div(X, (int64_t)1 << d) > cutoff) ++d;
-        } else if (!tuned_strassen_depth(variant, N, P, M, &d)) {
-            // untuned default: one level per doubling above 1024, at most 3
-            for (int64_t t = X; t >= 2048 && d < 3; t >>= 1) ++d;
-        }
-        const int64_t q = (int64_t)1 << d;
-        *depth = d;
-        *Np = ceil_div(N, q) * q;
-        *Pp = ceil_div(P, q) * q;
-        *Mp = ceil_div(M, q) * q;
+// One fused recursion level for `nodes` equal-size nodes: node z's A operand
+// (2n x 2p, leading dimension lda, reads at or past arows x acols return 0) sits
+// at A + z za, its B operand (2p x 2m) at B + z zb, and its C (2n x 2m, writes
+// at or past crows x ccols dropped) at C + z zc.
+int run_strassen_level(int variant, int64_t nodes, int64_t n, int64_t p, int64_t m, const double *A, int64_t lda,
+                       int64_t arows, int64_t acols, int64_t za, const double *B, int64_t ldb, int64_t brows,
+                       int64_t bcols, int64_t zb, double *C, int64_t ldc, int64_t crows, int64_t ccols, int64_t zc,
+                       cudaStream_t st) {
+    LevelArgs a{};
+    a.A = View{A, lda, arows, acols};
+    a.B = View{B, ldb, brows, bcols};
+    a.C = C;
+    a.ldc = ldc;
+    a.crows = crows;
+    a.ccols = ccols;
+    a.n = n;
+    a.p = p;
+    a.m = m;
+    a.za = za;
+    a.zb = zb;
+    a.zc = zc;
+    a.nprod = 7;
+    if (variant == 0)
+        strassen_products(a.prod);
+    else
+        strassen_winograd_products(a.prod);
+    for (int64_t z0 = 0; z0 < nodes; z0 += 65535) {  // grid z holds at most 65535 nodes per launch
+        LevelArgs b = a;
+        b.A.p = A + z0 * za;
+        b.B.p = B + z0 * zb;
+        b.C = C + z0 * zc;
+        const int rc = launch_level(b, false, st, std::min<int64_t>(65535, nodes - z0));
+        if (rc) return rc;
     }
-    if (*depth > 10) return fail(MM_ERR_UNSUPPORTED, "Strassen depth %d exceeds 10", *depth);
-    int64_t launches = 1;
-    for (int i = 1; i < *depth; ++i) launches *= 7;
-    if (launches > 2401) return fail(MM_ERR_UNSUPPORTED, "Strassen depth %d needs %lld innermost launches (> 2401)",
-                                     *depth, (long long)launches);
     return MM_OK;
-}
-
-size_t strassen_ws_bytes(int variant, int depth, int64_t Np, int64_t Pp, int64_t Mp) {
-    size_t total = 0;
-    for (int L = 0; L + 2 <= depth; ++L) total += node_bytes(variant, Np >> L, Pp >> L, Mp >> L);
-    return total;
-}
-
-int run_strassen(int variant, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
-                 int64_t ldb, double *C, int64_t ldc, int depth, int64_t Np, int64_t Pp, int64_t Mp, void *ws,
-                 cudaStream_t st) {
-    if (depth == 0) return run_naive(N, P, M, A, lda, B, ldb, C, ldc, st);
-    Arena arena{(char *)ws, 0};
-    return node(variant, depth, Np, Pp, Mp, View{A, lda, N, P}, View{B, ldb, P, M}, C, ldc, N, M, arena, st);
 }
 
 }  // namespace mm

@@ -94,7 +94,10 @@ def test_host_side_queries_and_checks(native):
                                     8, 1e-14, None, 0, None) == -1
     assert lib.mm_strassen_emulated(8, 8, 8, fake, 8, ctypes.c_void_p(0x30000), 8, ctypes.c_void_p(0x50000), 8, 0, 1, 0,
                                     8, 1e-14, None, 0, None) == -6  # no workspace
-    # the paper's Strassen rule beyond 2401 innermost launches is refused
-    assert lib.mm_strassen_workspace_bytes(4096, 4096, 4096, 0) == 0
+    # the paper's Strassen rule at 4096 (depth 8) needs a workspace; depth 17 (X = 2^21) is refused
+    assert lib.mm_strassen_workspace_bytes(4096, 4096, 4096, 0) > 0
     assert lib.mm_strassen(4096, 4096, 4096, fake, 4096, ctypes.c_void_p(0x30000), 4096, ctypes.c_void_p(0x10000000000),
-                           4096, 0, None, 0, None) == -4
+                           4096, 0, None, 0, None) == -6
+    assert lib.mm_strassen_workspace_bytes(1 << 21, 1, 1, 0) == 0
+    assert lib.mm_strassen(1 << 21, 1, 1, fake, 1, ctypes.c_void_p(0x1000000000), 1, ctypes.c_void_p(0x2000000000),
+                           1, 0, None, 0, None) == -4

@@ -87,3 +87,6 @@ def test_fp64_methods_full_size_sampled_rows(mm, orc, n):
     truth = orc.dot2_product(ar, b)
     for name in ("winograd_scaled", "winograd_rowcol_scaled", "strassen", "strassen_winograd"):
         assert normwise(rows_of(getattr(mm, name)(ta, tb)), truth) <= 1e-14, name
+    # The paper's own depth rule: 8 levels (Y = 4352) at 4095, 9 (Y = 8704) at 8192.
+    for name in ("strassen", "strassen_winograd"):
+        assert normwise(rows_of(getattr(mm, name)(ta, tb, cutoff=0)), truth) <= 1e-14, name
