@@ -62,6 +62,26 @@ inline size_t span_bytes(int64_t rows, int64_t cols, int64_t ld) {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Side of the square output tile of a CUDA-core or FP64-MMA kernel, from
+// `sides` (largest first): the one whose grid of tiles fills the SMs' waves
+// best (ctas / (waves * SMs), waves = ceil(ctas / SMs)), the larger one when
+// two are within 2% (fewer operand reloads); `batch` grids of that size run
+// together.  Small products then take small tiles and keep every SM busy.
+inline int pick_tile(int64_t N, int64_t M, const int *sides, int count, int64_t batch = 1) {
+    const int64_t sms = sm_count();
+    int best = sides[0];
+    double best_eff = -1.0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t ctas = ceil_div(N, sides[i]) * ceil_div(M, sides[i]) * batch;
+        const double eff = (double)ctas / (double)(ceil_div(ctas, sms) * sms);
+        if (eff > best_eff + 0.02) {
+            best = sides[i];
+            best_eff = eff;
+        }
+    }
+    return best;
+}
+
 // Checks shared by every C = A B entry point.  Returns MM_OK or MM_ERR_ARG.
 int check_gemm_args(const char *fn, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
                     int64_t ldb, const double *C, int64_t ldc);

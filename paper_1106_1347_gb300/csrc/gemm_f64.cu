@@ -22,7 +22,7 @@
 // runs the fused level of every node of a recursion level (strassen.cu drives
 // the levels above it).
 //
-// Tiling: 64x64 output tile (32x32 when that leaves SMs idle), K-step 16,
+// Tiling: 64x64 output tile (32x32 or 16x16 when that leaves SMs idle), K-step 16,
 // 4 warps each owning a quarter as 8x8x4 MMA tiles.  The kernel is bound by the FP64 pipe: on GB300 the
 // m8n8k4 f64 MMA and DFMA both measure ~1.06 TFLOP/s, and the MMA needs 16x
 // fewer instructions.  At that rate the loads do not matter, so operand tiles
@@ -121,8 +121,8 @@ __device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
 }
 
 // BM x BN output tile per CTA of 4 warps (2 x 2), each warp owning
-// (BM/2) x (BN/2) as MI x NI MMA tiles of 8 x 8.  64 x 64 for large grids,
-// 32 x 32 when the 64 x 64 grid would leave SMs idle.
+// (BM/2) x (BN/2) as MI x NI MMA tiles of 8 x 8: 64 x 64 for large grids,
+// 32 x 32 or 16 x 16 when a larger tile's grid would leave SMs idle.
 template <bool kSingle, int BM, int BN>
 __global__ void __launch_bounds__(128) level_kernel(const __grid_constant__ LevelArgs args) {
     constexpr int BST = BN + 4;  // B tile row stride
@@ -290,23 +290,27 @@ void strassen_winograd_products(Product (&pr)[7]) {
 
 int launch_level(const LevelArgs &a, bool single, cudaStream_t st, int64_t nodes = 1) {
     if (a.m <= 0 || a.n <= 0 || nodes <= 0) return MM_OK;
-    // 64 x 64 tiles when they give at least four CTAs per SM, else 32 x 32.
-    const bool big = mm::ceil_div(a.m, 64) * mm::ceil_div(a.n, 64) * nodes >= 4 * mm::sm_count();
-    const int tile = big ? 64 : 32;
+    // 64 x 64, 32 x 32 or 16 x 16 tiles: the side whose grid fills the SMs best.
+    static const int sides[3] = {64, 32, 16};
+    const int tile = mm::pick_tile(a.n, a.m, sides, 3, nodes);
     dim3 grid((unsigned)mm::ceil_div(a.m, tile), (unsigned)mm::ceil_div(a.n, tile), (unsigned)nodes);
     if (grid.y > 65535 || nodes > 65535) return mm::fail(MM_ERR_UNSUPPORTED, "product too tall for one launch");
     if (single)
         return mm::launch("gemm_f64_dmma", st, [&] {
-            if (big)
+            if (tile == 64)
                 level_kernel<true, 64, 64><<<grid, 128, 0, st>>>(a);
-            else
+            else if (tile == 32)
                 level_kernel<true, 32, 32><<<grid, 128, 0, st>>>(a);
+            else
+                level_kernel<true, 16, 16><<<grid, 128, 0, st>>>(a);
         });
     return mm::launch("strassen_level_dmma", st, [&] {
-        if (big)
+        if (tile == 64)
             level_kernel<false, 64, 64><<<grid, 128, 0, st>>>(a);
-        else
+        else if (tile == 32)
             level_kernel<false, 32, 32><<<grid, 128, 0, st>>>(a);
+        else
+            level_kernel<false, 16, 16><<<grid, 128, 0, st>>>(a);
     });
 }
 

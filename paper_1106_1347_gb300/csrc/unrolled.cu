@@ -11,39 +11,41 @@
 // here it only fixes the rounding order, and the plain FP64 product
 // (mm_naive, DMMA) is the fast path.
 //
-// Same tiling as the Kahan kernel: 64x64 output tile, 256 threads, each owning
-// 4x4 outputs strided by 16, (aux, group) pairs in registers; FP64-pipe bound at
-// 1 DMUL + 1 DADD per k per output plus 1 DADD per group.
+// Same tiling as the Kahan kernel: 256 threads, each owning R x R outputs
+// strided by 16 in a 16R x 16R tile (R = 4, 2 or 1 by the size of the grid),
+// (aux, group) pairs in registers; FP64-pipe bound at 1 DMUL + 1 DADD per k per
+// output plus 1 DADD per group.
 #include <type_traits>
 
 #include "common.cuh"
 
 namespace {
 
-constexpr int TM = 64, TN = 64, TK = 16;
+constexpr int TK = 16;
 
-template <int U>
+template <int U, int R>
 __global__ void __launch_bounds__(256) unrolled_kernel(int64_t N, int64_t P, int64_t M, const double *__restrict__ A,
                                                        int64_t lda, const double *__restrict__ B, int64_t ldb,
                                                        double *__restrict__ C, int64_t ldc) {
-    __shared__ double As[TM][TK + 1];
-    __shared__ double Bs[TK][TN];
+    constexpr int T = 16 * R;  // output tile side
+    __shared__ double As[T][TK + 1];
+    __shared__ double Bs[TK][T];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t i0 = (int64_t)blockIdx.y * TM, j0 = (int64_t)blockIdx.x * TN;
+    const int64_t i0 = (int64_t)blockIdx.y * T, j0 = (int64_t)blockIdx.x * T;
     const int64_t full = (P / U) * U;  // products that fall in complete groups
-    double aux[4][4], grp[4][4];
+    double aux[R][R], grp[R][R];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) aux[r][c] = grp[r][c] = 0.0;
-    double ra[4], rb[4];
+        for (int c = 0; c < R; ++c) aux[r][c] = grp[r][c] = 0.0;
+    double ra[R], rb[R];
     auto fetch = [&](int64_t k0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < R; ++q) {
             const int e = tid + 256 * q;
             const int64_t gi = i0 + (e >> 4), gk = k0 + (e & 15);
             ra[q] = (gi < N && gk < P) ? A[gi * lda + gk] : 0.0;
-            const int64_t bk = k0 + (e >> 6), bj = j0 + (e & 63);
+            const int64_t bk = k0 + e / T, bj = j0 + e % T;
             rb[q] = (bk < P && bj < M) ? B[bk * ldb + bj] : 0.0;
         }
     };
@@ -52,10 +54,10 @@ __global__ void __launch_bounds__(256) unrolled_kernel(int64_t N, int64_t P, int
     for (int64_t k0 = 0; k0 < P; k0 += TK) {
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < R; ++q) {
             const int e = tid + 256 * q;
             As[e >> 4][e & 15] = ra[q];
-            Bs[e >> 6][e & 63] = rb[q];
+            Bs[e / T][e % T] = rb[q];
         }
         __syncthreads();
         if (k0 + TK < P) fetch(k0 + TK);
@@ -68,16 +70,16 @@ __global__ void __launch_bounds__(256) unrolled_kernel(int64_t N, int64_t P, int
                 constexpr int T0 = decltype(phase)::value;
 #pragma unroll
                 for (int kk = 0; kk < TK; ++kk) {
-                    double a[4], b[4];
+                    double a[R], b[R];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) a[r] = As[ty + 16 * r][kk];
+                    for (int r = 0; r < R; ++r) a[r] = As[ty + 16 * r][kk];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+                    for (int c = 0; c < R; ++c) b[c] = Bs[kk][tx + 16 * c];
                     const int pos = (T0 + kk) % U;
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
+                    for (int r = 0; r < R; ++r)
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
+                        for (int c = 0; c < R; ++c) {
                             const double x = __dmul_rn(a[r], b[c]);
                             if (U == 1) {
                                 aux[r][c] = __dadd_rn(aux[r][c], x);
@@ -98,16 +100,16 @@ __global__ void __launch_bounds__(256) unrolled_kernel(int64_t N, int64_t P, int
             continue;
         }
         for (int kk = 0; kk < kn; ++kk) {
-            double a[4], b[4];
+            double a[R], b[R];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] = As[ty + 16 * r][kk];
+            for (int r = 0; r < R; ++r) a[r] = As[ty + 16 * r][kk];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+            for (int c = 0; c < R; ++c) b[c] = Bs[kk][tx + 16 * c];
             const bool grouped = k0 + kk < full;
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < R; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < R; ++c) {
                     const double x = __dmul_rn(a[r], b[c]);
                     if (U == 1 || !grouped) {
                         aux[r][c] = __dadd_rn(aux[r][c], x);
@@ -120,11 +122,11 @@ __global__ void __launch_bounds__(256) unrolled_kernel(int64_t N, int64_t P, int
         }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < R; ++r) {
         const int64_t i = i0 + ty + 16 * r;
         if (i >= N) continue;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < R; ++c) {
             const int64_t j = j0 + tx + 16 * c;
             if (j < M) C[i * ldc + j] = aux[r][c];
         }
@@ -135,23 +137,34 @@ __global__ void __launch_bounds__(256) unrolled_kernel(int64_t N, int64_t P, int
 
 namespace mm {
 
+template <int U>
+int launch_unrolled(const char *name, int T, dim3 grid, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda,
+                    const double *B, int64_t ldb, double *C, int64_t ldc, cudaStream_t st) {
+    return launch(name, st, [&] {
+        if (T == 64)
+            unrolled_kernel<U, 4><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc);
+        else if (T == 32)
+            unrolled_kernel<U, 2><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc);
+        else
+            unrolled_kernel<U, 1><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc);
+    });
+}
+
 int run_unrolled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
                  double *C, int64_t ldc, int unroll, cudaStream_t st) {
-    dim3 grid((unsigned)ceil_div(M, TN), (unsigned)ceil_div(N, TM));
+    static const int sides[3] = {64, 32, 16};
+    const int T = pick_tile(N, M, sides, 3);
+    dim3 grid((unsigned)ceil_div(M, T), (unsigned)ceil_div(N, T));
     if (grid.y > 65535) return fail(MM_ERR_UNSUPPORTED, "mm_naive_unrolled: N too large for one launch");
     switch (unroll) {
     case 1:
-        return launch("naive_ordered_f64", st,
-                      [&] { unrolled_kernel<1><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc); });
+        return launch_unrolled<1>("naive_ordered_f64", T, grid, N, P, M, A, lda, B, ldb, C, ldc, st);
     case 2:
-        return launch("naive_unrolled2_f64", st,
-                      [&] { unrolled_kernel<2><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc); });
+        return launch_unrolled<2>("naive_unrolled2_f64", T, grid, N, P, M, A, lda, B, ldb, C, ldc, st);
     case 3:
-        return launch("naive_unrolled3_f64", st,
-                      [&] { unrolled_kernel<3><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc); });
+        return launch_unrolled<3>("naive_unrolled3_f64", T, grid, N, P, M, A, lda, B, ldb, C, ldc, st);
     case 4:
-        return launch("naive_unrolled4_f64", st,
-                      [&] { unrolled_kernel<4><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc); });
+        return launch_unrolled<4>("naive_unrolled4_f64", T, grid, N, P, M, A, lda, B, ldb, C, ldc, st);
     default:
         return fail(MM_ERR_ARG, "mm_naive_unrolled: unroll must be 1, 2, 3 or 4 (got %d)", unroll);
     }

@@ -21,6 +21,8 @@
 //     staged tiles by 2^-e_i and 2^-f_k and the result by 2^(e_i + f_k).
 // y and z are bit-identical to a sequential evaluation; the paired sum uses
 // one FMA per pair (2 DADD + 1 DFMA per pair per output, the FP64 pipe bound).
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace {
@@ -166,10 +168,12 @@ __device__ int brent_lambda(double a, double b) {
     return lam;
 }
 
-constexpr int TM = 64, TN = 64, TK = 16;
+constexpr int TK = 16;
 
 // kMode: 0 WinogradOriginal, 1 Brent's global lambda, 2 per-row/column exponents.
-template <int kMode>
+// 256 threads in a 16 x 16 layout, each owning R x R outputs strided by 16 of a
+// 16R x 16R tile (R = 4, 2 or 1 by the size of the grid).
+template <int kMode, int R>
 __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int64_t M, const double *__restrict__ A,
                                                        int64_t lda, const double *__restrict__ B, int64_t ldb,
                                                        double *__restrict__ C, int64_t ldc,
@@ -177,11 +181,12 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
                                                        const double *norms, int32_t *lambda_out,
                                                        const int32_t *__restrict__ ea, const int32_t *__restrict__ fb) {
     constexpr bool kScaled = kMode == 1, kRowCol = kMode == 2;
-    __shared__ double As[TM][TK + 1];
-    __shared__ double Bs[TK][TN];
+    constexpr int T = 16 * R;  // output tile side
+    __shared__ double As[T][TK + 1];
+    __shared__ double Bs[TK][T];
     __shared__ double s_scale[2];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t i0 = (int64_t)blockIdx.y * TM, j0 = (int64_t)blockIdx.x * TN;
+    const int64_t i0 = (int64_t)blockIdx.y * T, j0 = (int64_t)blockIdx.x * T;
     const int64_t K2 = (P / 2) * 2;
     if (tid == 0) {
         double sa = 1.0, sb = 1.0;
@@ -196,31 +201,31 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
     }
     __syncthreads();
     const double sa = s_scale[0], sb = s_scale[1];
-    double acc[4][4];
+    double acc[R][R];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
-    double ra[4], rb[4];
+        for (int c = 0; c < R; ++c) acc[r][c] = 0.0;
+    double ra[R], rb[R];
     // Per-row/column form: this thread stages rows (tid >> 4) + 16 q of A and
-    // column (tid & 63) of B in every K-step.
-    int erow[4], fcol = 0;
+    // column tid mod T of B in every K-step (256 q is a multiple of T).
+    int erow[R], fcol = 0;
     if (kRowCol) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < R; ++q) {
             const int64_t gi = i0 + ((tid + 256 * q) >> 4);
             erow[q] = gi < N ? ea[gi] : 0;
         }
-        const int64_t bj = j0 + (tid & 63);
+        const int64_t bj = j0 + (tid % T);
         fcol = bj < M ? fb[bj] : 0;
     }
     auto fetch = [&](int64_t k0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < R; ++q) {
             const int e = tid + 256 * q;
             const int64_t gi = i0 + (e >> 4), gk = k0 + (e & 15);
             double av = (gi < N && gk < K2) ? A[gi * lda + gk] : 0.0;
-            const int64_t bk = k0 + (e >> 6), bj = j0 + (e & 63);
+            const int64_t bk = k0 + e / T, bj = j0 + e % T;
             double bv = (bk < K2 && bj < M) ? B[bk * ldb + bj] : 0.0;
             if (kScaled) {
                 av *= sa;
@@ -238,30 +243,30 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
     for (int64_t k0 = 0; k0 < K2; k0 += TK) {
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < R; ++q) {
             const int e = tid + 256 * q;
             As[e >> 4][e & 15] = ra[q];
-            Bs[e >> 6][e & 63] = rb[q];
+            Bs[e / T][e % T] = rb[q];
         }
         __syncthreads();
         if (k0 + TK < K2) fetch(k0 + TK);
         const int np = (int)min((int64_t)TK, K2 - k0) / 2;
         for (int jj = 0; jj < np; ++jj) {
-            double ae[4], ao[4], be[4], bo[4];
+            double ae[R], ao[R], be[R], bo[R];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
+            for (int r = 0; r < R; ++r) {
                 ae[r] = As[ty + 16 * r][2 * jj];
                 ao[r] = As[ty + 16 * r][2 * jj + 1];
             }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < R; ++c) {
                 be[c] = Bs[2 * jj][tx + 16 * c];
                 bo[c] = Bs[2 * jj + 1][tx + 16 * c];
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < R; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < R; ++c) {
                     const double s1 = __dadd_rn(ae[r], bo[c]);
                     const double s2 = __dadd_rn(ao[r], be[c]);
                     acc[r][c] = fma(s1, s2, acc[r][c]);
@@ -270,7 +275,7 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
     }
     const bool odd = (P & 1) != 0;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < R; ++r) {
         const int64_t i = i0 + ty + 16 * r;
         if (i >= N) continue;
         double yi = y[i];
@@ -279,7 +284,7 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
         if (kScaled) yi = (yi * sa) * sa;
         if (odd) alast = kRowCol ? ldexp(A[i * lda + (P - 1)], -ei) : A[i * lda + (P - 1)] * sa;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < R; ++c) {
             const int64_t k = j0 + tx + 16 * c;
             if (k >= M) continue;
             double zk = z[k];
@@ -355,22 +360,25 @@ int run_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
         rc = launch("winograd_b_terms", st,
                     [&] { b_terms_kernel<<<(unsigned)ceil_div(M, 128), 128, 0, st>>>(P, M, B, ldb, z); });
     if (rc) return rc;
-    dim3 grid((unsigned)ceil_div(M, TN), (unsigned)ceil_div(N, TM));
+    static const int sides[3] = {64, 32, 16};
+    const int T = pick_tile(N, M, sides, 3);
+    dim3 grid((unsigned)ceil_div(M, T), (unsigned)ceil_div(N, T));
     if (grid.y > 65535) return fail(MM_ERR_UNSUPPORTED, "mm_winograd: N too large for one launch");
-    if (mode == 1)
-        return launch("winograd_scaled_f64", st, [&] {
-            winograd_kernel<1><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, norms, lambda_out,
-                                                     nullptr, nullptr);
-        });
-    if (mode == 2)
-        return launch("winograd_rowcol_scaled_f64", st, [&] {
-            winograd_kernel<2><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, nullptr, nullptr, ea,
-                                                     fb);
-        });
-    return launch("winograd_f64", st, [&] {
-        winograd_kernel<0><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, nullptr, nullptr, nullptr,
-                                                 nullptr);
-    });
+    auto go = [&](auto mode) {
+        constexpr int kM = decltype(mode)::value;
+        const double *nm = kM == 1 ? norms : nullptr;
+        int32_t *lo = kM == 1 ? lambda_out : nullptr;
+        const int32_t *e1 = kM == 2 ? ea : nullptr, *f1 = kM == 2 ? fb : nullptr;
+        if (T == 64)
+            winograd_kernel<kM, 4><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, nm, lo, e1, f1);
+        else if (T == 32)
+            winograd_kernel<kM, 2><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, nm, lo, e1, f1);
+        else
+            winograd_kernel<kM, 1><<<grid, 256, 0, st>>>(N, P, M, A, lda, B, ldb, C, ldc, y, z, nm, lo, e1, f1);
+    };
+    if (mode == 1) return launch("winograd_scaled_f64", st, [&] { go(std::integral_constant<int, 1>{}); });
+    if (mode == 2) return launch("winograd_rowcol_scaled_f64", st, [&] { go(std::integral_constant<int, 2>{}); });
+    return launch("winograd_f64", st, [&] { go(std::integral_constant<int, 0>{}); });
 }
 
 }  // namespace mm

@@ -60,7 +60,7 @@ def test_emulated_4096_16384_4096_sampled_bit_exact(mm, orc):
     assert np.array_equal(got, orc.split_product(a[rows], b[:, cols], 7, 8))
 
 
-@pytest.mark.parametrize("n", [4095, 8192])
+@pytest.mark.parametrize("n", [2047, 4095, 8192])
 def test_fp64_methods_full_size_sampled_rows(mm, orc, n):
     """Uniform entries at the sweep's largest and odd sizes: Kahan and the
     rounding-order naive sum are bit-exact on sampled rows; the FMA/MMA methods
