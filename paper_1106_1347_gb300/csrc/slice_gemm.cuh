@@ -79,25 +79,56 @@ __device__ __forceinline__ void raise_status(int *status, int code) {
     if (status) atomicOr(status, code);
 }
 
-// Exact signed 128-bit integer (hi, lo) rounded to the nearest double (ties to even).
-__device__ __forceinline__ double int128_to_double(int64_t hi, uint64_t lo) {
+// RN(W) * 2^E for the exact signed 128-bit integer W = (hi, lo), built from
+// integer operations only (the FP64 pipe of this part is too slow to spend per
+// output): W is rounded to a 53-bit significand, ties to even, with a sticky
+// bit for everything below; the scaling by 2^E is exact unless the result
+// leaves the normal range -- past the largest double it is +-inf, below the
+// smallest normal it is rounded once more to the subnormal grid (ties to
+// even), exactly as rounding to double and then scaling by 2^E does.
+__device__ __forceinline__ double int128_scaled_to_double(int64_t hi, uint64_t lo, int E) {
     const bool neg = hi < 0;
     uint64_t uh = (uint64_t)hi, ul = lo;
     if (neg) {
         ul = ~ul + 1;
         uh = ~uh + (ul == 0 ? 1 : 0);
     }
-    double r;
-    if (uh == 0) {
-        r = __ull2double_rn(ul);
+    if ((uh | ul) == 0) return 0.0;
+    const uint64_t sign = neg ? (1ull << 63) : 0ull;
+    // Normalise so the leading one sits at bit 127 of (h, l).
+    const int lz = uh ? __clzll((long long)uh) : 64 + __clzll((long long)ul);
+    uint64_t h, l;
+    if (lz >= 64) {
+        h = ul << (lz - 64);
+        l = 0;
+    } else if (lz > 0) {
+        h = (uh << lz) | (ul >> (64 - lz));
+        l = ul << lz;
     } else {
-        const int lz = __clzll((long long)uh);
-        const uint64_t top = lz ? ((uh << lz) | (ul >> (64 - lz))) : uh;
-        const uint64_t rest = ul << lz;
-        r = __ull2double_rn(top | (rest != 0 ? 1ull : 0ull));  // sticky bit below the rounding point
-        r = ldexp(r, 64 - lz);
+        h = uh;
+        l = ul;
     }
-    return neg ? -r : r;
+    // 53-bit significand, guard bit, sticky bit.
+    uint64_t m = h >> 11;
+    const bool guard = (h >> 10) & 1ull, sticky = (h & 0x3FFull) != 0 || l != 0;
+    int msb = 127 - lz;  // W's leading bit has weight 2^msb
+    if (guard && (sticky || (m & 1ull))) {
+        if (++m == (1ull << 53)) {
+            m >>= 1;
+            ++msb;
+        }
+    }
+    const int biased = msb + E + 1023;  // exponent field of RN(W) 2^E
+    if (biased >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+    if (biased >= 1)
+        return __longlong_as_double((long long)(sign | ((uint64_t)biased << 52) | (m & ((1ull << 52) - 1))));
+    // Subnormal: m 2^(msb - 52 + E) on the grid of 2^-1074, `shift` low bits dropped.
+    const int shift = 1 - biased;
+    if (shift > 53) return __longlong_as_double((long long)sign);
+    uint64_t q = m >> shift;
+    const uint64_t rem = m & ((1ull << shift) - 1), half = 1ull << (shift - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    return __longlong_as_double((long long)(sign | q));  // q = 2^52 carries into the exponent field
 }
 
 // Tile of CTA `id` in a tiles_m x tiles_n grid, in runs of 8 tile-rows so that
@@ -371,7 +402,7 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                         hi += (wl >> 63) + (lo2 < lo ? 1 : 0);
                         lo = lo2;
                         const int f = (col < p.M) ? p.fb[col] : 0;
-                        out[u] = ldexp(int128_to_double(hi, lo), e + f + 2 - beta * (s + 1));
+                        out[u] = int128_scaled_to_double(hi, lo, e + f + 2 - beta * (s + 1));
                     }
                     const int64_t col = n0 + 32 * h + k;
                     double *dst = crow + col;

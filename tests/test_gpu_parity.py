@@ -250,6 +250,24 @@ def test_strassen_tuned_default(mm, orc, gpu_name):
 
 # ---------------------------------------------------------------- emulated
 
+@pytest.mark.parametrize("kind,beta,s", [(0, 7, 8), (0, 7, 3), (1, 5, 6)])
+def test_emulated_subnormal_and_overflowing_results(mm, orc, kind, beta, s):
+    """The final rounding at the edges of the double range: results below
+    2^-1022 land on the subnormal grid (rounded once more, ties to even) and
+    results past the largest double are +-inf, bit for bit as the oracle's
+    RN(W) followed by ldexp."""
+    a, b = pair(130, 70, 90, "log", 40)
+    for sa, sb in ((-600, -460), (600, 390)):
+        a2, b2 = np.ldexp(a, sa), np.ldexp(b, sb)
+        ref = orc.split_product(a2, b2, beta, s)
+        if sa < 0:  # subnormal and normal results side by side
+            assert ((ref != 0) & (np.abs(ref) < 2.0 ** -1022)).sum() > 100 and (np.abs(ref) >= 2.0 ** -1022).sum() > 100
+        else:  # infinite and finite results side by side
+            assert np.isinf(ref).sum() > 100 and np.isfinite(ref).sum() > 100
+        got = host(mm.emulated(dev(a2), dev(b2), nslices=s, kind=kind))
+        assert np.array_equal(got, ref)
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 1), (5, 3, 7), (128, 32, 64), (129, 33, 65), (200, 333, 150),
                                    (256, 1100, 130)])
 @pytest.mark.parametrize("s", [8, 3])
