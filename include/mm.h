@@ -157,8 +157,9 @@ int mm_winograd_rowcol_scaled(int64_t N, int64_t P, int64_t M, const double *A, 
  *   cutoff  > 0: the smallest depth at which every padded dimension / 2^depth
  *                is <= cutoff, each dimension padded to a multiple of 2^depth;
  *   cutoff == -1: the depth mm_tune_strassen recorded for this shape bucket,
- *                else one level per doubling of max(N, P, M) above 1024 (at
- *                most 3); each dimension padded to a multiple of 2^depth.
+ *                else the paper's depth taken on the smallest dimension,
+ *                max(0, floor(log2 min(N, P, M)) - 4); each dimension padded
+ *                to a multiple of 2^depth.
  * Padding is virtual (out-of-range elements read as zero).  Every node of a
  * recursion level is processed by the same launch (breadth-first):
  *   - the operand sums (Plus/Minus) of one or two levels are formed in one
@@ -190,15 +191,16 @@ int mm_strassen_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64
 /*
  * Autotuner for the Strassen depth used by cutoff == -1 (not in the paper,
  * which fixes the depth by its padding rule).
- * mm_tune_strassen times the recursion at depths 0..3 (each dimension padded
- * to a multiple of 2^depth) on the given operands, writing C each time, and
- * records the fastest depth for (variant, floor(log2 max(N, P, M))); it
- * synchronises `stream`.  variant: 0 = StrassenNaiv, 1 = StrassenWinograd.
- * ws must hold mm_tune_strassen_workspace_bytes(N, P, M) bytes (depths whose
- * workspace does not fit are skipped).  The table persists with
- * mm_tune_save / mm_tune_load (text, one entry per line); if MM_TUNE_CACHE is
- * set, that file is loaded at first use.  mm_tune_load returns the number of
- * entries read.
+ * mm_tune_strassen times the recursion at every depth 0, 1, ... whose blocks
+ * stay at least 16 in every dimension (each dimension padded to a multiple of
+ * 2^depth) on the given operands, writing C each time, and records the
+ * fastest depth for (variant, floor(log2 max(N, P, M))); it synchronises
+ * `stream`.  variant: 0 = StrassenNaiv, 1 = StrassenWinograd.  ws must hold
+ * mm_tune_strassen_workspace_bytes(N, P, M) bytes (depths whose workspace does
+ * not fit are skipped).  The table (Strassen depths and the emulated choices
+ * below) persists with mm_tune_save / mm_tune_load (text, one entry per line);
+ * if MM_TUNE_CACHE is set, that file is loaded at first use.  mm_tune_load
+ * returns the number of entries read; mm_tune_clear empties the table.
  */
 size_t mm_tune_strassen_workspace_bytes(int64_t N, int64_t P, int64_t M);
 int mm_tune_strassen(int32_t variant, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
@@ -280,6 +282,41 @@ int mm_emulated_noalloc(int64_t N, int64_t P, int64_t M, const double *A, int64_
 size_t mm_emulated_noalloc_capacity(void);
 
 /*
+ * Autotuned FP64-accurate product (not in the paper).  For a requested tier
+ * the candidates are the two slice formats, each with the slice count the tier
+ * needs (mm_emulated_slices; a format that cannot reach the tier is skipped),
+ * times 0, 1 or 2 levels of Strassen-Winograd over the product (each level
+ * leaving blocks of at least 512).
+ *   mm_tune_emulated times every candidate that fits ws (the faster of two
+ *     runs after a warm-up, CUDA events on `stream`, which it synchronises) on
+ *     the given operands, writing C each time, and records the fastest for the
+ *     bucket (floor(log2 N), floor(log2 P), floor(log2 M), round(-log10 tier));
+ *     the chosen format, slice count, level count and time are written to the
+ *     optional outputs.  ws: mm_tune_emulated_workspace_bytes bytes.
+ *   mm_tune_emulated_choice (host only, no device work) reports the choice for
+ *     a shape and tier: the recorded one (returns 1) or, with none recorded,
+ *     the model's (returns 0): the format whose slice pairs cost less at the
+ *     nominal rates (an FP8-E4M3 pair at half a BF16 pair) and the level count
+ *     of mm_strassen_emulated's levels = -1.  Negative status for a tier <= 0
+ *     or one neither format reaches.
+ *   mm_emulated_auto computes C = A B with that choice (the direct product for
+ *     0 levels, else mm_strassen_emulated's variant 1); `used` (optional, 3
+ *     host int32) receives format, slice count and levels.  Its result meets
+ *     the tier like mm_emulated's; it is bit-identical to the mm_emulated /
+ *     mm_strassen_emulated call with the same choice.  Workspace:
+ *     mm_emulated_auto_workspace_bytes.  Errors as for mm_emulated.
+ */
+size_t mm_tune_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, double tier);
+int mm_tune_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                     double *C, int64_t ldc, double tier, void *ws, size_t ws_bytes, void *stream, int32_t *best_kind,
+                     int32_t *best_slices, int32_t *best_levels, double *best_ms);
+int mm_tune_emulated_choice(int64_t N, int64_t P, int64_t M, double tier, int32_t *kind, int32_t *slices,
+                            int32_t *levels);
+size_t mm_emulated_auto_workspace_bytes(int64_t N, int64_t P, int64_t M, double tier);
+int mm_emulated_auto(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                     double *C, int64_t ldc, double tier, void *ws, size_t ws_bytes, void *stream, int32_t *used);
+
+/*
  * Grouped FP64-accurate products (batching; no counterpart in the
  * paper): `count` independent products C_g = A_g B_g of uneven shapes, each
  * with the mm_emulated definition and one common slice count, in one launch
@@ -356,8 +393,9 @@ int mm_strassen_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64
  *     launch, replayed from a CUDA graph cached per stream, slice format and
  *     count when use_graphs != 0;
  *   - method 0: BF16 slices, the tier's count (mm_emulated_slices);
- *     method 2: per request the cheaper of BF16 and FP8-E4M3 slices for its
- *     tier (FP8 when the tier needs at most 8 FP8 slices and their pairs, at
+ *     method 2: per request the format and count of mm_tune_emulated_choice
+ *     for its shape and tier (the autotuner's entry when one is recorded,
+ *     else FP8 when the tier needs at most 8 FP8 slices and their pairs, at
  *     twice the BF16 rate, cost less -- e.g. 6 FP8 slices for 1e-6 against 5
  *     BF16 ones); method 1 runs one request at a time with mm_naive's FP64
  *     kernel (a baseline);
@@ -396,6 +434,10 @@ typedef struct {
     double busy_s; /* first submit -> last completion */
     double flops;  /* sum of 2NPM over completed requests */
     int64_t peak_arena_bytes;
+    /* From CUDA events recorded before each batch's first copy and after its
+     * last: device time covered by at least one batch, and by at least two
+     * batches at once (batches on different streams overlapping). */
+    double device_busy_ms, overlap_ms;
 } mm_server_stats_t;
 int mm_server_create(void *arena, size_t arena_bytes, int32_t max_batch, int32_t nstreams, int32_t use_graphs,
                      int32_t method, mm_server **out);

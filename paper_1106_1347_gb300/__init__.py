@@ -13,7 +13,7 @@ import ctypes
 
 from ._native import KernelStat, MMError, check, lib
 
-__all__ = ["naive", "naive_unrolled", "kahan", "winograd", "winograd_scaled", "winograd_rowcol_scaled", "strassen", "strassen_winograd", "strassen_emulated", "tune_strassen", "norm_inf",
+__all__ = ["naive", "naive_unrolled", "kahan", "winograd", "winograd_scaled", "winograd_rowcol_scaled", "strassen", "strassen_winograd", "strassen_emulated", "tune_strassen", "tune_emulated", "emulated_choice", "emulated_auto", "tune_save", "tune_load", "tune_clear", "norm_inf",
            "emulated", "emulated_host", "emulated_group", "emulated_noalloc", "emulated_slices", "probe_fp64_peak", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
            "SLICE_FP8E4M3"]
 
@@ -161,6 +161,59 @@ def tune_strassen(a, b, variant=0):
     check("mm_tune_strassen", lib().mm_tune_strassen(int(variant), *_gemm_args(a, b, c, n, p, m), _ptr(ws), need,
                                                      _stream(a.device), ctypes.byref(depth), ctypes.byref(ms)))
     return int(depth.value), float(ms.value)
+
+
+def tune_emulated(a, b, tier=1e-14):
+    """Times the emulated product's candidates (slice format x Strassen-Winograd
+    levels) for this shape and tier, records the fastest for the shape bucket
+    (used by emulated_auto and serving method 2) and returns
+    (format, slices, levels, ms)."""
+    a, b, c, n, p, m = _prep(a, b, None)
+    need = lib().mm_tune_emulated_workspace_bytes(n, p, m, float(tier))
+    ws = _ws(need, a.device)
+    k, s, lv, ms = ctypes.c_int32(-1), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+    check("mm_tune_emulated", lib().mm_tune_emulated(*_gemm_args(a, b, c, n, p, m), float(tier), _ptr(ws), need,
+                                                     _stream(a.device), ctypes.byref(k), ctypes.byref(s),
+                                                     ctypes.byref(lv), ctypes.byref(ms)))
+    return int(k.value), int(s.value), int(lv.value), float(ms.value)
+
+
+def emulated_choice(n, p, m, tier=1e-14):
+    """The (format, slices, levels) emulated_auto uses for this shape and tier,
+    and whether it comes from the tuned table (host only)."""
+    k, s, lv = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    rc = lib().mm_tune_emulated_choice(int(n), int(p), int(m), float(tier), ctypes.byref(k), ctypes.byref(s),
+                                       ctypes.byref(lv))
+    if rc < 0:
+        check("mm_tune_emulated_choice", rc)
+    return (int(k.value), int(s.value), int(lv.value)), rc == 1
+
+
+def emulated_auto(a, b, tier=1e-14, out=None, return_choice=False):
+    """FP64-accurate product with the autotuned (or modelled) format, slice
+    count and Strassen-Winograd levels for the tier (mm_emulated_auto)."""
+    a, b, c, n, p, m = _prep(a, b, out)
+    need = lib().mm_emulated_auto_workspace_bytes(n, p, m, float(tier))
+    ws = _ws(need, a.device)
+    used = (ctypes.c_int32 * 3)()
+    check("mm_emulated_auto", lib().mm_emulated_auto(*_gemm_args(a, b, c, n, p, m), float(tier), _ptr(ws), need,
+                                                     _stream(a.device), used))
+    return (c, (int(used[0]), int(used[1]), int(used[2]))) if return_choice else c
+
+
+def tune_save(path):
+    check("mm_tune_save", lib().mm_tune_save(str(path).encode()))
+
+
+def tune_load(path):
+    n = lib().mm_tune_load(str(path).encode())
+    if n < 0:
+        check("mm_tune_load", n)
+    return n
+
+
+def tune_clear():
+    check("mm_tune_clear", lib().mm_tune_clear())
 
 
 def norm_inf(a):

@@ -35,7 +35,7 @@ class Completion(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", i64), ("completed", i64), ("rejected", i64), ("batches", i64), ("graph_replays", i64),
                 ("p50_ms", dbl), ("p99_ms", dbl), ("mean_ms", dbl), ("max_ms", dbl), ("busy_s", dbl),
-                ("flops", dbl), ("peak_arena_bytes", i64)]
+                ("flops", dbl), ("peak_arena_bytes", i64), ("device_busy_ms", dbl), ("overlap_ms", dbl)]
 
 
 class KernelStat(ctypes.Structure):
@@ -82,6 +82,13 @@ SIGNATURES = {
     "mm_server_destroy": (ctypes.c_int, [vp]),
     "mm_tune_strassen_workspace_bytes": (sz, [i64, i64, i64]),
     "mm_tune_strassen": (ctypes.c_int, [i32] + GEMM + [vp, sz, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
+    "mm_tune_emulated_workspace_bytes": (sz, [i64, i64, i64, dbl]),
+    "mm_tune_emulated": (ctypes.c_int, GEMM + [dbl, vp, sz, vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                                ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
+    "mm_tune_emulated_choice": (ctypes.c_int, [i64, i64, i64, dbl, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                                ctypes.POINTER(i32)]),
+    "mm_emulated_auto_workspace_bytes": (sz, [i64, i64, i64, dbl]),
+    "mm_emulated_auto": (ctypes.c_int, GEMM + [dbl, vp, sz, vp, ctypes.POINTER(i32)]),
     "mm_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "mm_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "mm_tune_clear": (ctypes.c_int, []),

@@ -453,6 +453,39 @@ int mm_strassen_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64
     return run_strassen_emulated(variant, levels, N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st);
 }
 
+size_t mm_emulated_auto_workspace_bytes(int64_t N, int64_t P, int64_t M, double tier) {
+    int kind, s, levels;
+    if (N <= 0 || P <= 0 || M <= 0 || emulated_choice(N, P, M, tier, &kind, &s, &levels) < 0) return 0;
+    return levels == 0 ? emulated_ws_bytes(N, P, M, s, kind)
+                       : strassen_emulated_ws_bytes(1, levels, N, P, M, s, kind);
+}
+
+int mm_emulated_auto(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                     double *C, int64_t ldc, double tier, void *ws, size_t ws_bytes, void *stream, int32_t *used) {
+    const char *fn = "mm_emulated_auto";
+    int rc = check_gemm_args(fn, N, P, M, A, lda, B, ldb, C, ldc);
+    if (rc) return rc;
+    if (!(tier > 0.0)) return fail(MM_ERR_ARG, "%s: tier must be > 0", fn);
+    if (P > (int64_t(1) << 20)) return fail(MM_ERR_UNSUPPORTED, "%s: P > 2^20", fn);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N == 0 || M == 0) return MM_OK;
+    if (P == 0) return run_zero(N, M, C, ldc, st);
+    int kind, s, levels;
+    if (emulated_choice(N, P, M, tier, &kind, &s, &levels) < 0)
+        return fail(MM_ERR_UNSUPPORTED, "%s: tier %g needs more slices than either format holds", fn, tier);
+    const size_t need = levels == 0 ? emulated_ws_bytes(N, P, M, s, kind)
+                                    : strassen_emulated_ws_bytes(1, levels, N, P, M, s, kind);
+    if (ws_bytes < need || !ws)
+        return fail(MM_ERR_WORKSPACE, "%s: workspace %zu bytes < %zu required", fn, ws_bytes, need);
+    if (used) {
+        used[0] = kind;
+        used[1] = s;
+        used[2] = levels;
+    }
+    return levels == 0 ? run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st)
+                       : run_strassen_emulated(1, levels, N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st);
+}
+
 int mm_profile_enable(int on) {
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof_on = on != 0;

@@ -102,6 +102,10 @@ int run_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
 int strassen_plan(int variant, int64_t N, int64_t P, int64_t M, int32_t cutoff, int *depth, int64_t *Np,
                   int64_t *Pp, int64_t *Mp);
 bool tuned_strassen_depth(int variant, int64_t N, int64_t P, int64_t M, int *depth);
+// The emulated product's slice format, count and Strassen-Winograd levels for
+// a tier (tune.cu): the tuned entry of the shape bucket (returns 1), else the
+// model (returns 0); negative for an invalid or unreachable tier.
+int emulated_choice(int64_t N, int64_t P, int64_t M, double tier, int *kind, int *slices, int *levels);
 size_t strassen_ws_bytes(int variant, int depth, int64_t Np, int64_t Pp, int64_t Mp);
 int run_strassen(int variant, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
                  int64_t ldb, double *C, int64_t ldc, int depth, int64_t Np, int64_t Pp, int64_t Mp, void *ws,

@@ -39,6 +39,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -830,11 +831,19 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
     for (int k = 0; k < 5; ++k) begin[k] = (int64_t *)(image.data() + G.off_begin[k]);
     int64_t units[5] = {0, 0, 0, 0, 0};
     int *status = device_status_ptr();
+    // Table order = launch order: the persistent slice kernel deals tiles out
+    // round-robin in table order, so the problems with the longest inner
+    // dimension (the longest tiles) go first and the short ones fill the end,
+    // which evens out the CTAs' finishing times.  Each problem keeps its own
+    // data region; any order gives the same results.
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return probs[x].P > probs[y].P; });
     for (int i = 0; i < count; ++i) {
-        const mm_problem &q = probs[i];
+        const mm_problem &q = probs[order[i]];
         const Layout L = layout(q.N, q.P, q.M, s, kind);
         EmuProblem &e = tab[i];
-        char *w = data[i];
+        char *w = data[order[i]];
         unsigned long long *cm = (unsigned long long *)w;
         w += align_up((size_t)L.Mr * 8, 1024);
         int32_t *ea = (int32_t *)w;

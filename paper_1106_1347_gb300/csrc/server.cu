@@ -118,7 +118,7 @@ struct Slot {
 struct Batch {
     int slot;
     std::vector<Req *> reqs;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;  // timing events before the first copy and after the last
 };
 
 size_t operand_bytes(const mm_request &r) {
@@ -146,17 +146,19 @@ double request_ms(const Req &q) {
     return 1e3 * (bytes / 200e9 + 2.0 * r.N * r.P * r.M * pairs / rate);
 }
 
-// The slice format and count for a tier.  Method 2 takes FP8-E4M3 slices when
-// the tier allows them (at most 8) and their pairs, at twice the BF16 rate,
-// cost less than the BF16 pairs the tier needs.
-void choose_slices(int method, double tier, int *s, int *kind) {
+// The slice format and count for a request's tier.  Method 2 takes the
+// autotuner's choice for the request's shape bucket when one is recorded, else
+// FP8-E4M3 slices when the tier allows them (at most 8) and their pairs, at
+// twice the BF16 rate, cost less than the BF16 pairs the tier needs.  (Batches
+// run the direct product: a tuned Strassen level count is not used here.)
+void choose_slices(int method, const mm_request &r, int *s, int *kind) {
     *kind = MM_SLICE_BF16;
-    *s = mm::emulated_slices(MM_SLICE_BF16, 0, tier);
+    *s = mm::emulated_slices(MM_SLICE_BF16, 0, r.tier);
     if (method != 2) return;
-    const int s8 = mm::emulated_slices(MM_SLICE_FP8E4M3, 0, tier);
-    if (s8 > 0 && s8 * (s8 + 1) < 2 * (*s) * (*s + 1)) {
-        *s = s8;
-        *kind = MM_SLICE_FP8E4M3;
+    int k = 0, n = 0, levels = 0;
+    if (mm::emulated_choice(r.N, r.P, r.M, r.tier, &k, &n, &levels) >= 0) {
+        *kind = k;
+        *s = n;
     }
 }
 
@@ -181,7 +183,9 @@ struct mm_server {
     std::vector<Req *> admitted;
     std::vector<Batch> inflight;
 
+    cudaEvent_t t0 = nullptr;  // timing origin of the batches' device intervals
     std::mutex res_mu;
+    std::vector<std::pair<float, float>> intervals;  // each batch's [start, done] on the device, ms after t0
     std::deque<mm_completion> done;
     std::vector<double> latencies;
     int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, graph_replays = 0;
@@ -233,10 +237,17 @@ struct mm_server {
             const Clock::time_point now = Clock::now();
             const int st = (e == cudaSuccess) ? MM_OK : MM_ERR_CUDA;
             if (e != cudaSuccess) set_fatal(mm::cuda_fail(e, "server: batch completion"));
+            float ts = 0.f, te = 0.f;
+            if (e == cudaSuccess && cudaEventElapsedTime(&ts, t0, b.start) == cudaSuccess &&
+                cudaEventElapsedTime(&te, t0, b.done) == cudaSuccess) {
+                std::lock_guard<std::mutex> g(res_mu);
+                intervals.emplace_back(ts, te);
+            }
             for (Req *q : b.reqs) {
                 arena.release(q->block, q->block_bytes);
                 finish(q, st, now);
             }
+            cudaEventDestroy(b.start);
             cudaEventDestroy(b.done);
             slots[b.slot].busy = false;
             inflight.erase(inflight.begin() + i);
@@ -284,9 +295,19 @@ struct mm_server {
         }
         auto give_back = [&](int rc) {
             cudaStreamSynchronize(st);  // nothing of this batch may still touch its memory
+            if (b.start) cudaEventDestroy(b.start);
+            if (b.done) cudaEventDestroy(b.done);
             return rc;
         };
         const Clock::time_point now = Clock::now();
+        {
+            cudaError_t e = cudaEventCreate(&b.start);
+            if (e == cudaSuccess) e = cudaEventRecord(b.start, st);
+            if (e != cudaSuccess) {
+                if (b.start) cudaEventDestroy(b.start);
+                return mm::cuda_fail(e, "server: batch start event");
+            }
+        }
         for (Req *q : reqs) {
             q->launched = now;
             const mm_request &r = q->r;
@@ -347,7 +368,7 @@ struct mm_server {
             cudaError_t e = cudaMemcpy2DAsync(r.C, r.ldc * 8, q->dC, r.M * 8, r.M * 8, r.N, cudaMemcpyDeviceToHost, st);
             if (e != cudaSuccess) return give_back(mm::cuda_fail(e, "server: device-to-host copy"));
         }
-        cudaError_t e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+        cudaError_t e = cudaEventCreate(&b.done);
         if (e == cudaSuccess) e = cudaEventRecord(b.done, st);
         if (e != cudaSuccess) return give_back(mm::cuda_fail(e, "server: completion event"));
         b.reqs = reqs;
@@ -470,6 +491,19 @@ int mm_server_create(void *arena, size_t arena_bytes, int32_t max_batch, int32_t
         sl.table_dev = (char *)arena + (size_t)k * table_cap;
         sl.table_cap = table_cap;
     }
+    {
+        cudaError_t e = cudaEventCreate(&s->t0);
+        if (e == cudaSuccess) e = cudaEventRecord(s->t0, s->slots[0].stream);
+        if (e != cudaSuccess) {
+            for (Slot &sl : s->slots) {
+                if (sl.stream) cudaStreamDestroy(sl.stream);
+                if (sl.staging) cudaFreeHost(sl.staging);
+            }
+            if (s->t0) cudaEventDestroy(s->t0);
+            delete s;
+            return mm::cuda_fail(e, "mm_server_create: timing event");
+        }
+    }
     s->arena.init((char *)arena + table_cap * ns, arena_bytes - table_cap * ns);
     s->worker = std::thread([s] { s->run(); });
     *out = s;
@@ -489,7 +523,7 @@ int mm_server_submit(mm_server *s, const mm_request *req) {
     Req *q = new Req();
     q->r = r;
     q->arrival = Clock::now();
-    if (s->method != 1) choose_slices(s->method, r.tier, &q->s, &q->kind);
+    if (s->method != 1) choose_slices(s->method, r, &q->s, &q->kind);
     {
         std::lock_guard<std::mutex> g(s->res_mu);
         ++s->submitted;
@@ -559,6 +593,23 @@ int mm_server_stats(mm_server *s, mm_server_stats_t *out) {
         st.mean_ms = sum / (double)lat.size();
         st.busy_s = ms_between(s->first_arrival, s->last_done) / 1e3;
     }
+    // Device time covered by at least one batch, and by at least two at once
+    // (batches on different streams overlapping), from the batches' events.
+    std::vector<std::pair<float, int>> ends;
+    for (const auto &iv : s->intervals) {
+        ends.emplace_back(iv.first, +1);
+        ends.emplace_back(iv.second, -1);
+    }
+    std::sort(ends.begin(), ends.end());  // at equal times an end (-1) sorts before a start (+1)
+    int active = 0;
+    for (size_t i = 0; i < ends.size(); ++i) {
+        if (i > 0) {
+            const double dt = (double)ends[i].first - (double)ends[i - 1].first;
+            if (active >= 1) st.device_busy_ms += dt;
+            if (active >= 2) st.overlap_ms += dt;
+        }
+        active += ends[i].second;
+    }
     *out = st;
     return MM_OK;
 }
@@ -582,6 +633,7 @@ int mm_server_destroy(mm_server *s) {
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.staging) cudaFreeHost(sl.staging);
     }
+    if (s->t0) cudaEventDestroy(s->t0);
     int fatal;
     {
         std::lock_guard<std::mutex> g(s->res_mu);

@@ -584,8 +584,11 @@ int strassen_plan(int variant, int64_t N, int64_t P, int64_t M, int32_t cutoff, 
         if (cutoff > 0) {
             while (ceil_div(X, (int64_t)1 << d) > cutoff) ++d;
         } else if (!tuned_strassen_depth(variant, N, P, M, &d)) {
-            // untuned default: one level per doubling above 1024, at most 3
-            for (int64_t t = X; t >= 2048 && d < 3; t >>= 1) ++d;
+            // untuned default: the paper's depth floor(log2) - 4, taken on the
+            // smallest dimension (blocks of 16 to 31 there), fastest on GB300
+            int lg = -1;
+            for (int64_t t = std::min(N, std::min(P, M)); t > 0; t >>= 1) ++lg;
+            d = std::max(0, lg - 4);
         }
         const int64_t q = (int64_t)1 << d;
         *depth = d;

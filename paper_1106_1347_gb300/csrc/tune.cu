@@ -1,43 +1,84 @@
-// Autotuner: the Strassen recursion depth per (variant, shape bucket), chosen
-// by timing depths 0..3 on the device, kept in an in-library table that
-// mm_strassen / mm_strassen_winograd consult for cutoff == -1, and persisted
-// as a small text file (one "strassen <variant> <bucket> <depth>" line per
-// entry; MM_TUNE_CACHE names a file loaded at first use).  The slice count of
-// the emulated product needs no search: it follows from the requested tier.
+// Autotuner (not in the paper, which fixes its choices by rule):
+//   - the Strassen recursion depth per (variant, shape bucket), chosen by
+//     timing every depth whose blocks stay at least 16 wide, consulted by
+//     mm_strassen / mm_strassen_winograd for cutoff == -1;
+//   - for the FP64-accurate emulated product, per (shape bucket, tier): the
+//     slice format (BF16 or FP8-E4M3, each with the slice count the tier
+//     needs) and the number of Strassen-Winograd levels over it, chosen by
+//     timing every candidate; consulted by mm_emulated_auto and by the
+//     serving loop's method 2.
+// Both live in one in-library table, persisted as a small text file, one entry
+// per line:
+//   strassen <variant> <log2 max dim> <depth>
+//   emulated <log2 N> <log2 P> <log2 M> <tier decade> <format> <slices> <levels>
+// MM_TUNE_CACHE names a file loaded at first use.  Without an entry the
+// choices fall back to models: the paper's depth floor(log2 X) - 4 for
+// Strassen; for the emulated product the format whose slice pairs cost less at
+// the nominal rates (an FP8 pair costs half a BF16 one) and the measured
+// level crossovers of strassen_emulated_levels.
+#include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
+#include <string>
+#include <tuple>
 #include <utility>
 
 #include "common.cuh"
 
 namespace {
 
+struct EmuChoice {
+    int kind, slices, levels;
+    double ms;
+};
+using EmuKey = std::tuple<int, int, int, int>;  // log2 N, log2 P, log2 M, tier decade
+
 std::mutex g_mu;
 std::map<std::pair<int, int>, int> g_depth;  // (variant, bucket) -> depth
+std::map<EmuKey, EmuChoice> g_emu;
 bool g_env_loaded = false;
 
-int bucket_of(int64_t N, int64_t P, int64_t M) {
-    int64_t X = std::max(N, std::max(P, M));
+int lg2(int64_t x) {
     int b = 0;
-    while (X > 1) {
-        X >>= 1;
+    while (x > 1) {
+        x >>= 1;
         ++b;
     }
-    return b;  // floor(log2 max dim)
+    return b;
+}
+
+int bucket_of(int64_t N, int64_t P, int64_t M) { return lg2(std::max(N, std::max(P, M))); }
+
+int tier_decade(double tier) { return (int)lround(-log10(tier)); }
+
+EmuKey emu_key(int64_t N, int64_t P, int64_t M, double tier) {
+    return EmuKey{lg2(N), lg2(P), lg2(M), tier_decade(tier)};
 }
 
 int load_file(const char *path) {
     FILE *f = fopen(path, "r");
     if (!f) return mm::fail(MM_ERR_ARG, "mm_tune_load: cannot open %s", path);
-    char kind[32];
-    int variant, bucket, depth, n = 0;
-    while (fscanf(f, "%31s %d %d %d", kind, &variant, &bucket, &depth) == 4) {
-        if (std::string(kind) != "strassen" || variant < 0 || variant > 1 || depth < 0 || depth > 10) continue;
-        g_depth[{variant, bucket}] = depth;
-        ++n;
+    char line[256];
+    int n = 0;
+    while (fgets(line, sizeof line, f)) {
+        char kind[32];
+        int a[7];
+        if (sscanf(line, "%31s", kind) != 1) continue;
+        if (std::string(kind) == "strassen" && sscanf(line, "%*s %d %d %d", &a[0], &a[1], &a[2]) == 3) {
+            if (a[0] < 0 || a[0] > 1 || a[2] < 0 || a[2] > 16) continue;
+            g_depth[{a[0], a[1]}] = a[2];
+            ++n;
+        } else if (std::string(kind) == "emulated" &&
+                   sscanf(line, "%*s %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6]) == 7) {
+            if ((a[4] != MM_SLICE_BF16 && a[4] != MM_SLICE_FP8E4M3) || a[5] < 1 || a[5] > 8 || a[6] < 0 || a[6] > 4)
+                continue;
+            g_emu[EmuKey{a[0], a[1], a[2], a[3]}] = EmuChoice{a[4], a[5], a[6], 0.0};
+            ++n;
+        }
     }
     fclose(f);
     return n;
@@ -48,6 +89,43 @@ void load_env_once() {
     g_env_loaded = true;
     const char *p = getenv("MM_TUNE_CACHE");
     if (p && *p) (void)load_file(p);
+}
+
+// Deepest Strassen depth the tuner tries: blocks of at least 16 in every dimension.
+int max_tuned_depth(int64_t N, int64_t P, int64_t M) {
+    const int64_t lo = std::min(N, std::min(P, M));
+    int d = 0;
+    while (d < 16 && (lo >> (d + 1)) >= 16) ++d;
+    return d;
+}
+
+// The model's emulated choice for a tier (no table entry).
+int model_emulated(int64_t N, int64_t P, int64_t M, double tier, int *kind, int *slices, int *levels) {
+    const int sb = mm::emulated_slices(MM_SLICE_BF16, 0, tier);
+    if (sb < 0) return sb;
+    const int s8 = mm::emulated_slices(MM_SLICE_FP8E4M3, 0, tier);
+    *kind = MM_SLICE_BF16;
+    *slices = sb;
+    if (s8 > 0 && s8 * (s8 + 1) < 2 * sb * (sb + 1)) {
+        *kind = MM_SLICE_FP8E4M3;
+        *slices = s8;
+    }
+    *levels = mm::strassen_emulated_levels(-1, N, P, M);
+    return MM_OK;
+}
+
+// Candidate levels of Strassen-Winograd over the emulated product: each level
+// must leave blocks of at least 512 in every dimension.
+int max_emulated_levels(int64_t N, int64_t P, int64_t M) {
+    const int64_t lo = std::min(N, std::min(P, M));
+    int L = 0;
+    while (L < 2 && (lo >> (L + 1)) >= 512) ++L;
+    return L;
+}
+
+size_t emulated_candidate_bytes(int64_t N, int64_t P, int64_t M, int kind, int s, int levels) {
+    return levels == 0 ? mm::emulated_ws_bytes(N, P, M, s, kind)
+                       : mm::strassen_emulated_ws_bytes(1, levels, N, P, M, s, kind);
 }
 
 }  // namespace
@@ -63,6 +141,26 @@ bool tuned_strassen_depth(int variant, int64_t N, int64_t P, int64_t M, int *dep
     return true;
 }
 
+// The emulated product's format, slice count and Strassen levels for a tier:
+// the tuned entry of the shape bucket, else the model.  Returns 1 (tuned),
+// 0 (model) or a negative status for an invalid tier.
+int emulated_choice(int64_t N, int64_t P, int64_t M, double tier, int *kind, int *slices, int *levels) {
+    if (!(tier > 0.0)) return MM_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        load_env_once();
+        auto it = g_emu.find(emu_key(N, P, M, tier));
+        if (it != g_emu.end()) {
+            *kind = it->second.kind;
+            *slices = it->second.slices;
+            *levels = it->second.levels;
+            return 1;
+        }
+    }
+    const int rc = model_emulated(N, P, M, tier, kind, slices, levels);
+    return rc < 0 ? rc : 0;
+}
+
 }  // namespace mm
 
 extern "C" {
@@ -70,7 +168,7 @@ extern "C" {
 size_t mm_tune_strassen_workspace_bytes(int64_t N, int64_t P, int64_t M) {
     if (N <= 0 || P <= 0 || M <= 0) return 0;
     size_t most = 0;
-    for (int d = 1; d <= 3; ++d) {
+    for (int d = 1; d <= max_tuned_depth(N, P, M); ++d) {
         const int64_t q = (int64_t)1 << d;
         for (int v = 0; v < 2; ++v)
             most = std::max(most, mm::strassen_ws_bytes(v, d, mm::ceil_div(N, q) * q, mm::ceil_div(P, q) * q,
@@ -92,11 +190,10 @@ int mm_tune_strassen(int32_t variant, int64_t N, int64_t P, int64_t M, const dou
     cudaEventCreate(&e1);
     int best = -1;
     float best_t = 0.f;
-    for (int d = 0; d <= 3; ++d) {
+    for (int d = 0; d <= max_tuned_depth(N, P, M); ++d) {
         const int64_t q = (int64_t)1 << d;
         const int64_t Np = mm::ceil_div(N, q) * q, Pp = mm::ceil_div(P, q) * q, Mp = mm::ceil_div(M, q) * q;
-        if (d > 0 && (N < 2 * q || P < 2 * q || M < 2 * q)) break;  // blocks smaller than 2 rows: stop
-        if (mm::strassen_ws_bytes(variant, d, Np, Pp, Mp) > ws_bytes) break;
+        if (mm::strassen_ws_bytes(variant, d, Np, Pp, Mp) > ws_bytes) continue;
         float t = 0.f;
         for (int rep = 0; rep < 2 && rc == MM_OK; ++rep) {  // the first run warms up
             cudaEventRecord(e0, st);
@@ -125,12 +222,87 @@ int mm_tune_strassen(int32_t variant, int64_t N, int64_t P, int64_t M, const dou
     return MM_OK;
 }
 
+size_t mm_tune_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, double tier) {
+    if (N <= 0 || P <= 0 || M <= 0 || !(tier > 0.0)) return 0;
+    size_t most = 0;
+    for (int kind = MM_SLICE_BF16; kind <= MM_SLICE_FP8E4M3; ++kind) {
+        const int s = mm::emulated_slices(kind, 0, tier);
+        if (s < 0) continue;
+        for (int L = 0; L <= max_emulated_levels(N, P, M); ++L)
+            most = std::max(most, emulated_candidate_bytes(N, P, M, kind, s, L));
+    }
+    return most;
+}
+
+int mm_tune_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                     double *C, int64_t ldc, double tier, void *ws, size_t ws_bytes, void *stream, int32_t *best_kind,
+                     int32_t *best_slices, int32_t *best_levels, double *best_ms) {
+    int rc = mm::check_gemm_args("mm_tune_emulated", N, P, M, A, lda, B, ldb, C, ldc);
+    if (rc) return rc;
+    if (N == 0 || P == 0 || M == 0) return mm::fail(MM_ERR_ARG, "mm_tune_emulated: empty product");
+    if (!(tier > 0.0)) return mm::fail(MM_ERR_ARG, "mm_tune_emulated: tier must be > 0");
+    if (P > (int64_t(1) << 20)) return mm::fail(MM_ERR_UNSUPPORTED, "mm_tune_emulated: P > 2^20");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    EmuChoice best{-1, 0, 0, 0.0};
+    for (int kind = MM_SLICE_BF16; kind <= MM_SLICE_FP8E4M3 && rc == MM_OK; ++kind) {
+        const int s = mm::emulated_slices(kind, 0, tier);
+        if (s < 0) continue;  // the tier needs more slices than this format holds
+        for (int L = 0; L <= max_emulated_levels(N, P, M) && rc == MM_OK; ++L) {
+            if (emulated_candidate_bytes(N, P, M, kind, s, L) > ws_bytes) continue;
+            float t = 0.f, tmin = 0.f;
+            for (int rep = 0; rep < 3 && rc == MM_OK; ++rep) {  // one warm-up, the faster of two timed runs
+                cudaEventRecord(e0, st);
+                rc = L == 0 ? mm::run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st)
+                            : mm::run_strassen_emulated(1, L, N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st);
+                cudaEventRecord(e1, st);
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) rc = mm::cuda_fail(e, "mm_tune_emulated");
+                if (rc == MM_OK) cudaEventElapsedTime(&t, e0, e1);
+                if (rep == 1 || (rep == 2 && t < tmin)) tmin = t;
+            }
+            if (rc == MM_OK && (best.kind < 0 || tmin < best.ms)) best = EmuChoice{kind, s, L, (double)tmin};
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (best.kind < 0) return mm::fail(MM_ERR_WORKSPACE, "mm_tune_emulated: no candidate fits %zu bytes", ws_bytes);
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        load_env_once();
+        g_emu[emu_key(N, P, M, tier)] = best;
+    }
+    if (best_kind) *best_kind = best.kind;
+    if (best_slices) *best_slices = best.slices;
+    if (best_levels) *best_levels = best.levels;
+    if (best_ms) *best_ms = best.ms;
+    return MM_OK;
+}
+
+int mm_tune_emulated_choice(int64_t N, int64_t P, int64_t M, double tier, int32_t *kind, int32_t *slices,
+                            int32_t *levels) {
+    if (N < 0 || P < 0 || M < 0) return mm::fail(MM_ERR_ARG, "mm_tune_emulated_choice: negative size");
+    int k = 0, s = 0, l = 0;
+    const int rc = mm::emulated_choice(N, P, M, tier, &k, &s, &l);
+    if (rc < 0) return mm::fail(rc, "mm_tune_emulated_choice: tier must be > 0 and within the formats' reach");
+    if (kind) *kind = k;
+    if (slices) *slices = s;
+    if (levels) *levels = l;
+    return rc;
+}
+
 int mm_tune_save(const char *path) {
     if (!path) return mm::fail(MM_ERR_ARG, "mm_tune_save: NULL path");
     std::lock_guard<std::mutex> g(g_mu);
     FILE *f = fopen(path, "w");
     if (!f) return mm::fail(MM_ERR_ARG, "mm_tune_save: cannot open %s", path);
     for (auto &kv : g_depth) fprintf(f, "strassen %d %d %d\n", kv.first.first, kv.first.second, kv.second);
+    for (auto &kv : g_emu)
+        fprintf(f, "emulated %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                std::get<2>(kv.first), std::get<3>(kv.first), kv.second.kind, kv.second.slices, kv.second.levels);
     fclose(f);
     return MM_OK;
 }
@@ -145,6 +317,7 @@ int mm_tune_load(const char *path) {
 int mm_tune_clear(void) {
     std::lock_guard<std::mutex> g(g_mu);
     g_depth.clear();
+    g_emu.clear();
     g_env_loaded = true;
     return MM_OK;
 }

@@ -157,3 +157,24 @@ def test_graph_replay_across_batch_sizes(srv):
             for a, b, c in cases:
                 assert np.array_equal(c.numpy(), mm.emulated(a.cuda(), b.cuda(), tier=1e-14).cpu().numpy())
         assert s.stats()["graph_replays"] >= 1
+
+
+def test_batches_on_different_streams_overlap_on_the_device(srv):
+    """Each batch records a CUDA event before its first copy and after its last;
+    the server's device intervals show batches on different streams running
+    at the same time (their copies and products overlap), and none with one
+    stream."""
+    mm, serving = srv
+    cases = [_case(200 + i, 1536, 1536, 1536) for i in range(4)]
+    for nstreams in (1, 2):
+        with serving.Server(2 << 30, max_batch=1, nstreams=nstreams, use_graphs=False) as s:
+            for i, (a, b, c) in enumerate(cases):
+                s.submit(a, b, c, tier=1e-14, tag=i)
+            assert s.wait(120) == 0
+            st = s.stats()
+        assert st["completed"] == 4 and st["batches"] == 4
+        assert st["device_busy_ms"] > 0
+        if nstreams == 1:
+            assert st["overlap_ms"] == 0.0
+        else:
+            assert st["overlap_ms"] > 0.2 * st["device_busy_ms"], st
