@@ -158,8 +158,10 @@ int mm_winograd_rowcol_scaled(int64_t N, int64_t P, int64_t M, const double *A, 
  *                is <= cutoff, each dimension padded to a multiple of 2^depth;
  *   cutoff == -1: the depth mm_tune_strassen recorded for this shape bucket,
  *                else the paper's depth taken on the smallest dimension,
- *                max(0, floor(log2 min(N, P, M)) - 4); each dimension padded
- *                to a multiple of 2^depth.
+ *                max(0, floor(log2 min(N, P, M)) - 4), at most 6 for
+ *                mm_strassen_winograd (its normwise error about doubles per
+ *                level: 3e-15 at 6 levels, 3.5e-14 at 9 on uniform 8192^3);
+ *                each dimension padded to a multiple of 2^depth.
  * Padding is virtual (out-of-range elements read as zero).  Every node of a
  * recursion level is processed by the same launch (breadth-first):
  *   - the operand sums (Plus/Minus) of one or two levels are formed in one
@@ -192,9 +194,10 @@ int mm_strassen_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64
  * Autotuner for the Strassen depth used by cutoff == -1 (not in the paper,
  * which fixes the depth by its padding rule).
  * mm_tune_strassen times the recursion at every depth 0, 1, ... whose blocks
- * stay at least 16 in every dimension (each dimension padded to a multiple of
- * 2^depth) on the given operands, writing C each time, and records the
- * fastest depth for (variant, floor(log2 max(N, P, M))); it synchronises
+ * stay at least 16 in every dimension (at most 6 for StrassenWinograd; each
+ * dimension padded to a multiple of 2^depth) on the given operands, writing C
+ * each time, and records the fastest depth for (variant,
+ * floor(log2 max(N, P, M))); it synchronises
  * `stream`.  variant: 0 = StrassenNaiv, 1 = StrassenWinograd.  ws must hold
  * mm_tune_strassen_workspace_bytes(N, P, M) bytes (depths whose workspace does
  * not fit are skipped).  The table (Strassen depths and the emulated choices
@@ -225,12 +228,14 @@ int mm_tune_clear(void);
  *   kind:     MM_SLICE_BF16 (beta = 7, digits |d| <= 64, kind::f16 MMA) or
  *             MM_SLICE_FP8E4M3 (beta = 5, digits |d| <= 16, kind::f8f6f4 MMA at
  *             twice the rate per pair); anything else returns MM_ERR_ARG;
- *   nslices:  1..8, or 0 to choose from `tier`: s = ceil((log2(1/tier) + 9) / beta);
+ *   nslices:  1..8 (BF16) or 1..10 (FP8-E4M3), or 0 to choose from `tier`:
+ *             s = ceil((log2(1/tier) + 9) / beta);
  *   tier:     target ||C - AB||_inf / (||A||_inf ||B||_inf) when nslices == 0
  *             (<= 1e-14 selects 8 BF16 slices; FP8 reaches tiers down to about
- *             1e-9 -- a tier that needs more than 8 slices returns
- *             MM_ERR_UNSUPPORTED, because the kernel keeps one 64-column TMEM
- *             accumulator per diagonal and TMEM holds 8).
+ *             1e-12 with 10 slices -- a tier that needs more slices than the
+ *             format holds returns MM_ERR_UNSUPPORTED: the kernel keeps one TMEM
+ *             accumulator per diagonal, 64 columns wide up to 8 slices, 32
+ *             wide for 9 and 10, and TMEM holds 512 columns).
  * Requires N, M >= 1 and P <= 2^20 (larger P returns MM_ERR_UNSUPPORTED).
  */
 size_t mm_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t kind, int32_t nslices, double tier);
@@ -395,10 +400,10 @@ int mm_strassen_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64
  *   - method 0: BF16 slices, the tier's count (mm_emulated_slices);
  *     method 2: per request the format and count of mm_tune_emulated_choice
  *     for its shape and tier (the autotuner's entry when one is recorded,
- *     else FP8 when the tier needs at most 8 FP8 slices and their pairs, at
- *     twice the BF16 rate, cost less -- e.g. 6 FP8 slices for 1e-6 against 5
- *     BF16 ones); method 1 runs one request at a time with mm_naive's FP64
- *     kernel (a baseline);
+ *     else the format whose slice pairs cost less, an FP8 pair at half a
+ *     BF16 pair (three quarters past 8 FP8 slices) -- e.g. 6 FP8 slices for
+ *     1e-6 against 5 BF16 ones); method 1 runs one request at a time with
+ *     mm_naive's FP64 kernel (a baseline);
  *   - per request: host-to-device copies of A and B, the product, and the copy
  *     of C back into the caller's host buffer, whose completion ends the
  *     request's latency (measured from mm_server_submit).

@@ -314,11 +314,12 @@ size_t mm_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t kind
 // the count or the tier is invalid or the tier needs more than 8 slices.
 static int slices_or_fail(const char *fn, int32_t kind, int32_t nslices, double tier) {
     if (kind != MM_SLICE_BF16 && kind != MM_SLICE_FP8E4M3) return fail(MM_ERR_ARG, "%s: unknown slice kind %d", fn, kind);
-    if (nslices < 0 || nslices > 8) return fail(MM_ERR_ARG, "%s: nslices must be 0..8", fn);
+    const int most = kind == MM_SLICE_FP8E4M3 ? 10 : 8;
+    if (nslices < 0 || nslices > most) return fail(MM_ERR_ARG, "%s: nslices must be 0..%d for this format", fn, most);
     if (nslices == 0 && !(tier > 0.0)) return fail(MM_ERR_ARG, "%s: tier must be > 0 when nslices == 0", fn);
     const int s = emulated_slices(kind, nslices, tier);
     if (s == MM_ERR_UNSUPPORTED)
-        return fail(MM_ERR_UNSUPPORTED, "%s: tier %g needs more than 8 %s slices", fn, tier,
+        return fail(MM_ERR_UNSUPPORTED, "%s: tier %g needs more than %d %s slices", fn, tier, most,
                     kind == MM_SLICE_FP8E4M3 ? "FP8-E4M3" : "BF16");
     if (s <= 0) return fail(MM_ERR_ARG, "%s: invalid slice request", fn);
     return s;

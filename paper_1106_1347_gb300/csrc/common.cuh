@@ -102,6 +102,11 @@ int run_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
 int strassen_plan(int variant, int64_t N, int64_t P, int64_t M, int32_t cutoff, int *depth, int64_t *Np,
                   int64_t *Pp, int64_t *Mp);
 bool tuned_strassen_depth(int variant, int64_t N, int64_t P, int64_t M, int *depth);
+// Deepest Strassen-Winograd recursion chosen without being asked for by
+// depth (cutoff -1: the default and the tuner): its normwise error about
+// doubles per level on uniform inputs (measured 3.0e-15 at 6 levels and
+// 3.5e-14 at 9, 8192^3), so 6 levels keep a margin under 1e-14.
+constexpr int kWinogradSafeDepth = 6;
 // The emulated product's slice format, count and Strassen-Winograd levels for
 // a tier (tune.cu): the tuned entry of the shape bucket (returns 1), else the
 // model (returns 0); negative for an invalid or unreachable tier.
@@ -128,6 +133,16 @@ size_t emulated_host_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind);
 int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
                       double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st);
 
+// An operand formed while the emulated product splits it: the operand pointer
+// x0 and up to three more views x1..x3 of the same shape and leading
+// dimension, summed in the nesting `shape` (1: x0; 2: x0 o0 x1; 3: x0 o0 (x1
+// o1 x2); 4: (x0 o0 x1) o1 x2; 5: x0 o0 (x1 o1 (x2 o2 x3)); 6: x0 o0 ((x1 o1
+// x2) o2 x3)), o = +1 or -1, each node rounded.  shape 0 means x0 alone.
+struct OpTerms {
+    const double *x[3];  // x1, x2, x3
+    int8_t shape, op[3];
+};
+
 // Pieces of a grouped emulated launch, for runtimes that place the table part
 // (problem table, header, prefix arrays) and the data part (column maxima,
 // exponents, slices) themselves and replay the kernels from CUDA graphs.
@@ -136,16 +151,21 @@ struct GroupLaunch {
     const int64_t *begin[5];  // device prefix arrays
     int64_t grid[5];          // CTAs per kernel (grid-stride kernels: any size works)
     int s, kind;              // slice count and format
+    bool expr;                // some operand is a sum of views (split kernels evaluate it)
 };
 size_t group_table_bytes(int count);
 size_t problem_data_bytes(const mm_problem &q, int s, int kind = MM_SLICE_BF16);
 size_t group_data_bytes(const mm_problem *probs, int count, int s, int kind = MM_SLICE_BF16);
+// ta / tb (optional, one entry per problem): each problem's A (B) is then the
+// sum of its views described there, with probs[i].A (.B) as x0.
 int group_build(const mm_problem *probs, int count, int capacity, int s, void *table_dev, char *const *data,
-                std::vector<unsigned char> &image, GroupLaunch &gl, int kind = MM_SLICE_BF16);
+                std::vector<unsigned char> &image, GroupLaunch &gl, int kind = MM_SLICE_BF16,
+                const OpTerms *ta = nullptr, const OpTerms *tb = nullptr);
 int group_kernels(const GroupLaunch &gl, cudaStream_t st);
 int64_t group_grid_cap(int kernel);  // fixed grid of grouped kernel `kernel` (0..4)
 void prof_suspend(bool on);  // skip kernel timing while a stream is being captured
-int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void *ws, cudaStream_t st);
+int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void *ws, cudaStream_t st,
+                       const OpTerms *ta = nullptr, const OpTerms *tb = nullptr);
 // Strassen (variant 0) / Strassen-Winograd (1) levels over the emulated product.
 int strassen_emulated_levels(int levels, int64_t N, int64_t P, int64_t M);  // resolves levels == -1
 size_t strassen_emulated_ws_bytes(int variant, int levels, int64_t N, int64_t P, int64_t M, int s, int kind);
@@ -288,6 +308,16 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+// 32 lanes x 16 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
 }

@@ -133,7 +133,8 @@ __device__ __forceinline__ int peel_digit(I &x) {
 // vector store at dst0 + (s-1-t) * stride (dst0: slice 0 at this row and
 // column).  With more than LO = floor(28 / beta) slices, V = hi 2^(LO beta) +
 // lo is split first: the LO low digits come from lo and the rest from hi +
-// the carry lo leaves, all in 32-bit arithmetic (|V| < 2^55, so |hi| < 2^27);
+// the carry lo leaves, all in 32-bit arithmetic (|V| < 2^(beta s - 1) <= 2^55,
+// so |hi| < 2^27);
 // the digits are the same as those of V itself.  Every index is a
 // compile-time constant, so nothing leaves registers.
 template <int KIND>
@@ -156,7 +157,7 @@ __device__ __forceinline__ void store_digits8(int64_t (&V)[8], int s, unsigned c
 #pragma unroll
         for (int u = 0; u < 8; ++u) hi[u] += lo[u];  // the carry, 0 or 1
 #pragma unroll
-        for (int t = LO; t < 8; ++t) {
+        for (int t = LO; t < fmt_max_slices(KIND); ++t) {
             if (t < s) {
                 int d[8];
 #pragma unroll
@@ -167,7 +168,7 @@ __device__ __forceinline__ void store_digits8(int64_t (&V)[8], int s, unsigned c
         return;
     }
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
+    for (int t = 0; t < fmt_max_slices(KIND); ++t) {
         if (t < s) {
             int d[8];
 #pragma unroll
@@ -193,6 +194,71 @@ __device__ __forceinline__ void load8(const double *__restrict__ a, int64_t c, i
     }
 }
 
+// v := v o w (w_left: v := w o v), element by element, rounded.
+__device__ __forceinline__ void fold8(double (&v)[8], int8_t o, const double (&w)[8], bool w_left) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = w_left ? plus_minus(w[u], o, v[u]) : plus_minus(v[u], o, w[u]);
+}
+
+// load8 of the operand of a split: one view, or the sum of up to four views
+// (OpTerms) evaluated element by element in its nesting order, innermost sum
+// first, so only two groups of eight values are live; `off` is the row's
+// element offset, the same in every view.  kExpr = false compiles the plain
+// load alone.
+template <bool kExpr>
+__device__ __forceinline__ void load8_op(const double *a0, const OpTerms &ex, int64_t off, int64_t c, int64_t P,
+                                         bool vec, double (&v)[8]) {
+    if (!kExpr || ex.shape <= 1) {
+        load8(a0 + off, c, P, vec, v);
+        return;
+    }
+    const double *x0 = a0 + off, *x1 = ex.x[0] + off, *x2 = ex.x[1] + off, *x3 = ex.x[2] + off;
+    double w[8];
+    switch (ex.shape) {
+        case 2:  // x0 o0 x1
+            load8(x0, c, P, vec, v), load8(x1, c, P, vec, w), fold8(v, ex.op[0], w, false);
+            break;
+        case 3:  // x0 o0 (x1 o1 x2)
+            load8(x1, c, P, vec, v), load8(x2, c, P, vec, w), fold8(v, ex.op[1], w, false);
+            load8(x0, c, P, vec, w), fold8(v, ex.op[0], w, true);
+            break;
+        case 4:  // (x0 o0 x1) o1 x2
+            load8(x0, c, P, vec, v), load8(x1, c, P, vec, w), fold8(v, ex.op[0], w, false);
+            load8(x2, c, P, vec, w), fold8(v, ex.op[1], w, false);
+            break;
+        case 5:  // x0 o0 (x1 o1 (x2 o2 x3))
+            load8(x2, c, P, vec, v), load8(x3, c, P, vec, w), fold8(v, ex.op[2], w, false);
+            load8(x1, c, P, vec, w), fold8(v, ex.op[1], w, true);
+            load8(x0, c, P, vec, w), fold8(v, ex.op[0], w, true);
+            break;
+        default:  // 6: x0 o0 ((x1 o1 x2) o2 x3)
+            load8(x1, c, P, vec, v), load8(x2, c, P, vec, w), fold8(v, ex.op[1], w, false);
+            load8(x3, c, P, vec, w), fold8(v, ex.op[2], w, false);
+            load8(x0, c, P, vec, w), fold8(v, ex.op[0], w, true);
+            break;
+    }
+}
+
+// Element (k, j) of a column split's operand (one view or a sum of views).
+__device__ __forceinline__ double load_op(const SplitB &p, int64_t k, int64_t j) {
+    const int64_t off = k * p.ldb + j;
+    const double x0 = __ldg(p.B + off);
+    if (p.ex.shape <= 1) return x0;
+    const int nt = terms_of(p.ex.shape);
+    const double x1 = __ldg(p.ex.x[0] + off);
+    const double x2 = nt > 2 ? __ldg(p.ex.x[1] + off) : 0.0;
+    const double x3 = nt > 3 ? __ldg(p.ex.x[2] + off) : 0.0;
+    return eval_terms(p.ex, x0, x1, x2, x3);
+}
+
+// Every view of an operand starts its rows on 16 bytes (vector loads).
+__device__ __forceinline__ bool rows_aligned(const double *a0, const OpTerms &ex, int64_t off) {
+    uintptr_t bits = (uintptr_t)(a0 + off);
+    const int nt = terms_of(ex.shape);
+    for (int t = 0; t + 1 < nt; ++t) bits |= (uintptr_t)(ex.x[t] + off);
+    return (bits & 15) == 0;
+}
+
 constexpr int kRowThreads = 256;
 // Rows of at most this many (padded) elements are split by one warp each, 8
 // rows per CTA; longer ones by a whole CTA.
@@ -206,16 +272,16 @@ constexpr int64_t kWarpRowMax = 1024;
 // GPU at 8192 columns), so A crosses HBM once.  `tid` is the thread's index
 // among the T; with T = 256 `red` is 8 words of shared memory (unused for a
 // warp).
-template <int KIND, int T>
+template <int KIND, int T, bool kExpr = false>
 __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int tid, unsigned long long *red) {
-    const double *__restrict__ a = p.A + row * p.lda;
+    const int64_t off = row * p.lda;
     const int64_t P = p.P, Pp = p.Pp;
     const int s = p.s;
-    const bool vec = (((uintptr_t)a) & 15) == 0;
+    const bool vec = kExpr ? rows_aligned(p.A, p.ex, off) : (((uintptr_t)(p.A + off)) & 15) == 0;
     unsigned long long mx = 0;
     for (int64_t c = 8 * tid; c < P; c += 8 * T) {
         double x[8];
-        load8(a, c, P, vec, x);
+        load8_op<kExpr>(p.A, p.ex, off, c, P, vec, x);
 #pragma unroll
         for (int u = 0; u < 8; ++u) mx = umax64(mx, absbits(x[u]));
     }
@@ -239,7 +305,7 @@ __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int tid,
     // starting before Pp ends by Pp.
     for (int64_t c = 8 * tid; c < Pp; c += 8 * T) {
         double x[8];
-        load8(a, c, P, vec, x);
+        load8_op<kExpr>(p.A, p.ex, off, c, P, vec, x);
         int64_t V[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) V[u] = round_scaled(x[u], sh);
@@ -266,7 +332,11 @@ __device__ __forceinline__ void col_max_part(const SplitB &p, int64_t j, int64_t
     if (j >= p.M) return;
     const int64_t k1 = min(p.P, k0 + 256);
     unsigned long long mx = 0;
-    for (int64_t k = k0; k < k1; ++k) mx = umax64(mx, absbits(p.B[k * p.ldb + j]));
+    if (p.ex.shape <= 1) {
+        for (int64_t k = k0; k < k1; ++k) mx = umax64(mx, absbits(p.B[k * p.ldb + j]));
+    } else {
+        for (int64_t k = k0; k < k1; ++k) mx = umax64(mx, absbits(load_op(p, k, j)));
+    }
     if (mx) atomicMax(p.colmax + j, mx);
 }
 
@@ -298,13 +368,23 @@ __device__ __forceinline__ void split_cols_tile(const SplitB &p, int64_t jt, int
     const double *__restrict__ bj = p.B + j;
     unsigned char *row0 = p.slices + j * Pp * es;
     const int64_t stride = (int64_t)p.Mr * Pp * es;
-    // All 32 loads first, so they are in flight together.
+    // All 32 loads first, so they are in flight together (an operand summed
+    // from several views evaluates each element as it is loaded).
     double x[4][8];
+    if (p.ex.shape <= 1) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int64_t k0 = kt * SC_K + 8 * (kg + 4 * r);
+        for (int r = 0; r < 4; ++r) {
+            const int64_t k0 = kt * SC_K + 8 * (kg + 4 * r);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) x[r][u] = (k0 + u < P) ? __ldg(bj + (k0 + u) * ldb) : 0.0;
+            for (int u = 0; u < 8; ++u) x[r][u] = (k0 + u < P) ? __ldg(bj + (k0 + u) * ldb) : 0.0;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t k0 = kt * SC_K + 8 * (kg + 4 * r);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[r][u] = (k0 + u < P) ? load_op(p, k0 + u, j) : 0.0;
+        }
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -337,7 +417,9 @@ __global__ void __launch_bounds__(256) group_zero_colmax_kernel(const EmuProblem
     }
 }
 
-template <int KIND>
+// kExpr: some problem of the launch splits a sum of views (Strassen levels
+// over the product); launches without any take the plain instantiation.
+template <int KIND, bool kExpr>
 __global__ void __launch_bounds__(kRowThreads, 4) group_split_rows_kernel(const EmuProblem *tab,
                                                                           const int64_t *begin,
                                                                           const GroupHeader *hdr) {
@@ -348,9 +430,9 @@ __global__ void __launch_bounds__(kRowThreads, 4) group_split_rows_kernel(const 
         const SplitA &p = tab[g].spa;
         if (p.Pp <= kWarpRowMax) {  // 8 rows per unit, one per warp (the whole CTA takes this branch)
             const int64_t row = (u - begin[g]) * (kRowThreads / 32) + (threadIdx.x >> 5);
-            if (row < p.N) split_row<KIND, 32>(p, row, threadIdx.x & 31, nullptr);
+            if (row < p.N) split_row<KIND, 32, kExpr>(p, row, threadIdx.x & 31, nullptr);
         } else {  // one row per unit
-            split_row<KIND, kRowThreads>(p, u - begin[g], threadIdx.x, red);
+            split_row<KIND, kRowThreads, kExpr>(p, u - begin[g], threadIdx.x, red);
         }
     }
 }
@@ -445,16 +527,17 @@ namespace mm {
 
 // Slice count for a tier, or for an explicit count: MM_ERR_ARG for an unknown
 // format or an invalid request, MM_ERR_UNSUPPORTED when the tier needs more
-// than the 8 slices (8 TMEM accumulators of 64 columns) the kernel holds.
+// slices than the format's kernel holds (8 BF16 accumulators of 64 TMEM
+// columns; 10 FP8-E4M3 ones of 32).
 int emulated_slices(int32_t kind, int32_t nslices, double tier) {
     if (kind != MM_SLICE_BF16 && kind != MM_SLICE_FP8E4M3) return MM_ERR_ARG;
-    if (nslices > 0) return nslices <= 8 ? nslices : MM_ERR_ARG;
+    if (nslices > 0) return nslices <= fmt_max_slices(kind) ? nslices : MM_ERR_ARG;
     if (!(tier > 0.0)) return MM_ERR_ARG;
     // beta*s - 1 bits of each row/column; about 8 more bits than -log2(tier) keep the
     // normwise error below the tier on wide-exponent inputs.
     const double need = (-log2(tier) + 9.0) / fmt_beta(kind);
     const int s = std::max(1, (int)ceil(need));
-    if (s > 8) return MM_ERR_UNSUPPORTED;
+    if (s > fmt_max_slices(kind)) return MM_ERR_UNSUPPORTED;
     return s;
 }
 
@@ -535,7 +618,7 @@ int slice_product(const EmuWork &w, int64_t r0, int64_t n, int64_t P, int64_t M,
     const size_t es = fmt_esize(kind);
     const int64_t nr = mm::ceil_div(n, BM) * BM;
     int rc = encode_slices(&tmA, w.sa + (size_t)r0 * w.L.Pp * es, nr, w.L.Pp, s, BM, kind, w.L.Nr);
-    if (!rc) rc = encode_slices(&tmB, w.sb, w.L.Mr, w.L.Pp, s, BN, kind);
+    if (!rc) rc = encode_slices(&tmB, w.sb, w.L.Mr, w.L.Pp, s, slice_bn(s), kind);
     if (rc) return rc;
     EmuParams prm{};
     fill_common(prm, s);
@@ -543,7 +626,7 @@ int slice_product(const EmuWork &w, int64_t r0, int64_t n, int64_t P, int64_t M,
     prm.P = P;
     prm.M = M;
     prm.tiles_m = (int)mm::ceil_div(n, BM);
-    prm.tiles_n = (int)mm::ceil_div(M, BN);
+    prm.tiles_n = (int)mm::ceil_div(M, slice_bn(s));
     prm.ea = w.ea + r0;
     prm.fb = w.fb;
     prm.C = C;
@@ -778,8 +861,11 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
     if (rc) return rc;
     if (gl.grid[U_ROWS] > 0)
         rc = launch("emu_group_split_rows", st, [&] {
-            const auto k = gl.kind == MM_SLICE_FP8E4M3 ? group_split_rows_kernel<MM_SLICE_FP8E4M3>
-                                                       : group_split_rows_kernel<MM_SLICE_BF16>;
+            const auto k = gl.kind == MM_SLICE_FP8E4M3
+                               ? (gl.expr ? group_split_rows_kernel<MM_SLICE_FP8E4M3, true>
+                                          : group_split_rows_kernel<MM_SLICE_FP8E4M3, false>)
+                               : (gl.expr ? group_split_rows_kernel<MM_SLICE_BF16, true>
+                                          : group_split_rows_kernel<MM_SLICE_BF16, false>);
             k<<<(unsigned)gl.grid[U_ROWS], kRowThreads, 0, st>>>((const EmuProblem *)gl.tab, gl.begin[U_ROWS],
                                                          (const GroupHeader *)gl.hdr);
         });
@@ -820,7 +906,7 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
 // problem i's data region of problem_data_bytes(probs[i], s, kind) bytes; the
 // table is laid out for `capacity` problems (>= count).
 int group_build(const mm_problem *probs, int count, int capacity, int s, void *table_dev, char *const *data,
-                std::vector<unsigned char> &image, GroupLaunch &gl, int kind) {
+                std::vector<unsigned char> &image, GroupLaunch &gl, int kind, const OpTerms *ta, const OpTerms *tb) {
     if (capacity < count) return fail(MM_ERR_ARG, "grouped launch: %d problems exceed capacity %d", count, capacity);
     const GroupLayout G = group_layout(capacity);
     char *t = (char *)table_dev;
@@ -838,6 +924,7 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
     // data region; any order gives the same results.
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
+    bool expr = false;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return probs[x].P > probs[y].P; });
     for (int i = 0; i < count; ++i) {
         const mm_problem &q = probs[order[i]];
@@ -853,21 +940,22 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
         unsigned char *sa = (unsigned char *)w;
         w += slices_bytes(L.Nr, L.Pp, s, kind);
         unsigned char *sb = (unsigned char *)w;
-        e.spa = SplitA{q.N, q.P, q.lda, L.Nr, L.Pp, q.A, s, ea, sa};
-        e.spb = SplitB{q.P, q.M, q.ldb, L.Mr, L.Pp, q.B, s, cm, fb, sb};
+        e.spa = SplitA{q.N, q.P, q.lda, L.Nr, L.Pp, q.A, s, ea, sa, ta ? ta[order[i]] : OpTerms{}};
+        e.spb = SplitB{q.P, q.M, q.ldb, L.Mr, L.Pp, q.B, s, cm, fb, sb, tb ? tb[order[i]] : OpTerms{}};
+        if (e.spa.ex.shape > 1 || e.spb.ex.shape > 1) expr = true;
         fill_common(e.prm, s);
         e.prm.N = q.N;
         e.prm.P = q.P;
         e.prm.M = q.M;
         e.prm.tiles_m = (int)ceil_div(q.N, BM);
-        e.prm.tiles_n = (int)ceil_div(q.M, BN);
+        e.prm.tiles_n = (int)ceil_div(q.M, slice_bn(s));
         e.prm.ea = ea;
         e.prm.fb = fb;
         e.prm.C = q.C;
         e.prm.ldc = q.ldc;
         e.prm.status = status;
         int rc = encode_slices(&e.tmA, sa, L.Nr, L.Pp, s, BM, kind);
-        if (!rc) rc = encode_slices(&e.tmB, sb, L.Mr, L.Pp, s, BN, kind);
+        if (!rc) rc = encode_slices(&e.tmB, sb, L.Mr, L.Pp, s, slice_bn(s), kind);
         if (rc) return rc;
         for (int k = 0; k < 5; ++k) begin[k][i] = units[k];
         units[U_ROWS] += L.Pp <= kWarpRowMax ? ceil_div(q.N, kRowThreads / 32) : q.N;
@@ -887,11 +975,14 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
     gl.hdr = t + G.off_hdr;
     gl.s = s;
     gl.kind = kind;
+    gl.expr = expr;
     return MM_OK;
 }
 
-int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void *ws, cudaStream_t st) {
+int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void *ws, cudaStream_t st,
+                       const OpTerms *ta, const OpTerms *tb) {
     std::vector<mm_problem> live;
+    std::vector<OpTerms> lta, ltb;
     live.reserve(count);
     for (int i = 0; i < count; ++i) {
         const mm_problem &q = probs[i];
@@ -902,6 +993,8 @@ int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void
             continue;
         }
         live.push_back(q);
+        lta.push_back(ta ? ta[i] : OpTerms{});
+        ltb.push_back(tb ? tb[i] : OpTerms{});
     }
     if (live.empty()) return MM_OK;
     std::vector<unsigned char> image;
@@ -912,7 +1005,8 @@ int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void
         data[i] = d;
         d += problem_data_bytes(live[i], s, kind);
     }
-    int rc = group_build(live.data(), (int)live.size(), (int)live.size(), s, ws, data.data(), image, gl, kind);
+    int rc = group_build(live.data(), (int)live.size(), (int)live.size(), s, ws, data.data(), image, gl, kind,
+                         lta.data(), ltb.data());
     if (rc) return rc;
     // Pageable source: the copy is staged before cudaMemcpyAsync returns, so `image` may go.
     cudaError_t e = cudaMemcpyAsync((void *)gl.tab, image.data(), image.size(), cudaMemcpyHostToDevice, st);

@@ -13,7 +13,7 @@
 
 namespace emu {
 
-constexpr int BM = 128, BN = 64;  // output tile rows and columns
+constexpr int BM = 128, BN = 64;  // output tile rows and (at most) columns
 constexpr int KB_BYTES = 64;       // one K-block of one slice row: 32 BF16 or 64 FP8 values
 
 // Slice formats.  BF16 holds balanced base-2^7 digits (|d| <= 64, 8-bit
@@ -27,13 +27,22 @@ __host__ __device__ constexpr int fmt_bke(int kind) { return KB_BYTES / fmt_esiz
 __host__ __device__ constexpr int fmt_pair_blocks(int kind) {
     return (1 << (26 - 2 * fmt_beta(kind))) / fmt_bke(kind);
 }
+// Most slices per format: TMEM holds 512 FP32 columns, one accumulator per
+// diagonal; 8 diagonals of 64 columns fill it, and FP8-E4M3 goes on to 10
+// diagonals of 32 columns.
+__host__ __device__ constexpr int fmt_max_slices(int kind) { return kind == MM_SLICE_FP8E4M3 ? 10 : 8; }
+// Output tile width for s slices: 64 columns per diagonal up to 8 slices, 32
+// beyond (so s accumulators still fit TMEM's 512 columns).
+__host__ __device__ constexpr int slice_bn(int s) { return s > 8 ? 32 : BN; }
 // Launch-wide constants of the slice product, functions of the slice format
 // and count only (so the kernel, templated on both, has them at compile time):
 // a stage holds one K-block (64 bytes per slice row) of all s slices of A and
 // B; up to 4 stages fit the shared memory; an exact chunk is the exact length
 // of diagonal s - 1; TMEM is allocated in powers of two >= 32 columns.
 constexpr int kSmemLimit = 232448;  // opt-in dynamic shared memory per block on sm_103
-__host__ __device__ constexpr uint32_t slice_stage_bytes(int s) { return (uint32_t)s * (BM + BN) * KB_BYTES; }
+__host__ __device__ constexpr uint32_t slice_stage_bytes(int s) {
+    return (uint32_t)s * (BM + slice_bn(s)) * KB_BYTES;
+}
 __host__ __device__ constexpr int slice_stages(int s) {
     return (int)((kSmemLimit - 2048) / slice_stage_bytes(s)) < 4 ? (int)((kSmemLimit - 2048) / slice_stage_bytes(s)) : 4;
 }
@@ -41,28 +50,61 @@ __host__ __device__ constexpr int slice_chunk_blocks(int kind, int s) {
     return fmt_pair_blocks(kind) / s > 1 ? fmt_pair_blocks(kind) / s : 1;
 }
 __host__ __device__ constexpr uint32_t slice_tmem_cols(int s) {
-    return (uint32_t)(s * BN <= 32 ? 32 : s * BN <= 64 ? 64 : s * BN <= 128 ? 128 : s * BN <= 256 ? 256 : 512);
+    return (uint32_t)(s * slice_bn(s) <= 32    ? 32
+                      : s * slice_bn(s) <= 64  ? 64
+                      : s * slice_bn(s) <= 128 ? 128
+                      : s * slice_bn(s) <= 256 ? 256
+                                               : 512);
 }
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
+// An operand formed while it is split, from the operand pointer x0 and up to
+// three more views x1..x3 with the same shape and leading dimension (the
+// quadrants of a Strassen node), each node of the sum rounded as the
+// Plus/Minus matrices of sections "StrassenNaiv" and "StrassenWinograd" are,
+// o = +1 (Plus) or -1 (Minus):
+//   shape 0 or 1: x0;              2: x0 o0 x1;
+//   3: x0 o0 (x1 o1 x2);           4: (x0 o0 x1) o1 x2;
+//   5: x0 o0 (x1 o1 (x2 o2 x3));   6: x0 o0 ((x1 o1 x2) o2 x3).
+using mm::OpTerms;
+
+__device__ __forceinline__ double plus_minus(double a, int8_t o, double b) {
+    return o > 0 ? __dadd_rn(a, b) : __dsub_rn(a, b);
+}
+__device__ __forceinline__ double eval_terms(const OpTerms &e, double x0, double x1, double x2, double x3) {
+    switch (e.shape) {
+        case 2: return plus_minus(x0, e.op[0], x1);
+        case 3: return plus_minus(x0, e.op[0], plus_minus(x1, e.op[1], x2));
+        case 4: return plus_minus(plus_minus(x0, e.op[0], x1), e.op[1], x2);
+        case 5: return plus_minus(x0, e.op[0], plus_minus(x1, e.op[1], plus_minus(x2, e.op[2], x3)));
+        case 6: return plus_minus(x0, e.op[0], plus_minus(plus_minus(x1, e.op[1], x2), e.op[2], x3));
+        default: return x0;
+    }
+}
+__host__ __device__ constexpr int terms_of(int shape) {
+    return shape <= 1 ? 1 : shape == 2 ? 2 : (shape == 3 || shape == 4) ? 3 : 4;
+}
+
 // Everything one split of A needs (one problem).
 struct SplitA {
     int64_t N, P, lda, Nr, Pp;
-    const double *A;
+    const double *A;  // the operand, or its first term when ex.shape > 1
     int s;
     int32_t *ea;
     unsigned char *slices;  // [s][Nr][Pp] elements of the slice format (the kernels' template parameter)
+    OpTerms ex;             // shape 0: A itself
 };
 
 // Everything the column split of B needs (one problem).
 struct SplitB {
     int64_t P, M, ldb, Mr, Pp;
-    const double *B;
+    const double *B;  // the operand, or its first term when ex.shape > 1
     int s;
     unsigned long long *colmax;  // zeroed before col_max runs
     int32_t *fb;
     unsigned char *slices;  // [s][Mr][Pp] elements of the slice format
+    OpTerms ex;             // shape 0: B itself
 };
 
 struct EmuParams {
@@ -149,25 +191,27 @@ __device__ __forceinline__ void tile_of(int64_t id, int tiles_m, int tiles_n, in
 // slices.  Diagonals 2j and 2j + 1 share one period, that of 2j + 1 (the
 // shorter, so both stay exact): they are written by the same N = 128 MMAs
 // (see slice_tiles) and must start over together.  The countdowns live in one
-// register, 4 bits per diagonal.
-__device__ __forceinline__ uint32_t drain_periods(int CB, int pair_blocks) {
-    uint32_t R = 0;
+// register (64 bits: 4 bits per diagonal, up to 10).
+constexpr int kMaxDiag = 10;
+__device__ __forceinline__ uint64_t drain_periods(int CB, int pair_blocks) {
+    uint64_t R = 0;
 #pragma unroll
-    for (int d = 0; d < 8; ++d) {
+    for (int d = 0; d < kMaxDiag; ++d) {
         const int dd = d | 1;
-        R |= (uint32_t)(min(16, max(1, (pair_blocks / (dd + 1)) / CB)) - 1) << (4 * d);
+        R |= (uint64_t)(min(16, max(1, (pair_blocks / (dd + 1)) / CB)) - 1) << (4 * d);
     }
     return R;
 }
 // Diagonals due at this chunk end; advances the countdowns.
-__device__ __forceinline__ uint32_t drain_due(uint32_t &cnt, uint32_t R, bool last) {
-    uint32_t due = 0, nc = 0;
+__device__ __forceinline__ uint32_t drain_due(uint64_t &cnt, uint64_t R, bool last) {
+    uint32_t due = 0;
+    uint64_t nc = 0;
 #pragma unroll
-    for (int d = 0; d < 8; ++d) {
-        const uint32_t v = (cnt >> (4 * d)) & 15u;
+    for (int d = 0; d < kMaxDiag; ++d) {
+        const uint32_t v = (uint32_t)(cnt >> (4 * d)) & 15u;
         const bool z = last || v == 0;
         due |= (uint32_t)z << d;
-        nc |= (z ? (R >> (4 * d)) & 15u : v - 1) << (4 * d);
+        nc |= (uint64_t)(z ? (uint32_t)(R >> (4 * d)) & 15u : v - 1) << (4 * d);
     }
     cnt = nc;
     return due;
@@ -206,10 +250,12 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int KIND = kFP8 ? MM_SLICE_FP8E4M3 : MM_SLICE_BF16;
     constexpr int bke = fmt_bke(KIND), pair_blocks = fmt_pair_blocks(KIND);
-    static_assert(kS >= 1 && kS <= 8, "1 to 8 slices");
+    static_assert(kS >= 1 && kS <= fmt_max_slices(KIND), "1 to 8 BF16 or 1 to 10 FP8-E4M3 slices");
     constexpr int s = kS;
+    constexpr int TBN = slice_bn(s);  // tile width: 64, or 32 past 8 slices
+    constexpr int CPT = TBN / 2;      // columns each epilogue thread drains and rounds
     constexpr int S = slice_stages(s), CB = slice_chunk_blocks(KIND, s);
-    constexpr uint32_t a_bytes = (uint32_t)s * BM * KB_BYTES, b_bytes = (uint32_t)s * BN * KB_BYTES;
+    constexpr uint32_t a_bytes = (uint32_t)s * BM * KB_BYTES, b_bytes = (uint32_t)s * TBN * KB_BYTES;
     constexpr uint32_t stage_bytes = slice_stage_bytes(s), tmem_cols = slice_tmem_cols(s);
     static_assert(a_bytes + b_bytes == stage_bytes, "stage layout");
     uint64_t *full = bars, *empty = bars + 8, *acc_full = bars + 16, *acc_empty = bars + 17, *mma_done = bars + 18;
@@ -248,7 +294,7 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                 mmdev::prefetch_tmap(j.tmA);
                 mmdev::prefetch_tmap(j.tmB);
                 const int nkb = (int)((j.p.P + bke - 1) / bke);
-                const int32_t m0 = j.tm * BM, n0 = j.tn * BN;
+                const int32_t m0 = j.tm * BM, n0 = j.tn * TBN;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const uint32_t st = it % S, use = it / S;
                     if (use > 0 && !mmdev::mbar_wait(&empty[st], (use - 1) & 1u)) {
@@ -277,9 +323,9 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
         // as 20 MMAs per K-step, and the loop is fully unrolled with no branch
         // between them.  sigma = 0 writes every accumulator first, so it alone
         // carries the start-over flag.
-        const uint32_t idesc = kFP8 ? mmdev::idesc_e4m3_f32(BM, BN) : mmdev::idesc_bf16_f32(BM, BN);
-        const uint32_t idesc2 = kFP8 ? mmdev::idesc_e4m3_f32(BM, 2 * BN) : mmdev::idesc_bf16_f32(BM, 2 * BN);
-        const uint32_t R = drain_periods(CB, pair_blocks);
+        const uint32_t idesc = kFP8 ? mmdev::idesc_e4m3_f32(BM, TBN) : mmdev::idesc_bf16_f32(BM, TBN);
+        const uint32_t idesc2 = kFP8 ? mmdev::idesc_e4m3_f32(BM, 2 * TBN) : mmdev::idesc_bf16_f32(BM, 2 * TBN);
+        const uint64_t R = drain_periods(CB, pair_blocks);
         uint32_t it = 0, ev = 0;  // K-blocks consumed and chunks handed to the epilogue, over all tiles
         bool ok = true;
         for (int64_t id = blockIdx.x; id < total && ok; id += gridDim.x) {
@@ -287,7 +333,8 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
             tiles.get(id, j);
             const int nkb = (int)((j.p.P + bke - 1) / bke);
             int kin = 0;                // K-block within the current exact chunk
-            uint32_t cnt = R, fresh = 0xffu;  // accumulators that start over at the next chunk
+            uint64_t cnt = R;
+            uint32_t fresh = ~0u;  // accumulators that start over at the next chunk
             for (int kb = 0; kb < nkb; ++kb, ++it) {
                 const uint32_t st = it % S, use = it / S;
                 if (kin == 0 && ev > 0) {  // the accumulators must have been read out
@@ -310,12 +357,12 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
                             const uint64_t ad = da + (uint64_t)((sg * (BM * KB_BYTES) + kk * 32) >> 4);
-                            const uint64_t bd = db + (uint64_t)((tu * (BN * KB_BYTES) + kk * 32) >> 4);
+                            const uint64_t bd = db + (uint64_t)((tu * (TBN * KB_BYTES) + kk * 32) >> 4);
                             const uint32_t acc = (sg == 0 && kk == 0) ? (((fresh_now >> d) & 1u) ^ 1u) : 1u;
                             if (kFP8)
-                                mmdev::mma_e4m3_elect(tmem + (uint32_t)(d * BN), ad, bd, id2, acc);
+                                mmdev::mma_e4m3_elect(tmem + (uint32_t)(d * TBN), ad, bd, id2, acc);
                             else
-                                mmdev::mma_bf16_elect(tmem + (uint32_t)(d * BN), ad, bd, id2, acc);
+                                mmdev::mma_bf16_elect(tmem + (uint32_t)(d * TBN), ad, bd, id2, acc);
                         }
                     }
                 }
@@ -334,12 +381,12 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
         (void)mmdev::mbar_wait(mma_done, 0);
     } else {
         const int q = warp & 3, h = (warp - 2) >> 2;
-        const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h);
+        const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(CPT * h);
         uint32_t ev = 0;
         bool ok = true;
         constexpr int hsplit = (s + 1) / 2;  // diagonals [0, hsplit) sum into whi, the rest into wlo
         constexpr int beta = fmt_beta(KIND);
-        const uint32_t R = drain_periods(CB, pair_blocks);
+        const uint64_t R = drain_periods(CB, pair_blocks);
         for (int64_t id = blockIdx.x; id < total && ok; id += gridDim.x) {
             int nchunks;
             {
@@ -347,10 +394,10 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                 tiles.get(id, j);
                 nchunks = ((int)((j.p.P + bke - 1) / bke) + CB - 1) / CB;
             }
-            int64_t whi[32], wlo[32];
+            int64_t whi[CPT], wlo[CPT];
 #pragma unroll
-            for (int k = 0; k < 32; ++k) whi[k] = wlo[k] = 0;
-            uint32_t cnt = R;
+            for (int k = 0; k < CPT; ++k) whi[k] = wlo[k] = 0;
+            uint64_t cnt = R;
             for (int ch = 0; ch < nchunks; ++ch, ++ev) {
                 if (!mmdev::mbar_wait(acc_full, ev & 1u)) {
                     raise_status(c.status, mm::kStatusTimeoutEpi);
@@ -365,13 +412,16 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
 #pragma unroll
                 for (int d = 0; d < s; ++d) {
                     if (!((due >> d) & 1u)) continue;
-                    uint32_t v[32];
-                    mmdev::tmem_ld_32x32b_x32(tbase + (uint32_t)(d * BN), v);
+                    uint32_t v[CPT];
+                    if constexpr (CPT == 32)
+                        mmdev::tmem_ld_32x32b_x32(tbase + (uint32_t)(d * TBN), v);
+                    else
+                        mmdev::tmem_ld_32x32b_x16(tbase + (uint32_t)(d * TBN), v);
                     mmdev::tmem_wait_ld();
                     const int32_t weight = 1 << (d < hsplit ? beta * (hsplit - 1 - d) : beta * (s - 1 - d));
                     int64_t *acc = d < hsplit ? whi : wlo;
 #pragma unroll
-                    for (int k = 0; k < 32; ++k)
+                    for (int k = 0; k < CPT; ++k)
                         acc[k] = mad_wide(__float2int_rn(__uint_as_float(v[k])), weight, acc[k]);
                 }
                 mmdev::tc_fence_before();
@@ -383,17 +433,17 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
             TileJob j;
             tiles.get(id, j);
             const EmuParams &p = j.p;
-            const int64_t row = (int64_t)j.tm * BM + 32 * q + lane, n0 = (int64_t)j.tn * BN;
+            const int64_t row = (int64_t)j.tm * BM + 32 * q + lane, n0 = (int64_t)j.tn * TBN;
             if (ok && row < p.N) {
                 const int e = p.ea[row];
                 const int sh2 = beta * (s - hsplit);
                 double *crow = p.C + row * p.ldc;
 #pragma unroll
-                for (int k = 0; k < 32; k += 2) {
+                for (int k = 0; k < CPT; k += 2) {
                     double out[2];
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
-                        const int64_t col = n0 + 32 * h + k + u;
+                        const int64_t col = n0 + CPT * h + k + u;
                         const int64_t wh = whi[k + u], wl = wlo[k + u];
                         // W = wh * 2^sh2 + wl as a signed 128-bit integer.
                         uint64_t lo = sh2 ? ((uint64_t)wh << sh2) : (uint64_t)wh;
@@ -404,7 +454,7 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
                         const int f = (col < p.M) ? p.fb[col] : 0;
                         out[u] = int128_scaled_to_double(hi, lo, e + f + 2 - beta * (s + 1));
                     }
-                    const int64_t col = n0 + 32 * h + k;
+                    const int64_t col = n0 + CPT * h + k;
                     double *dst = crow + col;
                     if (col + 1 < p.M && (((uintptr_t)dst & 15) == 0)) {
                         *reinterpret_cast<double2 *>(dst) = make_double2(out[0], out[1]);
@@ -506,10 +556,10 @@ __global__ void __launch_bounds__(kThreads, 1) group_slice_gemm_kernel(const Emu
 }
 
 // Launchers, one per slice format (defined in slice_gemm_bf16.cu and
-// slice_gemm_fp8.cu): launch the instantiation for slice count s (1..8) with
-// the given grid and dynamic shared memory on st.  cudaErrorInvalidValue for
-// an s outside 1..8 (nothing is launched); otherwise cudaSuccess, launch
-// errors are left for cudaGetLastError.
+// slice_gemm_fp8.cu): launch the instantiation for slice count s (1..8 BF16,
+// 1..10 FP8-E4M3) with the given grid and dynamic shared memory on st.
+// cudaErrorInvalidValue for an s outside that range (nothing is launched);
+// otherwise cudaSuccess, launch errors are left for cudaGetLastError.
 cudaError_t launch_slice_gemm_bf16(int s, unsigned grid, size_t smem, cudaStream_t st, const CUtensorMap &tmA,
                                    const CUtensorMap &tmB, const EmuParams &prm);
 cudaError_t launch_slice_gemm_fp8(int s, unsigned grid, size_t smem, cudaStream_t st, const CUtensorMap &tmA,
@@ -531,7 +581,7 @@ cudaError_t dispatch_slice_gemm(int s, unsigned grid, size_t smem, cudaStream_t 
         slice_gemm_kernel<kFP8, kS><<<grid, kThreads, smem, st>>>(tmA, tmB, prm);
         return cudaSuccess;
     }
-    if constexpr (kS < 8)
+    if constexpr (kS < fmt_max_slices(kFP8 ? MM_SLICE_FP8E4M3 : MM_SLICE_BF16))
         return dispatch_slice_gemm<kFP8, kS + 1>(s, grid, smem, st, tmA, tmB, prm);
     return cudaErrorInvalidValue;
 }
@@ -543,7 +593,7 @@ cudaError_t dispatch_group_slice_gemm(int s, unsigned grid, size_t smem, cudaStr
         group_slice_gemm_kernel<kFP8, kS><<<grid, kThreads, smem, st>>>(tab, begin, hdr);
         return cudaSuccess;
     }
-    if constexpr (kS < 8)
+    if constexpr (kS < fmt_max_slices(kFP8 ? MM_SLICE_FP8E4M3 : MM_SLICE_BF16))
         return dispatch_group_slice_gemm<kFP8, kS + 1>(s, grid, smem, st, tab, begin, hdr);
     return cudaErrorInvalidValue;
 }
@@ -555,7 +605,7 @@ cudaError_t set_slice_gemm_smem(int bytes) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute((const void *)group_slice_gemm_kernel<kFP8, kS>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if constexpr (kS < 8)
+    if constexpr (kS < fmt_max_slices(kFP8 ? MM_SLICE_FP8E4M3 : MM_SLICE_BF16))
         if (e == cudaSuccess) return set_slice_gemm_smem<kFP8, kS + 1>(bytes);
     return e;
 }

@@ -1,4 +1,4 @@
-// The FP8-E4M3 instantiations of the persistent slice product, slice counts 1..8
+// The FP8-E4M3 instantiations of the persistent slice product, slice counts 1..10
 // (one translation unit per format, so the build compiles them in parallel).
 #include "slice_gemm.cuh"
 

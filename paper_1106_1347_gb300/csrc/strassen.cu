@@ -233,11 +233,21 @@ __global__ void __launch_bounds__(256) leaf_naive_kernel(const Mat A, const Mat 
         for (int e = threadIdx.x; e < n * p; e += blockDim.x) As[e] = at(A, z, e / p, e % p);
         for (int e = threadIdx.x; e < p * m; e += blockDim.x) Bs[e] = at(B, z, e / m, e % m);
         __syncthreads();
-        for (int o = threadIdx.x; o < n * m; o += blockDim.x) {
-            const int r = o / m, c = o - (o / m) * m;
-            double acc = 0.0;
-            for (int k = 0; k < p; ++k) acc = fma(As[r * p + k], Bs[k * m + c], acc);
-            put(C, z, r, c, acc);
+        for (int o0 = threadIdx.x; o0 < n * m; o0 += 4 * blockDim.x) {  // four FMA chains per thread
+            int r[4], c[4];
+            double acc[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int o = min(o0 + i * (int)blockDim.x, n * m - 1);
+                r[i] = o / m, c[i] = o - (o / m) * m, acc[i] = 0.0;
+            }
+            for (int k = 0; k < p; ++k) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] = fma(As[r[i] * p + k], Bs[k * m + c[i]], acc[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (o0 + i * (int)blockDim.x < n * m) put(C, z, r[i], c[i], acc[i]);
         }
         __syncthreads();
     }
@@ -292,17 +302,35 @@ __device__ __forceinline__ void leaf_level_step(const double *As, const double *
         Ts[e] = o[child];
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < n * m; o += blockDim.x) {
-        const int r = o / m, c = o - (o / m) * m;
-        double acc = 0.0;
-        for (int k = 0; k < p; ++k) acc = fma(Ss[r * p + k], Ts[k * m + c], acc);
-        target<walk_step(V, S).quad[0], walk_step(V, S).sign[0], walk_step(V, S).first[0]>(Cs, r, c, n, m, acc);
-        if constexpr (nt > 1)
-            target<walk_step(V, S).quad[1], walk_step(V, S).sign[1], walk_step(V, S).first[1]>(Cs, r, c, n, m, acc);
-        if constexpr (nt > 2)
-            target<walk_step(V, S).quad[2], walk_step(V, S).sign[2], walk_step(V, S).first[2]>(Cs, r, c, n, m, acc);
-        if constexpr (nt > 3)
-            target<walk_step(V, S).quad[3], walk_step(V, S).sign[3], walk_step(V, S).first[3]>(Cs, r, c, n, m, acc);
+    // Four outputs per thread at once: four independent FMA chains keep the
+    // FP64 pipe fed even with one CTA per SM (blocks of 32).
+    for (int o0 = threadIdx.x; o0 < n * m; o0 += 4 * blockDim.x) {
+        int r[4], c[4];
+        double acc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int o = min(o0 + i * (int)blockDim.x, n * m - 1);  // past the end: a duplicate, not stored
+            r[i] = o / m, c[i] = o - (o / m) * m, acc[i] = 0.0;
+        }
+        for (int k = 0; k < p; ++k) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = fma(Ss[r[i] * p + k], Ts[k * m + c[i]], acc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (o0 + i * (int)blockDim.x >= n * m) break;
+            target<walk_step(V, S).quad[0], walk_step(V, S).sign[0], walk_step(V, S).first[0]>(Cs, r[i], c[i], n, m,
+                                                                                              acc[i]);
+            if constexpr (nt > 1)
+                target<walk_step(V, S).quad[1], walk_step(V, S).sign[1], walk_step(V, S).first[1]>(Cs, r[i], c[i], n,
+                                                                                                  m, acc[i]);
+            if constexpr (nt > 2)
+                target<walk_step(V, S).quad[2], walk_step(V, S).sign[2], walk_step(V, S).first[2]>(Cs, r[i], c[i], n,
+                                                                                                  m, acc[i]);
+            if constexpr (nt > 3)
+                target<walk_step(V, S).quad[3], walk_step(V, S).sign[3], walk_step(V, S).first[3]>(Cs, r[i], c[i], n,
+                                                                                                  m, acc[i]);
+        }
     }
     __syncthreads();
     if constexpr (S < 6) leaf_level_step<V, S + 1>(As, Bs, Cs, Ss, Ts, n, p, m);
@@ -585,10 +613,12 @@ int strassen_plan(int variant, int64_t N, int64_t P, int64_t M, int32_t cutoff, 
             while (ceil_div(X, (int64_t)1 << d) > cutoff) ++d;
         } else if (!tuned_strassen_depth(variant, N, P, M, &d)) {
             // untuned default: the paper's depth floor(log2) - 4, taken on the
-            // smallest dimension (blocks of 16 to 31 there), fastest on GB300
+            // smallest dimension (blocks of 16 to 31 there), fastest on GB300;
+            // at most kWinogradSafeDepth levels of Winograd's variant
             int lg = -1;
             for (int64_t t = std::min(N, std::min(P, M)); t > 0; t >>= 1) ++lg;
             d = std::max(0, lg - 4);
+            if (variant == 1) d = std::min(d, kWinogradSafeDepth);
         }
         const int64_t q = (int64_t)1 << d;
         *depth = d;

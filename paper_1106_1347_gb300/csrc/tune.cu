@@ -1,7 +1,9 @@
 // Autotuner (not in the paper, which fixes its choices by rule):
 //   - the Strassen recursion depth per (variant, shape bucket), chosen by
-//     timing every depth whose blocks stay at least 16 wide, consulted by
-//     mm_strassen / mm_strassen_winograd for cutoff == -1;
+//     timing every depth whose blocks stay at least 16 wide (at most
+//     kWinogradSafeDepth levels of Winograd's variant, whose error grows
+//     about twice per level), consulted by mm_strassen / mm_strassen_winograd
+//     for cutoff == -1;
 //   - for the FP64-accurate emulated product, per (shape bucket, tier): the
 //     slice format (BF16 or FP8-E4M3, each with the slice count the tier
 //     needs) and the number of Strassen-Winograd levels over it, chosen by
@@ -14,7 +16,8 @@
 // MM_TUNE_CACHE names a file loaded at first use.  Without an entry the
 // choices fall back to models: the paper's depth floor(log2 X) - 4 for
 // Strassen; for the emulated product the format whose slice pairs cost less at
-// the nominal rates (an FP8 pair costs half a BF16 one) and the measured
+// the nominal rates (an FP8 pair costs half a BF16 one, three quarters past 8
+// slices) and the measured
 // level crossovers of strassen_emulated_levels.
 #include <math.h>
 #include <stdio.h>
@@ -74,7 +77,8 @@ int load_file(const char *path) {
             ++n;
         } else if (std::string(kind) == "emulated" &&
                    sscanf(line, "%*s %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6]) == 7) {
-            if ((a[4] != MM_SLICE_BF16 && a[4] != MM_SLICE_FP8E4M3) || a[5] < 1 || a[5] > 8 || a[6] < 0 || a[6] > 4)
+            if ((a[4] != MM_SLICE_BF16 && a[4] != MM_SLICE_FP8E4M3) || a[5] < 1 || a[5] > (a[4] ? 10 : 8) ||
+                a[6] < 0 || a[6] > 4)
                 continue;
             g_emu[EmuKey{a[0], a[1], a[2], a[3]}] = EmuChoice{a[4], a[5], a[6], 0.0};
             ++n;
@@ -99,14 +103,19 @@ int max_tuned_depth(int64_t N, int64_t P, int64_t M) {
     return d;
 }
 
-// The model's emulated choice for a tier (no table entry).
+// The model's emulated choice for a tier (no table entry): the format whose
+// slice pairs cost less, an FP8-E4M3 pair at half a BF16 pair up to 8 slices
+// (both issue N = 128 MMAs) and at three quarters past 8 (N = 64 MMAs on
+// 32-column accumulators, which issue at about 2/3 of the N = 128 rate).
 int model_emulated(int64_t N, int64_t P, int64_t M, double tier, int *kind, int *slices, int *levels) {
     const int sb = mm::emulated_slices(MM_SLICE_BF16, 0, tier);
-    if (sb < 0) return sb;
     const int s8 = mm::emulated_slices(MM_SLICE_FP8E4M3, 0, tier);
+    if (sb < 0 && s8 < 0) return sb;
     *kind = MM_SLICE_BF16;
     *slices = sb;
-    if (s8 > 0 && s8 * (s8 + 1) < 2 * sb * (sb + 1)) {
+    const double cost8 = s8 > 0 ? s8 * (s8 + 1) * (s8 > 8 ? 0.75 : 0.5) : 1e30;
+    const double cost16 = sb > 0 ? (double)sb * (sb + 1) : 1e30;
+    if (cost8 < cost16) {
         *kind = MM_SLICE_FP8E4M3;
         *slices = s8;
     }
@@ -190,7 +199,9 @@ int mm_tune_strassen(int32_t variant, int64_t N, int64_t P, int64_t M, const dou
     cudaEventCreate(&e1);
     int best = -1;
     float best_t = 0.f;
-    for (int d = 0; d <= max_tuned_depth(N, P, M); ++d) {
+    const int dmax = variant == 1 ? std::min(max_tuned_depth(N, P, M), mm::kWinogradSafeDepth)
+                                  : max_tuned_depth(N, P, M);
+    for (int d = 0; d <= dmax; ++d) {
         const int64_t q = (int64_t)1 << d;
         const int64_t Np = mm::ceil_div(N, q) * q, Pp = mm::ceil_div(P, q) * q, Mp = mm::ceil_div(M, q) * q;
         if (mm::strassen_ws_bytes(variant, d, Np, Pp, Mp) > ws_bytes) continue;

@@ -39,10 +39,10 @@ ROWS = np.array([0, 1, 127, 128, 4095, 5000, 8190, 8191])
 COLS = np.concatenate([np.arange(0, 64), np.arange(4032, 4160), np.arange(8128, 8192)])
 
 
-@pytest.mark.parametrize("kind,s", [(0, 8), (1, 6)])
+@pytest.mark.parametrize("kind,s", [(0, 8), (1, 6), (1, 10)])
 def test_emulated_8192_cubed_sampled_bit_exact(mm, orc, kind, s):
     """8192^3, log-uniform entries (the bench workload): sampled entries equal
-    the oracle's definition bit for bit (BF16 8 slices; FP8-E4M3 6 slices)."""
+    the oracle's definition bit for bit (BF16 8 slices; FP8-E4M3 6 and 10)."""
     a = S.loguniform(8192, 8192, S.stream_seed(3, 0))
     b = S.loguniform(8192, 8192, S.stream_seed(3, 1))
     c = mm.emulated(_dev(a), _dev(b), nslices=s, kind=kind)

@@ -333,9 +333,10 @@ def test_emulated_extreme_digit_sums(mm, orc):
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (5, 3, 7), (128, 64, 64), (129, 65, 65), (200, 333, 150),
                                    (256, 1100, 130)])
-@pytest.mark.parametrize("s", [8, 6, 3, 1])
+@pytest.mark.parametrize("s", [10, 9, 8, 6, 3, 1])
 def test_emulated_fp8_bit_exact_vs_oracle(mm, orc, shape, s):
-    """FP8-E4M3 slices hold balanced base-2^5 digits: the same definition with beta = 5."""
+    """FP8-E4M3 slices hold balanced base-2^5 digits: the same definition with
+    beta = 5 (9 and 10 slices run on 32-column tiles and accumulators)."""
     a, b = pair(*shape, "log", 40 + s)
     got = host(mm.emulated(dev(a), dev(b), nslices=s, kind=mm.SLICE_FP8E4M3))
     assert np.array_equal(got, orc.split_product(a, b, 5, s))
@@ -355,23 +356,29 @@ def test_emulated_fp8_tiers(mm, orc):
     got = host(mm.emulated(dev(a), dev(b), tier=1e-6, kind=mm.SLICE_FP8E4M3))
     assert orc.rel_inf_error(got, truth, a, b) <= 1e-6
     assert mm.emulated_slices(tier=1e-6, kind=mm.SLICE_FP8E4M3) == 6
-    with pytest.raises(mm.MMError):  # 1e-14 needs 12 FP8 slices: more than the 8 accumulators
+    # 1e-12 needs ceil((log2(1e12) + 9) / 5) = 10 slices, the most the FP8 kernel holds
+    assert mm.emulated_slices(tier=1e-12, kind=mm.SLICE_FP8E4M3) == 10
+    got = host(mm.emulated(dev(a), dev(b), tier=1e-12, kind=mm.SLICE_FP8E4M3))
+    assert orc.rel_inf_error(got, truth, a, b) <= 1e-12
+    with pytest.raises(mm.MMError):  # 1e-14 needs 12 FP8 slices: more than the 10 accumulators
         mm.emulated(dev(a), dev(b), tier=1e-14, kind=mm.SLICE_FP8E4M3)
 
 
-def test_emulated_fp8_extreme_digit_sums(mm, orc):
+@pytest.mark.parametrize("s", [8, 10])
+def test_emulated_fp8_extreme_digit_sums(mm, orc, s):
     """Every base-2^5 digit at the split's extreme (-15 on top, -16 below), rows
-    of alternating sign and P past the exact length of diagonal 7 (8192 K for 8
-    slices): the accumulators run whole chunks at FP32's exact-integer edge."""
-    v = 15 * 2 ** 35 + 16 * sum(2 ** (5 * t) for t in range(7))
-    x = -float(v) * 2.0 ** -39
-    assert x * 2.0 ** 39 == -v
+    of alternating sign and P past the exact length of the last diagonal (8192 K
+    for 8 slices, 6553 K for 10): the accumulators run whole chunks at FP32's
+    exact-integer edge."""
+    v = 15 * 2 ** (5 * (s - 1)) + 16 * sum(2 ** (5 * t) for t in range(s - 1))
+    x = -float(v) * 2.0 ** -(5 * s - 1)
+    assert x * 2.0 ** (5 * s - 1) == -v
     n, p, m = 130, 9000, 70
     sign = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)[:, None]
     a = np.full((n, p), x) * sign
     b = np.full((p, m), x)
-    got = host(mm.emulated(dev(a), dev(b), nslices=8, kind=mm.SLICE_FP8E4M3))
-    assert np.array_equal(got, orc.split_product(a, b, 5, 8))
+    got = host(mm.emulated(dev(a), dev(b), nslices=s, kind=mm.SLICE_FP8E4M3))
+    assert np.array_equal(got, orc.split_product(a, b, 5, s))
 
 
 def test_emulated_fp8_group_matches_single_calls(mm, orc):
@@ -379,9 +386,10 @@ def test_emulated_fp8_group_matches_single_calls(mm, orc):
     hostpairs = [(S.loguniform(n, p, S.stream_seed(6, 50 + i)), S.loguniform(p, m, S.stream_seed(6, 60 + i)))
                  for i, (n, p, m) in enumerate(shapes)]
     pairs = [(dev(a), dev(b)) for a, b in hostpairs]
-    outs = mm.emulated_group(pairs, nslices=5, kind=mm.SLICE_FP8E4M3)
-    for (a, b), c in zip(hostpairs, outs):
-        assert np.array_equal(host(c), orc.split_product(a, b, 5, 5))
+    for s in (5, 10):
+        outs = mm.emulated_group(pairs, nslices=s, kind=mm.SLICE_FP8E4M3)
+        for (a, b), c in zip(hostpairs, outs):
+            assert np.array_equal(host(c), orc.split_product(a, b, 5, s))
 
 
 # ------------------------------------------------- host-operand pipeline

@@ -70,3 +70,7 @@ def test_untuned_strassen_default_is_the_papers_depth(lib):
     for n, depth in ((1024, 6), (4096, 8), (300, 4)):
         assert lib.mm_strassen_workspace_bytes(n, n, n, -1) == \
             lib.mm_strassen_workspace_bytes(n, n, n, -(-n // (1 << depth)))
+    # Winograd's variant stops at 6 levels (its error about doubles per level)
+    for n, depth in ((1024, 6), (8192, 6), (300, 4)):
+        assert lib.mm_strassen_winograd_workspace_bytes(n, n, n, -1) == \
+            lib.mm_strassen_winograd_workspace_bytes(n, n, n, -(-n // (1 << depth)))
