@@ -377,6 +377,14 @@ def grouped_vs_single(dev, count=256):
     outs = [torch.empty((r["N"], r["M"]), dtype=torch.float64, device=dev) for r in trace]
     flop = sum(2.0 * r["N"] * r["P"] * r["M"] for r in trace)
     ms_group = timed(lambda: mm.emulated_group(pairs, nslices=8, outs=outs), 3)
+    with mm.profile() as prof:  # per-kernel device time of one more grouped launch
+        mm.emulated_group(pairs, nslices=8, outs=outs)
+        torch.cuda.synchronize()
+    kernels = {k: round(v[1] / max(v[0], 1), 4) for k, v in prof.stats.items()}
+    # Useful and padded work of the slice product: 36 pair products per 2NPM, tiles of
+    # 128 x 64 outputs and K-blocks of 32.
+    padded = sum(2.0 * -(-r["N"] // 128) * 128 * -(-r["M"] // 64) * 64 * -(-r["P"] // 32) * 32 for r in trace)
+    gemm_ms = kernels.get("emu_group_slice_gemm_tcgen05")
 
     def singles():
         for (ta, tb), c in zip(pairs, outs):
@@ -384,8 +392,44 @@ def grouped_vs_single(dev, count=256):
 
     ms_single = timed(singles, 3)
     return {"problems": count, "dims": "N, P, M log-uniform [32, 4096]", "slices": 8, "gflop": flop / 1e9,
-            "grouped": {"ms": ms_group, "tflops": flop / (ms_group * 1e-3) / 1e12},
+            "grouped": {"ms": ms_group, "tflops": flop / (ms_group * 1e-3) / 1e12, "kernel_ms": kernels,
+                        "slice_gemm_pair_tflops_useful": (36 * flop / (gemm_ms * 1e-3) / 1e12) if gemm_ms else None,
+                        "slice_gemm_pair_tflops_padded": (36 * padded / (gemm_ms * 1e-3) / 1e12) if gemm_ms else None,
+                        "padding_efficiency": flop / padded},
             "one_call_each": {"ms": ms_single, "tflops": flop / (ms_single * 1e-3) / 1e12}}
+
+
+def autotuner(dev):
+    """The library's autotuner on a few shape buckets: the Strassen depth at
+    4096^3 for both variants, and the emulated product's format x Strassen-
+    Winograd levels for several tiers, against the models' choices (the tuned
+    table lives in this process only)."""
+    import torch
+
+    import paper_1106_1347_gb300 as mm
+    import synthetic as S
+
+    mm.tune_clear()
+    out = {"strassen": {}, "emulated": []}
+    a = torch.from_numpy(S.uniform(4096, 4096, S.stream_seed(1, 0))).to(dev)
+    b = torch.from_numpy(S.uniform(4096, 4096, S.stream_seed(1, 1))).to(dev)
+    for variant, name in ((0, "strassen"), (1, "strassen_winograd")):
+        depth, ms = mm.tune_strassen(a, b, variant=variant)
+        out["strassen"][name] = {"n": 4096, "depth": depth, "ms": ms, "tflops": 2.0 * 4096 ** 3 / (ms * 1e-3) / 1e12}
+    del a, b
+    for n, tier in ((1024, 1e-14), (1024, 1e-6), (4096, 1e-9), (4096, 1e-12), (8192, 1e-14)):
+        a = torch.from_numpy(S.loguniform(n, n, S.stream_seed(3, 0))).to(dev)
+        b = torch.from_numpy(S.loguniform(n, n, S.stream_seed(3, 1))).to(dev)
+        model, _ = mm.emulated_choice(n, n, n, tier)
+        kind, slices, levels, ms = mm.tune_emulated(a, b, tier=tier)
+        out["emulated"].append({"n": n, "tier": tier, "tuned": {"format": kind, "slices": slices, "levels": levels},
+                                "ms": ms, "tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+                                "model": {"format": model[0], "slices": model[1], "levels": model[2]}})
+        del a, b
+        torch.cuda.empty_cache()
+    mm.tune_clear()
+    out["formats"] = "0 = BF16 slices, 1 = FP8-E4M3 slices"
+    return out
 
 
 def badly_scaled_errors(dev, n=2048, nrows=64):
@@ -780,6 +824,9 @@ def compact_line(core, sections):
     if gv:
         summary["grouped_256"] = {"tflops": rnd(get(gv, "grouped", "tflops")),
                                   "one_call_each_tflops": rnd(get(gv, "one_call_each", "tflops"))}
+    at = sections.get("autotuner")
+    if at:
+        summary["autotuner"] = {k: v.get("depth") for k, v in at.get("strassen", {}).items()}
     sh = sections.get("shape_4096x16384x4096")
     if sh:
         summary["shape_4096x16384x4096_tflops"] = rnd(sh.get("tflops"))
@@ -969,6 +1016,7 @@ def run_ours(args):
             out["shape_4096x16384x4096"] = tall_inner_shape(dev)
             out["badly_scaled_2048"] = badly_scaled_errors(dev)
             out["grouped_vs_single"] = grouped_vs_single(dev)
+            out["autotuner"] = autotuner(dev)
             out["strassen_over_emulated"] = strassen_over_emulated(ta, tb, a, b, norm_a, norm_b, rows, truth)
             torch.cuda.empty_cache()
 

@@ -223,6 +223,37 @@ __global__ void __launch_bounds__(256) combine_kernel(const double *__restrict__
     }
 }
 
+// Naive block product into registers: thread t owns outputs o0 + t,
+// o0 + t + T, ..., o0 + t + (PER - 1) T of the n x m block (T threads; an
+// index past the block is clamped to its last output and not stored by the
+// caller), each summing its k in order with FMA; the PER chains are
+// independent, which keeps the FP64 pipe fed with few CTAs per SM.
+template <int PER>
+__device__ __forceinline__ void block_dot(const double *X, const double *Y, int n, int p, int m, int o0,
+                                          int (&r)[4], int (&c)[4], double (&acc)[4]) {
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int o = min(o0 + (int)threadIdx.x + i * (int)blockDim.x, n * m - 1);
+        r[i] = o / m, c[i] = o - (o / m) * m, acc[i] = 0.0;
+    }
+    for (int k = 0; k < p; ++k) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) acc[i] = fma(X[r[i] * p + k], Y[k * m + c[i]], acc[i]);
+    }
+}
+
+// Outputs o0 .. o0 + 4 T - 1 (or to the block's end): PER = the chains a
+// thread needs for them, 1..4.  Returns PER.
+__device__ __forceinline__ int block_dot_any(const double *X, const double *Y, int n, int p, int m, int o0,
+                                            int (&r)[4], int (&c)[4], double (&acc)[4]) {
+    const int per = min(4, (n * m - o0 + (int)blockDim.x - 1) / (int)blockDim.x);
+    if (per <= 1) block_dot<1>(X, Y, n, p, m, o0, r, c, acc);
+    else if (per == 2) block_dot<2>(X, Y, n, p, m, o0, r, c, acc);
+    else if (per == 3) block_dot<3>(X, Y, n, p, m, o0, r, c, acc);
+    else block_dot<4>(X, Y, n, p, m, o0, r, c, acc);
+    return per;
+}
+
 // Naive block products (blocks of at most 64): node z's n x p and p x m blocks
 // are staged in shared memory, each output sums its k in order with FMA.
 __global__ void __launch_bounds__(256) leaf_naive_kernel(const Mat A, const Mat B, const Out C, int64_t nodes, int n,
@@ -233,21 +264,14 @@ __global__ void __launch_bounds__(256) leaf_naive_kernel(const Mat A, const Mat 
         for (int e = threadIdx.x; e < n * p; e += blockDim.x) As[e] = at(A, z, e / p, e % p);
         for (int e = threadIdx.x; e < p * m; e += blockDim.x) Bs[e] = at(B, z, e / m, e % m);
         __syncthreads();
-        for (int o0 = threadIdx.x; o0 < n * m; o0 += 4 * blockDim.x) {  // four FMA chains per thread
+        // Up to 64 x 64 outputs: groups of 4 x 256, each thread up to four chains at a time.
+        for (int o0 = 0; o0 < n * m; o0 += 4 * (int)blockDim.x) {
             int r[4], c[4];
             double acc[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int o = min(o0 + i * (int)blockDim.x, n * m - 1);
-                r[i] = o / m, c[i] = o - (o / m) * m, acc[i] = 0.0;
-            }
-            for (int k = 0; k < p; ++k) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) acc[i] = fma(As[r[i] * p + k], Bs[k * m + c[i]], acc[i]);
-            }
+            const int per = block_dot_any(As, Bs, n, p, m, o0, r, c, acc);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (o0 + i * (int)blockDim.x < n * m) put(C, z, r[i], c[i], acc[i]);
+                if (i < per && o0 + (int)threadIdx.x + i * (int)blockDim.x < n * m) put(C, z, r[i], c[i], acc[i]);
         }
         __syncthreads();
     }
@@ -276,85 +300,81 @@ __host__ __device__ constexpr Step walk_step(int V, int s) {
                               : Step{6, 1, {2, 0, 0, 0}, {1, 0, 0, 0}, {0, 0, 0, 0}});   // H7: C21 +=
 }
 
-// C block `Q` at (r, c) := +-h (first touch) or C + (+-h).
+// C block `Q` of output i := +-h (first touch) or C + (+-h), in registers.
 template <int Q, int kSign, int kFirst>
-__device__ __forceinline__ void target(double *Cs, int r, int c, int n, int m, double h) {
-    double &dst = Cs[(r + (Q >> 1) * n) * (2 * m) + c + (Q & 1) * m];
+__device__ __forceinline__ void target(double (&cq)[4][4], int i, double h) {
     const double v = kSign > 0 ? h : -h;
-    dst = kFirst ? v : add(dst, v);
+    cq[i][Q] = kFirst ? v : add(cq[i][Q], v);
 }
 
-template <int V, int S>
-__device__ __forceinline__ void leaf_level_step(const double *As, const double *Bs, double *Cs, double *Ss,
-                                                double *Ts, int n, int p, int m) {
+// Step S of the walk: the operand sums of its product into shared memory, the
+// naive product of the n x p and p x m blocks, and the product added into its
+// C blocks, which each thread keeps in registers for its outputs (a thread
+// owns the same positions in every step).
+template <int V, int S, int PER>
+__device__ __forceinline__ void leaf_level_step(const double *As, const double *Bs, double *Ss, double *Ts,
+                                                double (&cq)[4][4], int (&r)[4], int (&c)[4], int n, int p, int m) {
     constexpr int child = walk_step(V, S).child, nt = walk_step(V, S).nt;
     const int P2 = 2 * p, M2 = 2 * m;
     for (int e = threadIdx.x; e < n * p; e += blockDim.x) {
-        const int r = e / p, c = e - (e / p) * p;
+        const int rr = e / p, cc = e - (e / p) * p;
         double o[7];
-        children<V, true>(As[r * P2 + c], As[r * P2 + c + p], As[(r + n) * P2 + c], As[(r + n) * P2 + c + p], o);
+        children<V, true>(As[rr * P2 + cc], As[rr * P2 + cc + p], As[(rr + n) * P2 + cc],
+                          As[(rr + n) * P2 + cc + p], o);
         Ss[e] = o[child];
     }
     for (int e = threadIdx.x; e < p * m; e += blockDim.x) {
-        const int r = e / m, c = e - (e / m) * m;
+        const int rr = e / m, cc = e - (e / m) * m;
         double o[7];
-        children<V, false>(Bs[r * M2 + c], Bs[r * M2 + c + m], Bs[(r + p) * M2 + c], Bs[(r + p) * M2 + c + m], o);
+        children<V, false>(Bs[rr * M2 + cc], Bs[rr * M2 + cc + m], Bs[(rr + p) * M2 + cc],
+                           Bs[(rr + p) * M2 + cc + m], o);
         Ts[e] = o[child];
     }
     __syncthreads();
-    // Four outputs per thread at once: four independent FMA chains keep the
-    // FP64 pipe fed even with one CTA per SM (blocks of 32).
-    for (int o0 = threadIdx.x; o0 < n * m; o0 += 4 * blockDim.x) {
-        int r[4], c[4];
-        double acc[4];
+    double acc[4];
+    block_dot<PER>(Ss, Ts, n, p, m, 0, r, c, acc);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int o = min(o0 + i * (int)blockDim.x, n * m - 1);  // past the end: a duplicate, not stored
-            r[i] = o / m, c[i] = o - (o / m) * m, acc[i] = 0.0;
-        }
-        for (int k = 0; k < p; ++k) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] = fma(Ss[r[i] * p + k], Ts[k * m + c[i]], acc[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (o0 + i * (int)blockDim.x >= n * m) break;
-            target<walk_step(V, S).quad[0], walk_step(V, S).sign[0], walk_step(V, S).first[0]>(Cs, r[i], c[i], n, m,
-                                                                                              acc[i]);
-            if constexpr (nt > 1)
-                target<walk_step(V, S).quad[1], walk_step(V, S).sign[1], walk_step(V, S).first[1]>(Cs, r[i], c[i], n,
-                                                                                                  m, acc[i]);
-            if constexpr (nt > 2)
-                target<walk_step(V, S).quad[2], walk_step(V, S).sign[2], walk_step(V, S).first[2]>(Cs, r[i], c[i], n,
-                                                                                                  m, acc[i]);
-            if constexpr (nt > 3)
-                target<walk_step(V, S).quad[3], walk_step(V, S).sign[3], walk_step(V, S).first[3]>(Cs, r[i], c[i], n,
-                                                                                                  m, acc[i]);
-        }
+    for (int i = 0; i < PER; ++i) {
+        target<walk_step(V, S).quad[0], walk_step(V, S).sign[0], walk_step(V, S).first[0]>(cq, i, acc[i]);
+        if constexpr (nt > 1)
+            target<walk_step(V, S).quad[1], walk_step(V, S).sign[1], walk_step(V, S).first[1]>(cq, i, acc[i]);
+        if constexpr (nt > 2)
+            target<walk_step(V, S).quad[2], walk_step(V, S).sign[2], walk_step(V, S).first[2]>(cq, i, acc[i]);
+        if constexpr (nt > 3)
+            target<walk_step(V, S).quad[3], walk_step(V, S).sign[3], walk_step(V, S).first[3]>(cq, i, acc[i]);
     }
-    __syncthreads();
-    if constexpr (S < 6) leaf_level_step<V, S + 1>(As, Bs, Cs, Ss, Ts, n, p, m);
+    __syncthreads();  // Ss and Ts are rewritten by the next step
+    if constexpr (S < 6) leaf_level_step<V, S + 1, PER>(As, Bs, Ss, Ts, cq, r, c, n, p, m);
 }
 
 // The last recursion level with naive products of blocks <= 32, in shared
 // memory: node z's operands are 2n x 2p and 2p x 2m, its result 2n x 2m.
-template <int V>
-__global__ void __launch_bounds__(256) leaf_level_kernel(const Mat A, const Mat B, const Out C, int64_t nodes,
-                                                         int n, int p, int m) {
+// PER = ceil(n m / 256) outputs per thread (1..4), a template parameter so
+// small blocks (the paper's 17 to 22) keep few registers and many CTAs per SM.
+template <int V, int PER>
+__global__ void __launch_bounds__(256, PER <= 2 ? 4 : 2)
+    leaf_level_kernel(const Mat A, const Mat B, const Out C, int64_t nodes, int n, int p, int m) {
     extern __shared__ double sm[];
-    double *As = sm, *Bs = As + 4 * n * p, *Cs = Bs + 4 * p * m, *Ss = Cs + 4 * n * m, *Ts = Ss + n * p;
+    double *As = sm, *Bs = As + 4 * n * p, *Ss = Bs + 4 * p * m, *Ts = Ss + n * p;
     const int N2 = 2 * n, P2 = 2 * p, M2 = 2 * m;
     for (int64_t z = blockIdx.x; z < nodes; z += gridDim.x) {
         for (int e = threadIdx.x; e < N2 * P2; e += blockDim.x) As[e] = at(A, z, e / P2, e % P2);
         for (int e = threadIdx.x; e < P2 * M2; e += blockDim.x) Bs[e] = at(B, z, e / M2, e % M2);
         __syncthreads();
-        leaf_level_step<V, 0>(As, Bs, Cs, Ss, Ts, n, p, m);
-        for (int e = threadIdx.x; e < N2 * M2; e += blockDim.x) put(C, z, e / M2, e % M2, Cs[e]);
-        __syncthreads();
+        double cq[4][4];
+        int r[4], c[4];
+        leaf_level_step<V, 0, PER>(As, Bs, Ss, Ts, cq, r, c, n, p, m);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            if ((int)threadIdx.x + i * (int)blockDim.x >= n * m) break;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) put(C, z, r[i] + (q >> 1) * n, c[i] + (q & 1) * m, cq[i][q]);
+        }
+        // the next node's staging waits at the first step's barrier
     }
 }
 
-size_t leaf_level_smem(int n, int p, int m) { return (size_t)(5 * n * p + 5 * p * m + 4 * n * m) * 8; }
+size_t leaf_level_smem(int n, int p, int m) { return (size_t)(5 * n * p + 5 * p * m) * 8; }
 size_t leaf_naive_smem(int n, int p, int m) { return (size_t)(n * p + p * m) * 8; }
 
 // ------------------------------------------------------------------ host plan
@@ -487,11 +507,12 @@ cudaError_t leaf_smem_attributes() {
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
         const int most = (int)leaf_level_smem(32, 32, 32);
-        err = cudaFuncSetAttribute((const void *)leaf_level_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   most);
-        if (err == cudaSuccess)
-            err = cudaFuncSetAttribute((const void *)leaf_level_kernel<1>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        const void *fns[8] = {(const void *)leaf_level_kernel<0, 1>, (const void *)leaf_level_kernel<0, 2>,
+                              (const void *)leaf_level_kernel<0, 3>, (const void *)leaf_level_kernel<0, 4>,
+                              (const void *)leaf_level_kernel<1, 1>, (const void *)leaf_level_kernel<1, 2>,
+                              (const void *)leaf_level_kernel<1, 3>, (const void *)leaf_level_kernel<1, 4>};
+        for (int i = 0; i < 8 && err == cudaSuccess; ++i)
+            err = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         if (err == cudaSuccess)
             err = cudaFuncSetAttribute((const void *)leaf_naive_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)leaf_naive_smem(64, 64, 64));
@@ -549,15 +570,23 @@ int run_sub(const Run &r, const Sub &s, const Mat &A, const Mat &B, const Out &C
         const int sh = level ? e + 1 : e;
         const int n = (int)(s.n0 >> sh), p = (int)(s.p0 >> sh), m = (int)(s.m0 >> sh);
         const size_t smem = level ? leaf_level_smem(n, p, m) : leaf_naive_smem(n, p, m);
-        const int per_sm = std::max(1, std::min(8, (int)(200000 / std::max<size_t>(smem, 1))));
+        const int per_sm = std::max(2, std::min(8, (int)(200000 / std::max<size_t>(smem, 1))));
         const unsigned g = (unsigned)std::min<int64_t>(nodes, (int64_t)per_sm * mm::sm_count());
         int rc = mm::launch(level ? "strassen_leaf_level" : "strassen_leaf_naive", r.st, [&] {
             if (!level)
                 leaf_naive_kernel<<<g, 256, smem, r.st>>>(curA, curB, outE, nodes, n, p, m);
-            else if (r.V == 0)
-                leaf_level_kernel<0><<<g, 256, smem, r.st>>>(curA, curB, outE, nodes, n, p, m);
-            else
-                leaf_level_kernel<1><<<g, 256, smem, r.st>>>(curA, curB, outE, nodes, n, p, m);
+            else {
+                const int per = (n * m + 255) / 256;  // outputs per thread, 1..4 (blocks <= 32 x 32)
+#define MM_LEAF(V_, P_) leaf_level_kernel<V_, P_><<<g, 256, smem, r.st>>>(curA, curB, outE, nodes, n, p, m)
+                if (r.V == 0) {
+                    if (per <= 1) MM_LEAF(0, 1); else if (per == 2) MM_LEAF(0, 2); else if (per == 3) MM_LEAF(0, 3);
+                    else MM_LEAF(0, 4);
+                } else {
+                    if (per <= 1) MM_LEAF(1, 1); else if (per == 2) MM_LEAF(1, 2); else if (per == 3) MM_LEAF(1, 3);
+                    else MM_LEAF(1, 4);
+                }
+#undef MM_LEAF
+            }
         });
         if (rc) return rc;
     }
