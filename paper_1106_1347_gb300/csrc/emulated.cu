@@ -260,22 +260,28 @@ __device__ __forceinline__ bool rows_aligned(const double *a0, const OpTerms &ex
 }
 
 constexpr int kRowThreads = 256;
-// Rows of at most this many (padded) elements are split by one warp each, 8
-// rows per CTA; longer ones by a whole CTA.
-constexpr int64_t kWarpRowMax = 1024;
+// Rows of at most kQuarterRowMax (padded) elements are split by 8 threads each
+// (4 rows per warp, 32 per CTA), rows of at most kWarpRowMax by one warp each
+// (8 rows per CTA), longer ones by a whole CTA: every thread has 8 elements
+// of its row to load at a time, whatever the row length.
+constexpr int64_t kQuarterRowMax = 64, kWarpRowMax = 1024;
 
-// One row of A by T threads (a whole CTA of 256, or one warp): max |A_ik| by
+// One row of A by T threads (a whole CTA of 256, one warp, or 8 lanes of one):
+// max |A_ik| by
 // integer max on the bit patterns, then the digits, written as slices
 // [s][Nr][Pp] (BF16 or FP8-E4M3); columns [P, Pp) get zero digits so every
 // K-block read is defined.  The digit pass reads the row again, from L2: with
 // one row per CTA only a few rows per SM are in flight (about 40 MB over the
 // GPU at 8192 columns), so A crosses HBM once.  `tid` is the thread's index
 // among the T; with T = 256 `red` is 8 words of shared memory (unused for a
-// warp).
+// warp).  With T = 8 the warp's four groups reduce among themselves, so every
+// lane of the warp must call it: a group past the last row passes valid =
+// false and only takes part in the reduction.
 template <int KIND, int T, bool kExpr = false>
-__device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int tid, unsigned long long *red) {
-    const int64_t off = row * p.lda;
-    const int64_t P = p.P, Pp = p.Pp;
+__device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int tid, unsigned long long *red,
+                                          bool valid = true) {
+    const int64_t off = valid ? row * p.lda : 0;
+    const int64_t P = valid ? p.P : 0, Pp = valid ? p.Pp : 0;
     const int s = p.s;
     const bool vec = kExpr ? rows_aligned(p.A, p.ex, off) : (((uintptr_t)(p.A + off)) & 15) == 0;
     unsigned long long mx = 0;
@@ -286,7 +292,7 @@ __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int tid,
         for (int u = 0; u < 8; ++u) mx = umax64(mx, absbits(x[u]));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+    for (int o = (T < 32 ? T : 32) / 2; o > 0; o >>= 1)  // within the T (or 32) lanes of the row
         mx = umax64(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mx, o));
     if (T > 32) {
         if ((tid & 31) == 0) red[tid >> 5] = mx;
@@ -296,11 +302,11 @@ __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int tid,
         __syncthreads();  // `red` is reused by the next row
     }
     const int e = frexp_exp_bits(mx);
-    if (tid == 0) p.ea[row] = e;
+    if (tid == 0 && valid) p.ea[row] = e;
     constexpr int beta = fmt_beta(KIND), es = fmt_esize(KIND);
     const int sh = beta * s - 1 - e;
-    const int64_t stride = (int64_t)p.Nr * Pp * es;
-    unsigned char *row0 = p.slices + row * Pp * es;
+    const int64_t stride = (int64_t)p.Nr * p.Pp * es;
+    unsigned char *row0 = p.slices + (valid ? row : 0) * p.Pp * es;
     // Pp is a multiple of 8 (BF16) or 16 (E4M3) elements: a group of eight
     // starting before Pp ends by Pp.
     for (int64_t c = 8 * tid; c < Pp; c += 8 * T) {
@@ -324,6 +330,14 @@ template <int KIND>
 __global__ void __launch_bounds__(kRowThreads, 4) split_rows_warp_kernel(const SplitA p) {
     const int64_t row = (int64_t)blockIdx.x * (kRowThreads / 32) + (threadIdx.x >> 5);
     if (row < p.N) split_row<KIND, 32>(p, row, threadIdx.x & 31, nullptr);
+}
+
+// Very short rows (Pp <= kQuarterRowMax): 8 threads per row, 32 rows per CTA.
+template <int KIND>
+__global__ void __launch_bounds__(kRowThreads, 4) split_rows_quarter_kernel(const SplitA p) {
+    const int64_t row = (int64_t)blockIdx.x * (kRowThreads / 8) + (threadIdx.x >> 3);
+    if (((int64_t)blockIdx.x * (kRowThreads / 8) + ((threadIdx.x & ~31u) >> 3)) >= p.N) return;  // whole warp
+    split_row<KIND, 8>(p, row, threadIdx.x & 7, nullptr, row < p.N);
 }
 
 
@@ -428,7 +442,11 @@ __global__ void __launch_bounds__(kRowThreads, 4) group_split_rows_kernel(const 
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const int g = find_problem(begin, hdr->count, u);
         const SplitA &p = tab[g].spa;
-        if (p.Pp <= kWarpRowMax) {  // 8 rows per unit, one per warp (the whole CTA takes this branch)
+        if (p.Pp <= kQuarterRowMax) {  // 32 rows per unit, 8 threads per row (the whole CTA takes this branch)
+            const int64_t row = (u - begin[g]) * (kRowThreads / 8) + (threadIdx.x >> 3);
+            const int64_t warp_row0 = (u - begin[g]) * (kRowThreads / 8) + ((threadIdx.x & ~31u) >> 3);
+            if (warp_row0 < p.N) split_row<KIND, 8, kExpr>(p, row, threadIdx.x & 7, nullptr, row < p.N);
+        } else if (p.Pp <= kWarpRowMax) {  // 8 rows per unit, one per warp
             const int64_t row = (u - begin[g]) * (kRowThreads / 32) + (threadIdx.x >> 5);
             if (row < p.N) split_row<KIND, 32, kExpr>(p, row, threadIdx.x & 31, nullptr);
         } else {  // one row per unit
@@ -596,7 +614,13 @@ int split_a_rows(const EmuWork &w, int64_t r0, int64_t n, int64_t P, const doubl
                      w.sa + (size_t)r0 * w.L.Pp * fmt_esize(kind)};
     return mm::launch("emu_split_rows", st, [&] {
         const bool fp8 = kind == MM_SLICE_FP8E4M3;
-        if (w.L.Pp <= kWarpRowMax) {
+        if (w.L.Pp <= kQuarterRowMax) {
+            const unsigned g = (unsigned)mm::ceil_div(n, kRowThreads / 8);
+            if (fp8)
+                split_rows_quarter_kernel<MM_SLICE_FP8E4M3><<<g, kRowThreads, 0, st>>>(spa);
+            else
+                split_rows_quarter_kernel<MM_SLICE_BF16><<<g, kRowThreads, 0, st>>>(spa);
+        } else if (w.L.Pp <= kWarpRowMax) {
             const unsigned g = (unsigned)mm::ceil_div(n, kRowThreads / 32);
             if (fp8)
                 split_rows_warp_kernel<MM_SLICE_FP8E4M3><<<g, kRowThreads, 0, st>>>(spa);
@@ -958,7 +982,9 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
         if (!rc) rc = encode_slices(&e.tmB, sb, L.Mr, L.Pp, s, slice_bn(s), kind);
         if (rc) return rc;
         for (int k = 0; k < 5; ++k) begin[k][i] = units[k];
-        units[U_ROWS] += L.Pp <= kWarpRowMax ? ceil_div(q.N, kRowThreads / 32) : q.N;
+        units[U_ROWS] += L.Pp <= kQuarterRowMax ? ceil_div(q.N, kRowThreads / 8)
+                         : L.Pp <= kWarpRowMax  ? ceil_div(q.N, kRowThreads / 32)
+                                                : q.N;
         units[U_COLMAX] += ceil_div(q.M, 128) * ceil_div(q.P, 256);
         units[U_SPLITCOLS] += ceil_div(q.M, SC_J) * ceil_div(L.Pp, SC_K);
         units[U_TILES] += (int64_t)e.prm.tiles_m * e.prm.tiles_n;

@@ -228,6 +228,15 @@ __global__ void __launch_bounds__(256) combine_kernel(const double *__restrict__
 // index past the block is clamped to its last output and not stored by the
 // caller), each summing its k in order with FMA; the PER chains are
 // independent, which keeps the FP64 pipe fed with few CTAs per SM.
+template <int C>
+__device__ __forceinline__ void dot_chains(const double *X, const double *Y, int p, int m, const int (&r)[4],
+                                           const int (&c)[4], double (&acc)[4]) {
+    for (int k = 0; k < p; ++k) {
+#pragma unroll
+        for (int i = 0; i < C; ++i) acc[i] = fma(X[r[i] * p + k], Y[k * m + c[i]], acc[i]);
+    }
+}
+
 template <int PER>
 __device__ __forceinline__ void block_dot(const double *X, const double *Y, int n, int p, int m, int o0,
                                           int (&r)[4], int (&c)[4], double (&acc)[4]) {
@@ -236,10 +245,16 @@ __device__ __forceinline__ void block_dot(const double *X, const double *Y, int 
         const int o = min(o0 + (int)threadIdx.x + i * (int)blockDim.x, n * m - 1);
         r[i] = o / m, c[i] = o - (o / m) * m, acc[i] = 0.0;
     }
-    for (int k = 0; k < p; ++k) {
+    // Chains the warp needs (warp-uniform): a chain no lane of the warp owns is
+    // skipped, so the clamped duplicates cost at most part of one warp's chain.
+    const int first = o0 + (int)(threadIdx.x & ~31u);
+    int need = 1;
 #pragma unroll
-        for (int i = 0; i < PER; ++i) acc[i] = fma(X[r[i] * p + k], Y[k * m + c[i]], acc[i]);
-    }
+    for (int i = 1; i < PER; ++i) need += first + i * (int)blockDim.x < n * m ? 1 : 0;
+    if (PER >= 4 && need >= 4) dot_chains<(PER >= 4 ? 4 : 1)>(X, Y, p, m, r, c, acc);
+    else if (PER >= 3 && need == 3) dot_chains<(PER >= 3 ? 3 : 1)>(X, Y, p, m, r, c, acc);
+    else if (PER >= 2 && need == 2) dot_chains<(PER >= 2 ? 2 : 1)>(X, Y, p, m, r, c, acc);
+    else dot_chains<1>(X, Y, p, m, r, c, acc);
 }
 
 // Outputs o0 .. o0 + 4 T - 1 (or to the block's end): PER = the chains a
