@@ -65,6 +65,10 @@ def parse():
                     help="file that receives every section of the run (the printed line carries summaries)")
     ap.add_argument("--grouped-only", type=int, default=0, metavar="COUNT",
                     help="profiling runs: only the grouped launch of COUNT serving-shaped products")
+    ap.add_argument("--method", default="",
+                    help="profiling runs: one FP64 method at n = --n, a warm-up and one timed call (naive, kahan, "
+                         "naive_unrolled_4, winograd, strassen, strassen_winograd, strassen_paper, "
+                         "strassen_winograd_paper)")
     ap.add_argument("--no-cpu-table", action="store_true", help="skip the CPU oracle's run of the paper's test")
     ap.add_argument("--cpu-table-repeats", type=int, default=10)
     args = ap.parse_args()
@@ -1102,6 +1106,30 @@ def main():
         mmbuild.build()
         # profiling runs: every FP64 method once (after one warm-up) at n = --n
         print(json.dumps(variants_bench(torch.device("cuda", 0), fp64_peak(0), (args.n,), reps=1)), flush=True)
+        return
+    if args.method:
+        import torch
+
+        import paper_1106_1347_gb300 as mm
+        import synthetic as S
+        from paper_1106_1347_gb300 import build as mmbuild
+
+        mmbuild.build()
+        calls = {"naive": lambda a, b: mm.naive(a, b), "kahan": lambda a, b: mm.kahan(a, b),
+                 "naive_unrolled_4": lambda a, b: mm.naive_unrolled(a, b, unroll=4),
+                 "winograd": lambda a, b: mm.winograd(a, b), "strassen": lambda a, b: mm.strassen(a, b),
+                 "strassen_winograd": lambda a, b: mm.strassen_winograd(a, b),
+                 "strassen_paper": lambda a, b: mm.strassen(a, b, cutoff=0),
+                 "strassen_winograd_paper": lambda a, b: mm.strassen_winograd(a, b, cutoff=0)}
+        if args.method not in calls:
+            raise SystemExit(f"unknown --method {args.method}")
+        n = args.n
+        a = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 0))).cuda()
+        b = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 1))).cuda()
+        fn = calls[args.method]
+        ms = timed(lambda: fn(a, b), 1)
+        print(json.dumps({"method": args.method, "n": n, "ms": ms, "tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12}),
+              flush=True)
         return
     if args.grouped_only:
         import torch
