@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--method", default="",
                     help="profiling runs: one FP64 method at n = --n, a warm-up and one timed call (naive, kahan, "
                          "naive_unrolled_4, winograd, strassen, strassen_winograd, strassen_paper, "
-                         "strassen_winograd_paper)")
+                         "strassen_winograd_paper, strassen_emulated_1)")
     ap.add_argument("--no-cpu-table", action="store_true", help="skip the CPU oracle's run of the paper's test")
     ap.add_argument("--cpu-table-repeats", type=int, default=10)
     args = ap.parse_args()
@@ -1120,12 +1120,17 @@ def main():
                  "winograd": lambda a, b: mm.winograd(a, b), "strassen": lambda a, b: mm.strassen(a, b),
                  "strassen_winograd": lambda a, b: mm.strassen_winograd(a, b),
                  "strassen_paper": lambda a, b: mm.strassen(a, b, cutoff=0),
-                 "strassen_winograd_paper": lambda a, b: mm.strassen_winograd(a, b, cutoff=0)}
+                 "strassen_winograd_paper": lambda a, b: mm.strassen_winograd(a, b, cutoff=0),
+                 "strassen_emulated_1": lambda a, b: mm.strassen_emulated(a, b, variant=1, levels=1, nslices=8)}
         if args.method not in calls:
             raise SystemExit(f"unknown --method {args.method}")
         n = args.n
-        a = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 0))).cuda()
-        b = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 1))).cuda()
+        if args.method.startswith("strassen_emulated"):  # the bench's log-uniform inputs
+            a = torch.from_numpy(S.loguniform(n, n, S.stream_seed(3, 0))).cuda()
+            b = torch.from_numpy(S.loguniform(n, n, S.stream_seed(3, 1))).cuda()
+        else:
+            a = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 0))).cuda()
+            b = torch.from_numpy(S.uniform(n, n, S.stream_seed(1, 1))).cuda()
         fn = calls[args.method]
         ms = timed(lambda: fn(a, b), 1)
         print(json.dumps({"method": args.method, "n": n, "ms": ms, "tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12}),
