@@ -133,16 +133,6 @@ size_t emulated_host_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind);
 int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
                       double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st);
 
-// An operand formed while the emulated product splits it: the operand pointer
-// x0 and up to three more views x1..x3 of the same shape and leading
-// dimension, summed in the nesting `shape` (1: x0; 2: x0 o0 x1; 3: x0 o0 (x1
-// o1 x2); 4: (x0 o0 x1) o1 x2; 5: x0 o0 (x1 o1 (x2 o2 x3)); 6: x0 o0 ((x1 o1
-// x2) o2 x3)), o = +1 or -1, each node rounded.  shape 0 means x0 alone.
-struct OpTerms {
-    const double *x[3];  // x1, x2, x3
-    int8_t shape, op[3];
-};
-
 // Pieces of a grouped emulated launch, for runtimes that place the table part
 // (problem table, header, prefix arrays) and the data part (column maxima,
 // exponents, slices) themselves and replay the kernels from CUDA graphs.
@@ -151,21 +141,16 @@ struct GroupLaunch {
     const int64_t *begin[5];  // device prefix arrays
     int64_t grid[5];          // CTAs per kernel (grid-stride kernels: any size works)
     int s, kind;              // slice count and format
-    bool expr;                // some operand is a sum of views (split kernels evaluate it)
 };
 size_t group_table_bytes(int count);
 size_t problem_data_bytes(const mm_problem &q, int s, int kind = MM_SLICE_BF16);
 size_t group_data_bytes(const mm_problem *probs, int count, int s, int kind = MM_SLICE_BF16);
-// ta / tb (optional, one entry per problem): each problem's A (B) is then the
-// sum of its views described there, with probs[i].A (.B) as x0.
 int group_build(const mm_problem *probs, int count, int capacity, int s, void *table_dev, char *const *data,
-                std::vector<unsigned char> &image, GroupLaunch &gl, int kind = MM_SLICE_BF16,
-                const OpTerms *ta = nullptr, const OpTerms *tb = nullptr);
+                std::vector<unsigned char> &image, GroupLaunch &gl, int kind = MM_SLICE_BF16);
 int group_kernels(const GroupLaunch &gl, cudaStream_t st);
 int64_t group_grid_cap(int kernel);  // fixed grid of grouped kernel `kernel` (0..4)
 void prof_suspend(bool on);  // skip kernel timing while a stream is being captured
-int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void *ws, cudaStream_t st,
-                       const OpTerms *ta = nullptr, const OpTerms *tb = nullptr);
+int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void *ws, cudaStream_t st);
 // Strassen (variant 0) / Strassen-Winograd (1) levels over the emulated product.
 int strassen_emulated_levels(int levels, int64_t N, int64_t P, int64_t M);  // resolves levels == -1
 size_t strassen_emulated_ws_bytes(int variant, int levels, int64_t N, int64_t P, int64_t M, int s, int kind);

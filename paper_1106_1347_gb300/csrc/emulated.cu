@@ -59,121 +59,98 @@ __device__ __forceinline__ unsigned long long absbits(double x) {
     return (unsigned long long)__double_as_longlong(x) & ~(1ull << 63);
 }
 
+// frexp's exponent of a finite double from its magnitude's bit pattern: the e
+// with |x| = f 2^e, f in [1/2, 1) (0 for x = 0).  Normal: e = E - 1022 for the
+// biased exponent E; subnormal: |x| = frac 2^-1074, so e = bitlength(frac) -
+// 1074.
 __device__ __forceinline__ int frexp_exp_bits(unsigned long long absbits) {
     if (absbits == 0) return 0;
-    int e;
-    (void)frexp(__longlong_as_double((long long)absbits), &e);
-    return e;
+    const int E = (int)(absbits >> 52);
+    return E ? E - 1022 : (64 - __clzll((long long)absbits)) - 1074;
 }
 
-// RN(x * 2^sh) as an integer, computed on the bit pattern (ties to even).
+// RN(x * 2^sh) as an integer, computed on the bit pattern (ties to even):
+// |x| = m 2^(E' - 1075) with E' = max(E, 1), so the result is m shifted left by
+// e2 = E' - 1075 + sh when e2 >= 0, else RN(m / 2^r) for r = -e2, which is
+// floor((m + 2^(r-1) - 1 + lsb(floor(m / 2^r))) / 2^r): the added amount carries
+// into bit r exactly when the remainder is above half, or equal to it with an
+// odd quotient (m < 2^53, so nothing overflows; r >= 64 gives 0).
 __device__ __forceinline__ int64_t round_scaled(double x, int sh) {
     const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const bool neg = (b >> 63) != 0;
-    int E = (int)((b >> 52) & 0x7FF);
-    uint64_t m = b & ((1ull << 52) - 1);
-    if (E == 0) {
-        if (m == 0) return 0;
-        E = 1;
-    } else {
-        m |= 1ull << 52;
-    }
-    const int e2 = E - 1075 + sh;
+    const int E = (int)((b >> 52) & 0x7FF);
+    const uint64_t m = (b & ((1ull << 52) - 1)) | (E ? 1ull << 52 : 0ull);
+    const int e2 = max(E, 1) - 1075 + sh;
     uint64_t q;
     if (e2 >= 0) {
-        q = m << e2;
+        q = m << min(e2, 63);
     } else {
-        const int r = -e2;
-        if (r > 63) {
-            q = 0;
-        } else {
-            q = m >> r;
-            const uint64_t rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
-            if (rem > half || (rem == half && (q & 1))) ++q;
-        }
+        const int r = min(-e2, 63);
+        q = (m + ((1ull << (r - 1)) - 1) + ((m >> r) & 1)) >> r;
     }
-    return neg ? -(int64_t)q : (int64_t)q;
+    return (b >> 63) ? -(int64_t)q : (int64_t)q;
 }
 
-// One slice's eight digits as one vector store: 16 bytes of BF16 or 8 bytes of
-// E4M3 at dst (16-byte aligned for BF16, 8 for E4M3).
+// Digit d (|d| < 2^22) as a float, exactly: the bits of 1.5 * 2^23 + d (floats
+// in [2^23, 2^24) are spaced by one) minus 1.5 * 2^23.  `biased` = d + bias
+// with 0 <= biased < 2^22 may be passed instead, with the bias subtracted too.
+constexpr uint32_t kMagicBits = 0x4B400000u;  // 1.5 * 2^23
+constexpr float kMagic = 12582912.0f;
+
+// One slice's eight digits (as exact floats) as one vector store: 16 bytes of
+// BF16 or 8 bytes of E4M3 at dst (16-byte aligned for BF16, 8 for E4M3).  A
+// digit has at most 8 significant bits, so its BF16 is the float's upper half
+// (the lower 16 bits are zero) and its E4M3 conversion is exact.
 template <int KIND>
-__device__ __forceinline__ void store_slice8(const int (&d)[8], unsigned char *dst) {
+__device__ __forceinline__ void store_slice8(const float (&f)[8], unsigned char *dst) {
     if (KIND == MM_SLICE_FP8E4M3) {
         uint32_t w[2] = {0u, 0u};
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-            w[u >> 2] |= (uint32_t)__nv_cvt_float_to_fp8((float)d[u], __NV_SATFINITE, __NV_E4M3) << (8 * (u & 3));
+            w[u >> 2] |= (uint32_t)__nv_cvt_float_to_fp8(f[u], __NV_SATFINITE, __NV_E4M3) << (8 * (u & 3));
         *reinterpret_cast<uint2 *>(dst) = make_uint2(w[0], w[1]);
     } else {
         uint32_t w[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn((float)d[2 * u], (float)d[2 * u + 1]);
-            w[u] = *reinterpret_cast<const uint32_t *>(&h2);
-        }
+        for (int u = 0; u < 4; ++u) w[u] = __byte_perm(__float_as_uint(f[2 * u]), __float_as_uint(f[2 * u + 1]), 0x7632);
         *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
-// The balanced low digit of x, d = ((x + 2^(beta-1)) mod 2^beta) - 2^(beta-1)
-// (in [-2^(beta-1), 2^(beta-1))), and x <- (x - d) / 2^beta, exactly.
-template <int beta, class I>
-__device__ __forceinline__ int peel_digit(I &x) {
-    constexpr int base = 1 << beta, half = base >> 1;
-    const int d = (int)((x + half) & (base - 1)) - half;
-    x = (x - d) >> beta;
-    return d;
-}
-
 // Eight consecutive elements of one slice row at a time.  V[u] holds
-// RN(x_u 2^sh) on entry; its balanced base-2^beta digits are peeled off from
-// the least significant one (low digits in [-2^(beta-1), 2^(beta-1)), the
-// rest is the top digit), and digit t of all eight goes to slice s-1-t as one
-// vector store at dst0 + (s-1-t) * stride (dst0: slice 0 at this row and
-// column).  With more than LO = floor(28 / beta) slices, V = hi 2^(LO beta) +
-// lo is split first: the LO low digits come from lo and the rest from hi +
-// the carry lo leaves, all in 32-bit arithmetic (|V| < 2^(beta s - 1) <= 2^55,
-// so |hi| < 2^27);
-// the digits are the same as those of V itself.  Every index is a
-// compile-time constant, so nothing leaves registers.
+// RN(x_u 2^sh) on entry.  Its balanced base-2^beta digits d_0 .. d_(s-2) lie in
+// [-2^(beta-1), 2^(beta-1)) and the top digit d_(s-1) is the rest, so with
+// H = 2^(beta-1) (1 + 2^beta + ... + 2^(beta(s-2))) the low beta(s-1) bits of
+// V + H hold the ordinary digits d_t + 2^(beta-1) and the bits above them,
+// read as a signed number, are d_(s-1): every digit is one shift and mask of
+// V + H, with no carry from one to the next.  Digit t of all eight goes to
+// slice s-1-t as one vector store at dst0 + (s-1-t) * stride (dst0: slice 0
+// at this row and column).  Every index is a compile-time constant, so nothing
+// leaves registers.
 template <int KIND>
-__device__ __forceinline__ void store_digits8(int64_t (&V)[8], int s, unsigned char *dst0, int64_t stride) {
-    constexpr int beta = fmt_beta(KIND), LO = 28 / beta, LOBITS = LO * beta;
-    if (s > LO) {
-        int32_t lo[8], hi[8];
+__device__ __forceinline__ void store_digits8(const int64_t (&V)[8], int s, unsigned char *dst0, int64_t stride) {
+    constexpr int beta = fmt_beta(KIND), half = 1 << (beta - 1);
+    constexpr uint32_t mask = (1u << beta) - 1;
+    uint64_t H = 0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            lo[u] = (int32_t)(V[u] & ((1ll << LOBITS) - 1));
-            hi[u] = (int32_t)(V[u] >> LOBITS);
-        }
+    for (int t = 0; t + 1 < fmt_max_slices(KIND); ++t)
+        if (t + 1 < s) H |= (uint64_t)half << (beta * t);
+    uint64_t z[8];
 #pragma unroll
-        for (int t = 0; t < LO; ++t) {
-            int d[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) d[u] = peel_digit<beta>(lo[u]);
-            store_slice8<KIND>(d, dst0 + (int64_t)(s - 1 - t) * stride);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) hi[u] += lo[u];  // the carry, 0 or 1
-#pragma unroll
-        for (int t = LO; t < fmt_max_slices(KIND); ++t) {
-            if (t < s) {
-                int d[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) d[u] = t < s - 1 ? peel_digit<beta>(hi[u]) : hi[u];
-                store_slice8<KIND>(d, dst0 + (int64_t)(s - 1 - t) * stride);
-            }
-        }
-        return;
-    }
+    for (int u = 0; u < 8; ++u) z[u] = (uint64_t)V[u] + H;
 #pragma unroll
     for (int t = 0; t < fmt_max_slices(KIND); ++t) {
         if (t < s) {
-            int d[8];
+            float f[8];
+            if (t + 1 < s) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) d[u] = t < s - 1 ? peel_digit<beta>(V[u]) : (int)V[u];
-            store_slice8<KIND>(d, dst0 + (int64_t)(s - 1 - t) * stride);
+                for (int u = 0; u < 8; ++u)
+                    f[u] = __uint_as_float(((uint32_t)(z[u] >> (beta * t)) & mask) | kMagicBits) - (kMagic + half);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    f[u] = __uint_as_float(kMagicBits + (uint32_t)(int32_t)((int64_t)z[u] >> (beta * t))) - kMagic;
+            }
+            store_slice8<KIND>(f, dst0 + (int64_t)(s - 1 - t) * stride);
         }
     }
 }
@@ -194,71 +171,6 @@ __device__ __forceinline__ void load8(const double *__restrict__ a, int64_t c, i
     }
 }
 
-// v := v o w (w_left: v := w o v), element by element, rounded.
-__device__ __forceinline__ void fold8(double (&v)[8], int8_t o, const double (&w)[8], bool w_left) {
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = w_left ? plus_minus(w[u], o, v[u]) : plus_minus(v[u], o, w[u]);
-}
-
-// load8 of the operand of a split: one view, or the sum of up to four views
-// (OpTerms) evaluated element by element in its nesting order, innermost sum
-// first, so only two groups of eight values are live; `off` is the row's
-// element offset, the same in every view.  kExpr = false compiles the plain
-// load alone.
-template <bool kExpr>
-__device__ __forceinline__ void load8_op(const double *a0, const OpTerms &ex, int64_t off, int64_t c, int64_t P,
-                                         bool vec, double (&v)[8]) {
-    if (!kExpr || ex.shape <= 1) {
-        load8(a0 + off, c, P, vec, v);
-        return;
-    }
-    const double *x0 = a0 + off, *x1 = ex.x[0] + off, *x2 = ex.x[1] + off, *x3 = ex.x[2] + off;
-    double w[8];
-    switch (ex.shape) {
-        case 2:  // x0 o0 x1
-            load8(x0, c, P, vec, v), load8(x1, c, P, vec, w), fold8(v, ex.op[0], w, false);
-            break;
-        case 3:  // x0 o0 (x1 o1 x2)
-            load8(x1, c, P, vec, v), load8(x2, c, P, vec, w), fold8(v, ex.op[1], w, false);
-            load8(x0, c, P, vec, w), fold8(v, ex.op[0], w, true);
-            break;
-        case 4:  // (x0 o0 x1) o1 x2
-            load8(x0, c, P, vec, v), load8(x1, c, P, vec, w), fold8(v, ex.op[0], w, false);
-            load8(x2, c, P, vec, w), fold8(v, ex.op[1], w, false);
-            break;
-        case 5:  // x0 o0 (x1 o1 (x2 o2 x3))
-            load8(x2, c, P, vec, v), load8(x3, c, P, vec, w), fold8(v, ex.op[2], w, false);
-            load8(x1, c, P, vec, w), fold8(v, ex.op[1], w, true);
-            load8(x0, c, P, vec, w), fold8(v, ex.op[0], w, true);
-            break;
-        default:  // 6: x0 o0 ((x1 o1 x2) o2 x3)
-            load8(x1, c, P, vec, v), load8(x2, c, P, vec, w), fold8(v, ex.op[1], w, false);
-            load8(x3, c, P, vec, w), fold8(v, ex.op[2], w, false);
-            load8(x0, c, P, vec, w), fold8(v, ex.op[0], w, true);
-            break;
-    }
-}
-
-// Element (k, j) of a column split's operand (one view or a sum of views).
-__device__ __forceinline__ double load_op(const SplitB &p, int64_t k, int64_t j) {
-    const int64_t off = k * p.ldb + j;
-    const double x0 = __ldg(p.B + off);
-    if (p.ex.shape <= 1) return x0;
-    const int nt = terms_of(p.ex.shape);
-    const double x1 = __ldg(p.ex.x[0] + off);
-    const double x2 = nt > 2 ? __ldg(p.ex.x[1] + off) : 0.0;
-    const double x3 = nt > 3 ? __ldg(p.ex.x[2] + off) : 0.0;
-    return eval_terms(p.ex, x0, x1, x2, x3);
-}
-
-// Every view of an operand starts its rows on 16 bytes (vector loads).
-__device__ __forceinline__ bool rows_aligned(const double *a0, const OpTerms &ex, int64_t off) {
-    uintptr_t bits = (uintptr_t)(a0 + off);
-    const int nt = terms_of(ex.shape);
-    for (int t = 0; t + 1 < nt; ++t) bits |= (uintptr_t)(ex.x[t] + off);
-    return (bits & 15) == 0;
-}
-
 constexpr int kRowThreads = 256;
 // Rows of at most kQuarterRowMax (padded) elements are split by 8 threads each
 // (4 rows per warp, 32 per CTA), rows of at most kWarpRowMax by one warp each
@@ -277,17 +189,17 @@ constexpr int64_t kQuarterRowMax = 64, kWarpRowMax = 1024;
 // warp).  With T = 8 the warp's four groups reduce among themselves, so every
 // lane of the warp must call it: a group past the last row passes valid =
 // false and only takes part in the reduction.
-template <int KIND, int T, bool kExpr = false>
+template <int KIND, int T>
 __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int tid, unsigned long long *red,
                                           bool valid = true) {
     const int64_t off = valid ? row * p.lda : 0;
     const int64_t P = valid ? p.P : 0, Pp = valid ? p.Pp : 0;
     const int s = p.s;
-    const bool vec = kExpr ? rows_aligned(p.A, p.ex, off) : (((uintptr_t)(p.A + off)) & 15) == 0;
+    const bool vec = (((uintptr_t)(p.A + off)) & 15) == 0;
     unsigned long long mx = 0;
     for (int64_t c = 8 * tid; c < P; c += 8 * T) {
         double x[8];
-        load8_op<kExpr>(p.A, p.ex, off, c, P, vec, x);
+        load8(p.A + off, c, P, vec, x);
 #pragma unroll
         for (int u = 0; u < 8; ++u) mx = umax64(mx, absbits(x[u]));
     }
@@ -311,7 +223,7 @@ __device__ __forceinline__ void split_row(const SplitA &p, int64_t row, int tid,
     // starting before Pp ends by Pp.
     for (int64_t c = 8 * tid; c < Pp; c += 8 * T) {
         double x[8];
-        load8_op<kExpr>(p.A, p.ex, off, c, P, vec, x);
+        load8(p.A + off, c, P, vec, x);
         int64_t V[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) V[u] = round_scaled(x[u], sh);
@@ -346,11 +258,7 @@ __device__ __forceinline__ void col_max_part(const SplitB &p, int64_t j, int64_t
     if (j >= p.M) return;
     const int64_t k1 = min(p.P, k0 + 256);
     unsigned long long mx = 0;
-    if (p.ex.shape <= 1) {
-        for (int64_t k = k0; k < k1; ++k) mx = umax64(mx, absbits(p.B[k * p.ldb + j]));
-    } else {
-        for (int64_t k = k0; k < k1; ++k) mx = umax64(mx, absbits(load_op(p, k, j)));
-    }
+    for (int64_t k = k0; k < k1; ++k) mx = umax64(mx, absbits(p.B[k * p.ldb + j]));
     if (mx) atomicMax(p.colmax + j, mx);
 }
 
@@ -382,23 +290,13 @@ __device__ __forceinline__ void split_cols_tile(const SplitB &p, int64_t jt, int
     const double *__restrict__ bj = p.B + j;
     unsigned char *row0 = p.slices + j * Pp * es;
     const int64_t stride = (int64_t)p.Mr * Pp * es;
-    // All 32 loads first, so they are in flight together (an operand summed
-    // from several views evaluates each element as it is loaded).
+    // All 32 loads first, so they are in flight together.
     double x[4][8];
-    if (p.ex.shape <= 1) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int64_t k0 = kt * SC_K + 8 * (kg + 4 * r);
+    for (int r = 0; r < 4; ++r) {
+        const int64_t k0 = kt * SC_K + 8 * (kg + 4 * r);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) x[r][u] = (k0 + u < P) ? __ldg(bj + (k0 + u) * ldb) : 0.0;
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int64_t k0 = kt * SC_K + 8 * (kg + 4 * r);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) x[r][u] = (k0 + u < P) ? load_op(p, k0 + u, j) : 0.0;
-        }
+        for (int u = 0; u < 8; ++u) x[r][u] = (k0 + u < P) ? __ldg(bj + (k0 + u) * ldb) : 0.0;
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -431,9 +329,7 @@ __global__ void __launch_bounds__(256) group_zero_colmax_kernel(const EmuProblem
     }
 }
 
-// kExpr: some problem of the launch splits a sum of views (Strassen levels
-// over the product); launches without any take the plain instantiation.
-template <int KIND, bool kExpr>
+template <int KIND>
 __global__ void __launch_bounds__(kRowThreads, 4) group_split_rows_kernel(const EmuProblem *tab,
                                                                           const int64_t *begin,
                                                                           const GroupHeader *hdr) {
@@ -445,12 +341,12 @@ __global__ void __launch_bounds__(kRowThreads, 4) group_split_rows_kernel(const 
         if (p.Pp <= kQuarterRowMax) {  // 32 rows per unit, 8 threads per row (the whole CTA takes this branch)
             const int64_t row = (u - begin[g]) * (kRowThreads / 8) + (threadIdx.x >> 3);
             const int64_t warp_row0 = (u - begin[g]) * (kRowThreads / 8) + ((threadIdx.x & ~31u) >> 3);
-            if (warp_row0 < p.N) split_row<KIND, 8, kExpr>(p, row, threadIdx.x & 7, nullptr, row < p.N);
+            if (warp_row0 < p.N) split_row<KIND, 8>(p, row, threadIdx.x & 7, nullptr, row < p.N);
         } else if (p.Pp <= kWarpRowMax) {  // 8 rows per unit, one per warp
             const int64_t row = (u - begin[g]) * (kRowThreads / 32) + (threadIdx.x >> 5);
-            if (row < p.N) split_row<KIND, 32, kExpr>(p, row, threadIdx.x & 31, nullptr);
+            if (row < p.N) split_row<KIND, 32>(p, row, threadIdx.x & 31, nullptr);
         } else {  // one row per unit
-            split_row<KIND, kRowThreads, kExpr>(p, u - begin[g], threadIdx.x, red);
+            split_row<KIND, kRowThreads>(p, u - begin[g], threadIdx.x, red);
         }
     }
 }
@@ -885,11 +781,8 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
     if (rc) return rc;
     if (gl.grid[U_ROWS] > 0)
         rc = launch("emu_group_split_rows", st, [&] {
-            const auto k = gl.kind == MM_SLICE_FP8E4M3
-                               ? (gl.expr ? group_split_rows_kernel<MM_SLICE_FP8E4M3, true>
-                                          : group_split_rows_kernel<MM_SLICE_FP8E4M3, false>)
-                               : (gl.expr ? group_split_rows_kernel<MM_SLICE_BF16, true>
-                                          : group_split_rows_kernel<MM_SLICE_BF16, false>);
+            const auto k = gl.kind == MM_SLICE_FP8E4M3 ? group_split_rows_kernel<MM_SLICE_FP8E4M3>
+                                                       : group_split_rows_kernel<MM_SLICE_BF16>;
             k<<<(unsigned)gl.grid[U_ROWS], kRowThreads, 0, st>>>((const EmuProblem *)gl.tab, gl.begin[U_ROWS],
                                                          (const GroupHeader *)gl.hdr);
         });
@@ -930,7 +823,7 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
 // problem i's data region of problem_data_bytes(probs[i], s, kind) bytes; the
 // table is laid out for `capacity` problems (>= count).
 int group_build(const mm_problem *probs, int count, int capacity, int s, void *table_dev, char *const *data,
-                std::vector<unsigned char> &image, GroupLaunch &gl, int kind, const OpTerms *ta, const OpTerms *tb) {
+                std::vector<unsigned char> &image, GroupLaunch &gl, int kind) {
     if (capacity < count) return fail(MM_ERR_ARG, "grouped launch: %d problems exceed capacity %d", count, capacity);
     const GroupLayout G = group_layout(capacity);
     char *t = (char *)table_dev;
@@ -948,7 +841,6 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
     // data region; any order gives the same results.
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
-    bool expr = false;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return probs[x].P > probs[y].P; });
     for (int i = 0; i < count; ++i) {
         const mm_problem &q = probs[order[i]];
@@ -964,9 +856,8 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
         unsigned char *sa = (unsigned char *)w;
         w += slices_bytes(L.Nr, L.Pp, s, kind);
         unsigned char *sb = (unsigned char *)w;
-        e.spa = SplitA{q.N, q.P, q.lda, L.Nr, L.Pp, q.A, s, ea, sa, ta ? ta[order[i]] : OpTerms{}};
-        e.spb = SplitB{q.P, q.M, q.ldb, L.Mr, L.Pp, q.B, s, cm, fb, sb, tb ? tb[order[i]] : OpTerms{}};
-        if (e.spa.ex.shape > 1 || e.spb.ex.shape > 1) expr = true;
+        e.spa = SplitA{q.N, q.P, q.lda, L.Nr, L.Pp, q.A, s, ea, sa};
+        e.spb = SplitB{q.P, q.M, q.ldb, L.Mr, L.Pp, q.B, s, cm, fb, sb};
         fill_common(e.prm, s);
         e.prm.N = q.N;
         e.prm.P = q.P;
@@ -1001,14 +892,11 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
     gl.hdr = t + G.off_hdr;
     gl.s = s;
     gl.kind = kind;
-    gl.expr = expr;
     return MM_OK;
 }
 
-int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void *ws, cudaStream_t st,
-                       const OpTerms *ta, const OpTerms *tb) {
+int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void *ws, cudaStream_t st) {
     std::vector<mm_problem> live;
-    std::vector<OpTerms> lta, ltb;
     live.reserve(count);
     for (int i = 0; i < count; ++i) {
         const mm_problem &q = probs[i];
@@ -1019,8 +907,6 @@ int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void
             continue;
         }
         live.push_back(q);
-        lta.push_back(ta ? ta[i] : OpTerms{});
-        ltb.push_back(tb ? tb[i] : OpTerms{});
     }
     if (live.empty()) return MM_OK;
     std::vector<unsigned char> image;
@@ -1031,8 +917,7 @@ int run_emulated_group(const mm_problem *probs, int count, int s, int kind, void
         data[i] = d;
         d += problem_data_bytes(live[i], s, kind);
     }
-    int rc = group_build(live.data(), (int)live.size(), (int)live.size(), s, ws, data.data(), image, gl, kind,
-                         lta.data(), ltb.data());
+    int rc = group_build(live.data(), (int)live.size(), (int)live.size(), s, ws, data.data(), image, gl, kind);
     if (rc) return rc;
     // Pageable source: the copy is staged before cudaMemcpyAsync returns, so `image` may go.
     cudaError_t e = cudaMemcpyAsync((void *)gl.tab, image.data(), image.size(), cudaMemcpyHostToDevice, st);

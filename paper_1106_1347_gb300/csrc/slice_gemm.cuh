@@ -59,52 +59,23 @@ __host__ __device__ constexpr uint32_t slice_tmem_cols(int s) {
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
-// An operand formed while it is split, from the operand pointer x0 and up to
-// three more views x1..x3 with the same shape and leading dimension (the
-// quadrants of a Strassen node), each node of the sum rounded as the
-// Plus/Minus matrices of sections "StrassenNaiv" and "StrassenWinograd" are,
-// o = +1 (Plus) or -1 (Minus):
-//   shape 0 or 1: x0;              2: x0 o0 x1;
-//   3: x0 o0 (x1 o1 x2);           4: (x0 o0 x1) o1 x2;
-//   5: x0 o0 (x1 o1 (x2 o2 x3));   6: x0 o0 ((x1 o1 x2) o2 x3).
-using mm::OpTerms;
-
-__device__ __forceinline__ double plus_minus(double a, int8_t o, double b) {
-    return o > 0 ? __dadd_rn(a, b) : __dsub_rn(a, b);
-}
-__device__ __forceinline__ double eval_terms(const OpTerms &e, double x0, double x1, double x2, double x3) {
-    switch (e.shape) {
-        case 2: return plus_minus(x0, e.op[0], x1);
-        case 3: return plus_minus(x0, e.op[0], plus_minus(x1, e.op[1], x2));
-        case 4: return plus_minus(plus_minus(x0, e.op[0], x1), e.op[1], x2);
-        case 5: return plus_minus(x0, e.op[0], plus_minus(x1, e.op[1], plus_minus(x2, e.op[2], x3)));
-        case 6: return plus_minus(x0, e.op[0], plus_minus(plus_minus(x1, e.op[1], x2), e.op[2], x3));
-        default: return x0;
-    }
-}
-__host__ __device__ constexpr int terms_of(int shape) {
-    return shape <= 1 ? 1 : shape == 2 ? 2 : (shape == 3 || shape == 4) ? 3 : 4;
-}
-
 // Everything one split of A needs (one problem).
 struct SplitA {
     int64_t N, P, lda, Nr, Pp;
-    const double *A;  // the operand, or its first term when ex.shape > 1
+    const double *A;
     int s;
     int32_t *ea;
     unsigned char *slices;  // [s][Nr][Pp] elements of the slice format (the kernels' template parameter)
-    OpTerms ex;             // shape 0: A itself
 };
 
 // Everything the column split of B needs (one problem).
 struct SplitB {
     int64_t P, M, ldb, Mr, Pp;
-    const double *B;  // the operand, or its first term when ex.shape > 1
+    const double *B;
     int s;
     unsigned long long *colmax;  // zeroed before col_max runs
     int32_t *fb;
     unsigned char *slices;  // [s][Mr][Pp] elements of the slice format
-    OpTerms ex;             // shape 0: B itself
 };
 
 struct EmuParams {

@@ -10,16 +10,16 @@
 // right.  Every step is deterministic, so the result is bit-identical to the
 // oracle's.
 //
-// GB300 layout of the work: above the last level, one elementwise kernel per
-// node and operand side reads the node's four quadrants once and writes all of
-// that side's operand sums (HBM-bound); the last level's operand sums are not
-// stored at all -- the split kernels of the grouped product read the 1 to 4
-// quadrants an operand needs and form its sum element by element, in the
-// printed order, before taking exponents and digits; all 7^L base products run as ONE grouped emulated launch
-// (persistent slice kernel over every leaf's tiles, so the tensor pipe sees
-// 7^L x tiles of work at once rather than 7^L small launches); one elementwise
-// kernel per internal node reads its seven H blocks once and writes its four
-// C quadrants.  Operands that are plain quadrants are passed as views (the
+// GB300 layout of the work: one elementwise kernel per node and operand side
+// reads the node's four quadrants once and writes all of that side's operand
+// sums (HBM-bound, one pass at about 0.8 of the copy bandwidth; forming the
+// sums inside the split kernels instead measured slower, since the column
+// split reads every operand twice and sums of up to four views cut the split
+// kernels' memory parallelism); all 7^L base products run as ONE grouped
+// emulated launch (persistent slice kernel over every leaf's tiles, so the
+// tensor pipe sees 7^L x tiles of work at once rather than 7^L small
+// launches); one elementwise kernel per internal node reads its seven H
+// blocks once and writes its four C quadrants.  Operands that are plain quadrants are passed as views (the
 // parent's leading dimension), never copied.
 #include <algorithm>
 #include <vector>
@@ -135,32 +135,12 @@ struct View {
 
 // One product of the recursion: out (leading dimension ldo) = a * b, at the
 // level's size.  `kids` is where its children's H1..H7 live once expanded.
-// At the last level a and b may be sums of views (ta, tb), which the split
-// kernels of the grouped product evaluate as they read them.
 struct Node {
     View a, b;
     double *out;
     int64_t ldo;
     double *kids;
-    mm::OpTerms ta, tb;
 };
-
-// x0 alone, x0 o x1, and the nestings of OpTerms (see common.cuh).
-mm::OpTerms plain() { return mm::OpTerms{{nullptr, nullptr, nullptr}, 0, {0, 0, 0}}; }
-mm::OpTerms sum2(int8_t o, const double *x1) { return mm::OpTerms{{x1, nullptr, nullptr}, 2, {o, 0, 0}}; }
-mm::OpTerms sum3(int8_t o0, const double *x1, int8_t o1, const double *x2) {  // x0 o0 (x1 o1 x2)
-    return mm::OpTerms{{x1, x2, nullptr}, 3, {o0, o1, 0}};
-}
-mm::OpTerms sum4(int8_t o0, const double *x1, int8_t o1, const double *x2) {  // (x0 o0 x1) o1 x2
-    return mm::OpTerms{{x1, x2, nullptr}, 4, {o0, o1, 0}};
-}
-mm::OpTerms sum5(int8_t o0, const double *x1, int8_t o1, const double *x2, int8_t o2, const double *x3) {
-    return mm::OpTerms{{x1, x2, x3}, 5, {o0, o1, o2}};  // x0 o0 (x1 o1 (x2 o2 x3))
-}
-mm::OpTerms sum6(int8_t o0, const double *x1, int8_t o1, const double *x2, int8_t o2, const double *x3) {
-    return mm::OpTerms{{x1, x2, x3}, 6, {o0, o1, o2}};  // x0 o0 ((x1 o1 x2) o2 x3)
-}
-constexpr int8_t kPlus = 1, kMinus = -1;
 
 // Grid of an elementwise kernel over an h x w block: 256 columns per CTA in x,
 // rows in y, about 16 CTAs per SM in all (the kernels stride over the rest).
@@ -198,48 +178,11 @@ int strassen_emulated_walk(bool dry, int variant, int levels, int64_t N, int64_t
         B0 = View{bp, Mp};
     }
     const int nsa = variant == 0 ? 5 : 4, nsb = variant == 0 ? 5 : 4;
-    std::vector<std::vector<Node>> tree(1, std::vector<Node>{Node{A0, B0, C0, ldc0, nullptr, plain(), plain()}});
+    std::vector<std::vector<Node>> tree(1, std::vector<Node>{Node{A0, B0, C0, ldc0, nullptr}});
     for (int j = 0; j < levels; ++j) {
         const int64_t h = (Np >> j) / 2, p2 = (Pp >> j) / 2, w = (Mp >> j) / 2;
         std::vector<Node> next;
         next.reserve(tree[j].size() * 7);
-        if (j == levels - 1) {
-            // The last level: its operand sums are formed by the split kernels of the
-            // grouped product as they read the quadrants (no pass of their own).
-            for (Node &nd : tree[j]) {
-                nd.kids = (double *)ar.take((size_t)7 * h * w * 8);
-                const int64_t la = nd.a.ld, lb = nd.b.ld;
-                const double *a11 = nd.a.p, *a12 = nd.a.p + p2, *a21 = nd.a.p + h * la, *a22 = a21 + p2;
-                const double *b11 = nd.b.p, *b12 = nd.b.p + w, *b21 = nd.b.p + p2 * lb, *b22 = b21 + w;
-                const double *xa[7], *xb[7];
-                mm::OpTerms ea[7], eb[7];
-                if (variant == 0) {  // H1..H7 of section "StrassenNaiv"
-                    xa[0] = a11, ea[0] = sum2(kPlus, a22), xb[0] = b11, eb[0] = sum2(kPlus, b22);
-                    xa[1] = a21, ea[1] = sum2(kPlus, a22), xb[1] = b11, eb[1] = plain();
-                    xa[2] = a11, ea[2] = plain(), xb[2] = b12, eb[2] = sum2(kMinus, b22);
-                    xa[3] = a22, ea[3] = plain(), xb[3] = b21, eb[3] = sum2(kMinus, b11);
-                    xa[4] = a11, ea[4] = sum2(kPlus, a12), xb[4] = b22, eb[4] = plain();
-                    xa[5] = a21, ea[5] = sum2(kMinus, a11), xb[5] = b11, eb[5] = sum2(kPlus, b12);
-                    xa[6] = a12, ea[6] = sum2(kMinus, a22), xb[6] = b21, eb[6] = sum2(kPlus, b22);
-                } else {  // H1..H7 of section "StrassenWinograd": A1 = A11-A21, A2 = A22-A1, B1 = B22-B12, B2 = B1+B11
-                    xa[0] = a11, ea[0] = plain(), xb[0] = b11, eb[0] = plain();
-                    xa[1] = a12, ea[1] = plain(), xb[1] = b21, eb[1] = plain();
-                    xa[2] = a22, ea[2] = sum3(kMinus, a11, kMinus, a21);                  // A2
-                    xb[2] = b22, eb[2] = sum4(kMinus, b12, kPlus, b11);                   // B2
-                    xa[3] = a21, ea[3] = sum2(kPlus, a22), xb[3] = b12, eb[3] = sum2(kMinus, b11);
-                    xa[4] = a11, ea[4] = sum2(kMinus, a21), xb[4] = b22, eb[4] = sum2(kMinus, b12);  // A1, B1
-                    xa[5] = a12, ea[5] = sum5(kMinus, a22, kMinus, a11, kMinus, a21);     // A12 - A2
-                    xb[5] = b22, eb[5] = plain();
-                    xa[6] = a22, ea[6] = plain();
-                    xb[6] = b21, eb[6] = sum6(kMinus, b22, kMinus, b12, kPlus, b11);      // B21 - B2
-                }
-                for (int k = 0; k < 7; ++k)
-                    next.push_back(Node{View{xa[k], la}, View{xb[k], lb}, nd.kids + (size_t)k * h * w, w, nullptr,
-                                        ea[k], eb[k]});
-            }
-            tree.push_back(std::move(next));
-            continue;
-        }
         for (Node &nd : tree[j]) {
             double *sa = (double *)ar.take((size_t)nsa * h * p2 * 8);
             double *sb = (double *)ar.take((size_t)nsb * p2 * w * 8);
@@ -280,24 +223,19 @@ int strassen_emulated_walk(bool dry, int variant, int levels, int64_t N, int64_t
                 ao[5] = S(3), bo[5] = b22;
                 ao[6] = a22, bo[6] = T(3);
             }
-            for (int k = 0; k < 7; ++k)
-                next.push_back(Node{ao[k], bo[k], nd.kids + (size_t)k * h * w, w, nullptr, plain(), plain()});
+            for (int k = 0; k < 7; ++k) next.push_back(Node{ao[k], bo[k], nd.kids + (size_t)k * h * w, w, nullptr});
         }
         tree.push_back(std::move(next));
     }
     // Every base product in one grouped launch.
     const int64_t nl = Np >> levels, pl = Pp >> levels, ml = Mp >> levels;
     std::vector<mm_problem> probs;
-    std::vector<mm::OpTerms> ta, tb;
     probs.reserve(tree[levels].size());
-    for (const Node &nd : tree[levels]) {
+    for (const Node &nd : tree[levels])
         probs.push_back(mm_problem{nl, pl, ml, nd.a.p, nd.a.ld, nd.b.p, nd.b.ld, nd.out, nd.ldo});
-        ta.push_back(nd.ta);
-        tb.push_back(nd.tb);
-    }
     char *gws = ar.take(mm::emulated_group_ws_bytes(probs.data(), (int)probs.size(), s, kind));
     if (!dry) {
-        int rc = mm::run_emulated_group(probs.data(), (int)probs.size(), s, kind, gws, st, ta.data(), tb.data());
+        int rc = mm::run_emulated_group(probs.data(), (int)probs.size(), s, kind, gws, st);
         if (rc) return rc;
         // Combine bottom-up: each internal node's C quadrants from its H1..H7.
         for (int j = levels - 1; j >= 0; --j) {
