@@ -268,6 +268,26 @@ def test_emulated_subnormal_and_overflowing_results(mm, orc, kind, beta, s):
         assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("kind,beta,s", [(0, 7, 8), (0, 7, 3), (1, 5, 10)])
+def test_emulated_subnormal_operands(mm, orc, kind, beta, s):
+    """Rows of A and columns of B whose largest entry is subnormal: the split
+    scales them by up to 2^(beta s + 1021) (a left shift of the mantissa far
+    past the normal case), bit for bit as the oracle's frexp and RN."""
+    a, b = pair(140, 90, 75, "log", 41)
+    a[:40] = np.ldexp(a[:40], -1050)              # whole rows subnormal (|a| < 2^-1030)
+    a[40:45] = 0.0
+    a[40:45, :3] = np.array([5e-324, 1.5e-323, -2e-323])  # rows of a few units in the last place
+    a[45:60, ::2] = np.ldexp(a[45:60, ::2], -1070)  # subnormal beside normal in one row
+    b = np.ldexp(b, 900)
+    b[:, :20] = np.ldexp(b[:, :20], -1950)        # whole columns subnormal
+    assert (np.abs(a[:40]) < 2.0 ** -1022).all() and (a[:40] != 0).all()
+    assert (np.abs(b[:, :20]) < 2.0 ** -1022).all() and (b[:, :20] != 0).all()
+    ref = orc.split_product(a, b, beta, s)
+    assert np.isfinite(ref).all() and (ref[:40] != 0).sum() > 1000
+    got = host(mm.emulated(dev(a), dev(b), nslices=s, kind=kind))
+    assert np.array_equal(got, ref)
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 1), (5, 3, 7), (128, 32, 64), (129, 33, 65), (200, 333, 150),
                                    (256, 1100, 130)])
 @pytest.mark.parametrize("s", [8, 3])
