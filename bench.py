@@ -513,11 +513,13 @@ def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000
     sat_trace = S.serving_trace(requests, S.stream_seed(4, 2), mean_gap_s=0.0)
 
     def warm():
-        # Latencies measured right after a long stretch of light load (the FP64
-        # arm's replay, about 20 s) came out 5-20x worse at p99 than the same
-        # replay after a burst of work, with the GPU at its maximum clock
-        # throughout: every paced replay starts after the same short saturated
-        # burst, so each one starts from the same state.
+        # In a long-lived process a paced replay could meet one stall of 10-60 ms
+        # (at a new server's first batches, or mid-replay), more often the
+        # longer the process had run or idled before it, with the GPU at its
+        # maximum clock throughout; the ~45 requests caught in it set p99.  So
+        # the latency replays run first, before the long light-load replays of
+        # the like-for-like comparison, each after the same short saturated
+        # burst.
         with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True) as w:
             serving.replay(w, sat_trace[:1000], a_pool, b_pool, c_pool)
 
@@ -532,6 +534,15 @@ def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000
     warm()
     with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True) as srv:
         st, comps, rc = serving.replay(srv, paced, a_pool, b_pool, c_pool)
+    # Latency against load: shorter Poisson streams at other fractions of the saturated rate.
+    sweep = {}
+    for frac in (0.3, 0.5, 1.0):
+        tr = S.serving_trace(sweep_requests, S.stream_seed(4, 3), mean_gap_s=1.0 / (frac * rate))
+        warm()
+        with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True) as srv:
+            st_f, _, rc_f = serving.replay(srv, tr, a_pool, b_pool, c_pool)
+        sweep[str(frac)] = {"arrival_rate_rps": frac * rate, "p50_ms": st_f["p50_ms"], "p99_ms": st_f["p99_ms"],
+                            "completed": st_f["completed"], "status": rc_f}
     # The same two runs when each request takes the cheaper of BF16 and FP8 slices for its tier.
     with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True,
                         method=serving.METHOD_EMULATED_AUTO) as srv:
@@ -579,15 +590,6 @@ def serve_bench(dev, requests, budget_gb, baseline_requests, sweep_requests=3000
                                   "max_ms": st_ef["max_ms"], "completed": st_ef["completed"], "status": rc_ef},
     }
     flop_all = st["flops"]
-    # Latency against load: shorter Poisson streams at other fractions of the saturated rate.
-    sweep = {}
-    for frac in (0.3, 0.5, 1.0):
-        tr = S.serving_trace(sweep_requests, S.stream_seed(4, 3), mean_gap_s=1.0 / (frac * rate))
-        warm()
-        with serving.Server(budget, max_batch=256, nstreams=4, use_graphs=True) as srv:
-            st_f, _, rc_f = serving.replay(srv, tr, a_pool, b_pool, c_pool)
-        sweep[str(frac)] = {"arrival_rate_rps": frac * rate, "p50_ms": st_f["p50_ms"], "p99_ms": st_f["p99_ms"],
-                            "completed": st_f["completed"], "status": rc_f}
     # A 1 GiB budget, where admission binds: the largest requests (about 1.5 GB with
     # their split workspace) can never fit and are rejected, the rest queue for memory.
     small = 1 << 30

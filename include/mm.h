@@ -247,10 +247,14 @@ int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, c
  * mm_emulated with HOST operands: A, B and C are host pointers (pinned memory
  * lets the copies overlap the products), `ws` is a device workspace of
  * mm_emulated_host_workspace_bytes bytes holding the device copies of A, B, C
- * and the split.  One internal copy stream carries B first and then A in up
- * to 8 row blocks; B is split as soon as it lands, each block's product
- * follows its copy, and its rows of C are copied back on a second internal
- * stream while later blocks run.  Asynchronous on `stream` (which waits for the last copy back); the
+ * and the split.  C is computed in blocks: up to 8 row blocks, and for
+ * N >= 4096 and M >= 2048 two column blocks, with row blocks of whole waves of
+ * tiles.  One internal copy
+ * stream carries the first row block of A, the column blocks of B, then the
+ * other row blocks of A; each block is split as soon as it lands, each block
+ * product follows the splits it needs, and its block of C is copied back on a
+ * second internal stream while later blocks run.  Asynchronous on `stream`
+ * (which waits for the last copy back); the
  * host buffers must stay valid and C unread until the stream completes.  With
  * P == 0 the call synchronises `stream` and writes C = 0 on the host.  Results are
  * bit-identical to mm_emulated.  Errors as for mm_emulated.

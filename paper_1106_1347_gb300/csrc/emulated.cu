@@ -483,19 +483,21 @@ EmuWork emu_work(int64_t N, int64_t P, int64_t M, int s, int kind, void *ws) {
     return w;
 }
 
-// Column exponents and slices of B.
-int split_b(const EmuWork &w, int64_t P, int64_t M, const double *B, int64_t ldb, int s, int kind,
+// Column exponents and slices of columns [c0, c0 + m) of B (B points at
+// column c0; c0 = 0 and m = M for all of B).
+int split_b(const EmuWork &w, int64_t c0, int64_t P, int64_t m, const double *B, int64_t ldb, int s, int kind,
             cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(w.colmax, 0, (size_t)M * 8, st);
+    cudaError_t e = cudaMemsetAsync(w.colmax + c0, 0, (size_t)m * 8, st);
     if (e != cudaSuccess) return mm::cuda_fail(e, "mm_emulated");
-    const SplitB spb{P, M, ldb, w.L.Mr, w.L.Pp, B, s, w.colmax, w.fb, w.sb};
+    const SplitB spb{P, m, ldb, w.L.Mr, w.L.Pp, B, s, w.colmax + c0, w.fb + c0,
+                     w.sb + (size_t)c0 * w.L.Pp * fmt_esize(kind)};
     int rc = mm::launch("emu_col_max", st, [&] {
-        dim3 g((unsigned)mm::ceil_div(M, 128), (unsigned)mm::ceil_div(P, 256));
+        dim3 g((unsigned)mm::ceil_div(m, 128), (unsigned)mm::ceil_div(P, 256));
         col_max_kernel<<<g, 128, 0, st>>>(spb);
     });
     if (rc) return rc;
     return mm::launch("emu_split_cols", st, [&] {
-        dim3 g((unsigned)mm::ceil_div(M, SC_J), (unsigned)mm::ceil_div(w.L.Pp, SC_K));
+        dim3 g((unsigned)mm::ceil_div(m, SC_J), (unsigned)mm::ceil_div(w.L.Pp, SC_K));
         if (kind == MM_SLICE_FP8E4M3)
             split_cols_kernel<MM_SLICE_FP8E4M3><<<g, 256, 0, st>>>(spb);
         else
@@ -530,25 +532,26 @@ int split_a_rows(const EmuWork &w, int64_t r0, int64_t n, int64_t P, const doubl
     });
 }
 
-// The slice product for rows [r0, r0 + n) of C (r0 a multiple of the tile
-// height; C points at row r0).
-int slice_product(const EmuWork &w, int64_t r0, int64_t n, int64_t P, int64_t M, double *C, int64_t ldc, int s,
-                  int kind, cudaStream_t st) {
+// The slice product for rows [r0, r0 + n) and columns [c0, c0 + m) of C (r0
+// a multiple of the tile height, c0 of the tile width; C points at (r0, c0)).
+int slice_product(const EmuWork &w, int64_t r0, int64_t n, int64_t c0, int64_t m, int64_t P, double *C, int64_t ldc,
+                  int s, int kind, cudaStream_t st) {
     CUtensorMap tmA, tmB;
     const size_t es = fmt_esize(kind);
-    const int64_t nr = mm::ceil_div(n, BM) * BM;
+    const int bn = slice_bn(s);
+    const int64_t nr = mm::ceil_div(n, BM) * BM, mr = mm::ceil_div(m, bn) * bn;
     int rc = encode_slices(&tmA, w.sa + (size_t)r0 * w.L.Pp * es, nr, w.L.Pp, s, BM, kind, w.L.Nr);
-    if (!rc) rc = encode_slices(&tmB, w.sb, w.L.Mr, w.L.Pp, s, slice_bn(s), kind);
+    if (!rc) rc = encode_slices(&tmB, w.sb + (size_t)c0 * w.L.Pp * es, mr, w.L.Pp, s, bn, kind, w.L.Mr);
     if (rc) return rc;
     EmuParams prm{};
     fill_common(prm, s);
     prm.N = n;
     prm.P = P;
-    prm.M = M;
+    prm.M = m;
     prm.tiles_m = (int)mm::ceil_div(n, BM);
-    prm.tiles_n = (int)mm::ceil_div(M, slice_bn(s));
+    prm.tiles_n = (int)mm::ceil_div(m, bn);
     prm.ea = w.ea + r0;
-    prm.fb = w.fb;
+    prm.fb = w.fb + c0;
     prm.C = C;
     prm.ldc = ldc;
     prm.status = mm::device_status_ptr();
@@ -575,18 +578,20 @@ int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
                  double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st) {
     const EmuWork w = emu_work(N, P, M, s, kind, ws);
     int rc = split_a_rows(w, 0, N, P, A, lda, s, kind, st);
-    if (!rc) rc = split_b(w, P, M, B, ldb, s, kind, st);
-    if (!rc) rc = slice_product(w, 0, N, P, M, C, ldc, s, kind, st);
+    if (!rc) rc = split_b(w, 0, P, M, B, ldb, s, kind, st);
+    if (!rc) rc = slice_product(w, 0, N, 0, M, P, C, ldc, s, kind, st);
     return rc;
 }
 
 // Host operands: device copies of A, B and C and the split workspace are carved
-// from ws.  One copy stream carries B and then the row blocks of A; B is split
-// on the caller's stream as soon as it lands, each block's split and slice
-// product follow its copy, and its rows of C come back on a second copy stream
-// as soon as they are done, so transfers overlap the products of other blocks.  The caller's
-// stream waits for the last copy back, and the copy streams wait for the
-// caller's earlier work, so consecutive calls on one stream stay ordered.
+// from ws.  One copy stream carries the first row block of A, the column
+// blocks of B, then the other row blocks of A; each block of A or B is split
+// on the caller's stream as soon as it lands, each block product of C follows
+// the splits it needs, and its block of C comes back on a second copy stream
+// as soon as it is done, so transfers overlap the products of other blocks.
+// The caller's stream waits for the last copy back, and the copy streams wait
+// for the caller's earlier work, so consecutive calls on one stream stay
+// ordered.  Every block of C is computed exactly as in the one-launch product.
 size_t emulated_host_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind) {
     return align_up((size_t)N * P * 8, 1024) + align_up((size_t)P * M * 8, 1024) + align_up((size_t)N * M * 8, 1024) +
            layout(N, P, M, s, kind).total;
@@ -628,10 +633,35 @@ int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t 
     double *dC = (double *)w8;
     w8 += align_up((size_t)N * M * 8, 1024);
     const EmuWork w = emu_work(N, P, M, s, kind, w8);
-    // Up to 8 row blocks of whole tiles: the first product waits for B and one
-    // block of A, and the last block's copy back trails the products.
-    const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(8, ceil_div(N, 512)));
-    const int64_t R = ceil_div(ceil_div(N, nb), BM) * BM;
+    // C in blocks: up to 8 row blocks of whole tiles, and for large products
+    // (N >= 4096, M >= 2048) two column blocks, with row blocks sized so each
+    // block product fills whole waves (four column blocks measured slower: 16
+    // launches of 4 waves each).  The first product then waits for one block of
+    // A and half of B instead of all of B, and the last block's copy back
+    // trails the products.
+    constexpr int kMaxColBlocks = 2;
+    const int64_t cb = N >= 4096 && M >= 2048 ? 2 : 1;
+    const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(8 / cb, ceil_div(N, 512 * cb)));
+    int64_t R = ceil_div(ceil_div(N, nb), BM) * BM;
+    const int64_t Mh = ceil_div(ceil_div(M, cb), (int64_t)BN) * BN;  // column block width
+    if (cb > 1) {
+        // Row blocks of 8 to 24 tile rows, the height whose block products come
+        // closest to whole waves of the persistent kernel (ties: the shorter, so
+        // the first product starts sooner); e.g. 19 tile rows x 64 tile columns
+        // = 8 waves of 152 SMs.
+        const int64_t tn = ceil_div(Mh, (int64_t)slice_bn(s)), sms = sm_count();
+        double best = 2.0;
+        for (int64_t tr = 8; tr <= 24; ++tr) {
+            const int64_t t = tr * tn;
+            const double waste = (double)(ceil_div(t, sms) * sms - t) / (double)t;
+            if (waste < best - 1e-9) best = waste, R = tr * BM;
+        }
+    }
+    int64_t c0s[kMaxColBlocks], ms[kMaxColBlocks];
+    for (int j = 0; j < kMaxColBlocks; ++j) {
+        c0s[j] = std::min<int64_t>(j * Mh, M);
+        ms[j] = std::min<int64_t>(Mh, M - c0s[j]);
+    }
     std::vector<cudaEvent_t> ev;
     auto event = [&](cudaEvent_t *e) {
         cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
@@ -642,40 +672,54 @@ int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t 
         for (cudaEvent_t e : ev) cudaEventDestroy(e);  // released once their work completes
         return r;
     };
-    // All uploads go through one copy stream in the order they are needed: B
-    // first (every product needs all of it), then the row blocks of A, so the
-    // link is not shared between B and A blocks that cannot start yet.
-    cudaEvent_t e0, eB, eA, eC, eEnd;
+    // All uploads go through one copy stream in the order they are needed: the
+    // first block of A, the column blocks of B, then the other blocks of A, so
+    // the link is not shared with blocks that cannot start yet.
+    cudaEvent_t e0, eB[kMaxColBlocks] = {}, eA, eC, eEnd;
     cudaError_t e = event(&e0);
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.up, e0, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.down, e0, 0);
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(dB, (size_t)M * 8, B, (size_t)ldb * 8, (size_t)M * 8, P, cudaMemcpyHostToDevice, cs.up);
-    if (e == cudaSuccess) e = event(&eB);
-    if (e == cudaSuccess) e = cudaEventRecord(eB, cs.up);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, eB, 0);
     if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
-    rc = split_b(w, P, M, dB, M, s, kind, st);
-    if (rc) return done(rc);
+    auto upload_b = [&](int j) {
+        if (ms[j] <= 0) return cudaSuccess;
+        cudaError_t r = cudaMemcpy2DAsync(dB + c0s[j], (size_t)M * 8, B + c0s[j], (size_t)ldb * 8, (size_t)ms[j] * 8,
+                                          P, cudaMemcpyHostToDevice, cs.up);
+        if (r == cudaSuccess) r = event(&eB[j]);
+        if (r == cudaSuccess) r = cudaEventRecord(eB[j], cs.up);
+        return r;
+    };
     for (int64_t r0 = 0; r0 < N; r0 += R) {
         const int64_t n = std::min(R, N - r0);
         e = cudaMemcpy2DAsync(dA + r0 * P, (size_t)P * 8, A + r0 * lda, (size_t)lda * 8, (size_t)P * 8, n,
                               cudaMemcpyHostToDevice, cs.up);
         if (e == cudaSuccess) e = event(&eA);
         if (e == cudaSuccess) e = cudaEventRecord(eA, cs.up);
+        if (r0 == 0)
+            for (int j = 0; j < kMaxColBlocks && e == cudaSuccess; ++j) e = upload_b(j);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, eA, 0);
         if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
         rc = split_a_rows(w, r0, n, P, dA + r0 * P, P, s, kind, st);
-        if (!rc) rc = slice_product(w, r0, n, P, M, dC + r0 * M, M, s, kind, st);
         if (rc) return done(rc);
-        e = event(&eC);
-        if (e == cudaSuccess) e = cudaEventRecord(eC, st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.down, eC, 0);
-        if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(C + r0 * ldc, (size_t)ldc * 8, dC + r0 * M, (size_t)M * 8, (size_t)M * 8, n,
-                                  cudaMemcpyDeviceToHost, cs.down);
-        if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
+        for (int j = 0; j < kMaxColBlocks; ++j) {
+            const int64_t c0 = c0s[j], m = ms[j];
+            if (m <= 0) continue;
+            if (r0 == 0) {  // this column block of B is split as soon as it lands
+                e = cudaStreamWaitEvent(st, eB[j], 0);
+                if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
+                rc = split_b(w, c0, P, m, dB + c0, M, s, kind, st);
+                if (rc) return done(rc);
+            }
+            rc = slice_product(w, r0, n, c0, m, P, dC + r0 * M + c0, M, s, kind, st);
+            if (rc) return done(rc);
+            e = event(&eC);
+            if (e == cudaSuccess) e = cudaEventRecord(eC, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.down, eC, 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(C + r0 * ldc + c0, (size_t)ldc * 8, dC + r0 * M + c0, (size_t)M * 8,
+                                      (size_t)m * 8, n, cudaMemcpyDeviceToHost, cs.down);
+            if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
+        }
     }
     e = event(&eEnd);
     if (e == cudaSuccess) e = cudaEventRecord(eEnd, cs.down);

@@ -414,11 +414,13 @@ def test_emulated_fp8_group_matches_single_calls(mm, orc):
 
 # ------------------------------------------------- host-operand pipeline
 
-@pytest.mark.parametrize("shape", [(2500, 300, 190), (129, 65, 65), (1, 1, 1), (700, 1000, 64)])
+@pytest.mark.parametrize("shape", [(2500, 300, 190), (129, 65, 65), (1, 1, 1), (700, 1000, 64), (4100, 70, 2100),
+                                   (4500, 60, 4097)])
 @pytest.mark.parametrize("kind", [0, 1])
 def test_emulated_host_matches_device_call(mm, shape, kind):
-    """Row blocks copied up, multiplied and copied back on overlapping streams
-    give the device call's result bit for bit (ragged last block included)."""
+    """Blocks of C (row blocks, and from N = 4096, M = 2048 on two column blocks)
+    copied up, multiplied and copied back on overlapping streams give the
+    device call's result bit for bit (ragged last blocks included)."""
     a, b = pair(*shape, "log", 70 + kind)
     s = 8 if kind == 0 else 6
     ref = host(mm.emulated(dev(a), dev(b), nslices=s, kind=kind))
@@ -436,6 +438,23 @@ def test_emulated_host_pinned_strided_views(mm, orc):
     assert np.array_equal(c.numpy(), orc.split_product(a.numpy(), b.numpy(), 7, 8))
     mask = np.ones(big_c.shape, dtype=bool)
     mask[11:1041, 7:87] = False
+    assert np.all(big_c.numpy()[mask] == 0.0)
+
+
+def test_emulated_host_wide_strided_views(mm):
+    """Two column blocks of B and C taken from views with leading dimensions
+    larger than their widths, against the device call on the same values."""
+    import torch
+
+    big_a = torch.from_numpy(S.loguniform(4200, 90, 75)).pin_memory()
+    big_b = torch.from_numpy(S.loguniform(80, 4300, 76)).pin_memory()
+    big_c = torch.zeros((4220, 4310), dtype=torch.float64).pin_memory()
+    a, b, c = big_a[5:4155, 9:77], big_b[3:71, 17:4250], big_c[13:4163, 41:4274]
+    mm.emulated_host(a, b, out=c, nslices=8)
+    ref = host(mm.emulated(dev(np.ascontiguousarray(a.numpy())), dev(np.ascontiguousarray(b.numpy())), nslices=8))
+    assert np.array_equal(c.numpy(), ref)
+    mask = np.ones(big_c.shape, dtype=bool)
+    mask[13:4163, 41:4274] = False
     assert np.all(big_c.numpy()[mask] == 0.0)
 
 
