@@ -178,3 +178,22 @@ def test_batches_on_different_streams_overlap_on_the_device(srv):
             assert st["overlap_ms"] == 0.0
         else:
             assert st["overlap_ms"] > 0.2 * st["device_busy_ms"], st
+
+
+@pytest.mark.parametrize("ratio", ["0.5", "4"])
+def test_class_ratio_batches_correctly(srv, monkeypatch, ratio):
+    """MM_SERVER_CLASS_RATIO limits a batch to requests within a factor of the
+    oldest one's estimated time; a factor below 1 counts as 1, and the oldest
+    request is always taken, so every request completes, bit for bit as the
+    single-call path."""
+    mm, serving = srv
+    monkeypatch.setenv("MM_SERVER_CLASS_RATIO", ratio)
+    cases = [_case(50 + i, *sh) for i, sh in enumerate(SHAPES)]
+    with serving.Server(1 << 30, max_batch=64, nstreams=2, use_graphs=True) as s:
+        for i, (a, b, c) in enumerate(cases):
+            s.submit(a, b, c, tier=TIERS[i], tag=i)
+        assert s.wait(120) == 0
+        st = s.stats()
+        assert st["completed"] == len(cases) and st["rejected"] == 0
+    for i, (a, b, c) in enumerate(cases):
+        assert np.array_equal(c.numpy(), mm.emulated(a.cuda(), b.cuda(), tier=TIERS[i]).cpu().numpy()), f"request {i}"
