@@ -434,10 +434,12 @@ def autotuner(dev):
         a = torch.from_numpy(S.loguniform(n, n, S.stream_seed(3, 0))).to(dev)
         b = torch.from_numpy(S.loguniform(n, n, S.stream_seed(3, 1))).to(dev)
         model, _ = mm.emulated_choice(n, n, n, tier)
-        kind, slices, levels, ms = mm.tune_emulated(a, b, tier=tier)
-        out["emulated"].append({"n": n, "tier": tier, "tuned": {"format": kind, "slices": slices, "levels": levels},
+        kind, slices, levels, ms, tile = mm.tune_emulated(a, b, tier=tier)
+        out["emulated"].append({"n": n, "tier": tier,
+                                "tuned": {"format": kind, "slices": slices, "levels": levels, "tile": tile},
                                 "ms": ms, "tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
-                                "model": {"format": model[0], "slices": model[1], "levels": model[2]}})
+                                "model": {"format": model[0], "slices": model[1], "levels": model[2],
+                                          "tile": model[3]}})
         del a, b
         torch.cuda.empty_cache()
     mm.tune_clear()

@@ -244,6 +244,19 @@ int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, c
                 void *stream);
 
 /*
+ * mm_emulated with the slice product's output tile width chosen by the caller
+ * (no counterpart in the paper): tile_n = 64 (up to 8 slices; the default),
+ * 32 (any slice count: half the column padding on narrow products, at the
+ * N = 64 MMA rate, about 2/3 of the 64-column one), or 0 for the default.
+ * Same arguments, workspace (mm_emulated_workspace_bytes) and result bit for
+ * bit as mm_emulated; MM_ERR_ARG for any other width.  mm_tune_emulated picks
+ * the width per shape bucket and mm_emulated_auto uses the pick.
+ */
+int mm_emulated_tiled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                      double *C, int64_t ldc, int32_t kind, int32_t nslices, double tier, int32_t tile_n, void *ws,
+                      size_t ws_bytes, void *stream);
+
+/*
  * mm_emulated with HOST operands: A, B and C are host pointers (pinned memory
  * lets the copies overlap the products), `ws` is a device workspace of
  * mm_emulated_host_workspace_bytes bytes holding the device copies of A, B, C
@@ -295,22 +308,28 @@ size_t mm_emulated_noalloc_capacity(void);
  * the candidates are the two slice formats, each with the slice count the tier
  * needs (mm_emulated_slices; a format that cannot reach the tier is skipped),
  * times 0, 1 or 2 levels of Strassen-Winograd over the product (each level
- * leaving blocks of at least 512).
+ * leaving blocks of at least 512), and for the direct product (0 levels) the
+ * two tile widths of mm_emulated_tiled (64 and 32; 32 only past 8 slices).
  *   mm_tune_emulated times every candidate that fits ws (the faster of two
  *     runs after a warm-up, CUDA events on `stream`, which it synchronises) on
  *     the given operands, writing C each time, and records the fastest for the
  *     bucket (floor(log2 N), floor(log2 P), floor(log2 M), round(-log10 tier));
- *     the chosen format, slice count, level count and time are written to the
- *     optional outputs.  ws: mm_tune_emulated_workspace_bytes bytes.
+ *     the chosen format, slice count, level count, time and tile width are
+ *     written to the optional outputs.  ws: mm_tune_emulated_workspace_bytes
+ *     bytes.
  *   mm_tune_emulated_choice (host only, no device work) reports the choice for
  *     a shape and tier: the recorded one (returns 1) or, with none recorded,
  *     the model's (returns 0): the format whose slice pairs cost less at the
- *     nominal rates (an FP8-E4M3 pair at half a BF16 pair) and the level count
- *     of mm_strassen_emulated's levels = -1.  Negative status for a tier <= 0
- *     or one neither format reaches.
+ *     nominal rates (an FP8-E4M3 pair at half a BF16 pair), the level count
+ *     of mm_strassen_emulated's levels = -1, and the 32-column tile only where
+ *     the 64-column one would pad M by more than 3/2 of the 32-column padding
+ *     (in practice M <= 32).  `tile` (optional) receives the tile width (the
+ *     default width when levels > 0).  Negative status for a tier <= 0 or one
+ *     neither format reaches.
  *   mm_emulated_auto computes C = A B with that choice (the direct product for
- *     0 levels, else mm_strassen_emulated's variant 1); `used` (optional, 3
- *     host int32) receives format, slice count and levels.  Its result meets
+ *     0 levels, with the chosen tile width, else mm_strassen_emulated's
+ *     variant 1); `used` (optional, 4 host int32) receives format, slice
+ *     count, levels and tile width.  Its result meets
  *     the tier like mm_emulated's; it is bit-identical to the mm_emulated /
  *     mm_strassen_emulated call with the same choice.  Workspace:
  *     mm_emulated_auto_workspace_bytes.  Errors as for mm_emulated.
@@ -318,9 +337,9 @@ size_t mm_emulated_noalloc_capacity(void);
 size_t mm_tune_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, double tier);
 int mm_tune_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
                      double *C, int64_t ldc, double tier, void *ws, size_t ws_bytes, void *stream, int32_t *best_kind,
-                     int32_t *best_slices, int32_t *best_levels, double *best_ms);
+                     int32_t *best_slices, int32_t *best_levels, double *best_ms, int32_t *best_tile);
 int mm_tune_emulated_choice(int64_t N, int64_t P, int64_t M, double tier, int32_t *kind, int32_t *slices,
-                            int32_t *levels);
+                            int32_t *levels, int32_t *tile);
 size_t mm_emulated_auto_workspace_bytes(int64_t N, int64_t P, int64_t M, double tier);
 int mm_emulated_auto(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
                      double *C, int64_t ldc, double tier, void *ws, size_t ws_bytes, void *stream, int32_t *used);

@@ -14,7 +14,7 @@ import ctypes
 from ._native import KernelStat, MMError, check, lib
 
 __all__ = ["naive", "naive_unrolled", "kahan", "winograd", "winograd_scaled", "winograd_rowcol_scaled", "strassen", "strassen_winograd", "strassen_emulated", "tune_strassen", "tune_emulated", "emulated_choice", "emulated_auto", "tune_save", "tune_load", "tune_clear", "norm_inf",
-           "emulated", "emulated_host", "emulated_group", "emulated_noalloc", "emulated_slices", "probe_fp64_peak", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
+           "emulated", "emulated_tiled", "emulated_host", "emulated_group", "emulated_noalloc", "emulated_slices", "probe_fp64_peak", "profile", "device_status", "MMError", "lib", "SLICE_BF16",
            "SLICE_FP8E4M3"]
 
 SLICE_BF16 = 0
@@ -165,40 +165,42 @@ def tune_strassen(a, b, variant=0):
 
 def tune_emulated(a, b, tier=1e-14):
     """Times the emulated product's candidates (slice format x Strassen-Winograd
-    levels) for this shape and tier, records the fastest for the shape bucket
-    (used by emulated_auto and serving method 2) and returns
-    (format, slices, levels, ms)."""
+    levels, and for the direct product the tile width) for this shape and tier,
+    records the fastest for the shape bucket (used by emulated_auto and, for
+    format and count, serving method 2) and returns
+    (format, slices, levels, ms, tile width)."""
     a, b, c, n, p, m = _prep(a, b, None)
     need = lib().mm_tune_emulated_workspace_bytes(n, p, m, float(tier))
     ws = _ws(need, a.device)
-    k, s, lv, ms = ctypes.c_int32(-1), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+    k, s, lv, ms, tl = ctypes.c_int32(-1), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0), ctypes.c_int32(0)
     check("mm_tune_emulated", lib().mm_tune_emulated(*_gemm_args(a, b, c, n, p, m), float(tier), _ptr(ws), need,
                                                      _stream(a.device), ctypes.byref(k), ctypes.byref(s),
-                                                     ctypes.byref(lv), ctypes.byref(ms)))
-    return int(k.value), int(s.value), int(lv.value), float(ms.value)
+                                                     ctypes.byref(lv), ctypes.byref(ms), ctypes.byref(tl)))
+    return int(k.value), int(s.value), int(lv.value), float(ms.value), int(tl.value)
 
 
 def emulated_choice(n, p, m, tier=1e-14):
-    """The (format, slices, levels) emulated_auto uses for this shape and tier,
-    and whether it comes from the tuned table (host only)."""
-    k, s, lv = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    """The (format, slices, levels, tile width) emulated_auto uses for this
+    shape and tier, and whether it comes from the tuned table (host only)."""
+    k, s, lv, tl = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
     rc = lib().mm_tune_emulated_choice(int(n), int(p), int(m), float(tier), ctypes.byref(k), ctypes.byref(s),
-                                       ctypes.byref(lv))
+                                       ctypes.byref(lv), ctypes.byref(tl))
     if rc < 0:
         check("mm_tune_emulated_choice", rc)
-    return (int(k.value), int(s.value), int(lv.value)), rc == 1
+    return (int(k.value), int(s.value), int(lv.value), int(tl.value)), rc == 1
 
 
 def emulated_auto(a, b, tier=1e-14, out=None, return_choice=False):
     """FP64-accurate product with the autotuned (or modelled) format, slice
-    count and Strassen-Winograd levels for the tier (mm_emulated_auto)."""
+    count, Strassen-Winograd levels and tile width for the tier
+    (mm_emulated_auto)."""
     a, b, c, n, p, m = _prep(a, b, out)
     need = lib().mm_emulated_auto_workspace_bytes(n, p, m, float(tier))
     ws = _ws(need, a.device)
-    used = (ctypes.c_int32 * 3)()
+    used = (ctypes.c_int32 * 4)()
     check("mm_emulated_auto", lib().mm_emulated_auto(*_gemm_args(a, b, c, n, p, m), float(tier), _ptr(ws), need,
                                                      _stream(a.device), used))
-    return (c, (int(used[0]), int(used[1]), int(used[2]))) if return_choice else c
+    return (c, tuple(int(u) for u in used)) if return_choice else c
 
 
 def tune_save(path):
@@ -236,6 +238,17 @@ def emulated(a, b, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
     ws = _ws(need, a.device)
     check("mm_emulated", lib().mm_emulated(*_gemm_args(a, b, c, n, p, m), kind, nslices, float(tier), _ptr(ws), need,
                                            _stream(a.device)))
+    return c
+
+
+def emulated_tiled(a, b, tile_n, nslices=0, tier=1e-14, kind=SLICE_BF16, out=None):
+    """mm_emulated with the slice product's tile width chosen (64, 32, or 0 for
+    the default); the result is bit-identical to emulated()."""
+    a, b, c, n, p, m = _prep(a, b, out)
+    need = lib().mm_emulated_workspace_bytes(n, p, m, kind, nslices, tier)
+    ws = _ws(need, a.device)
+    check("mm_emulated_tiled", lib().mm_emulated_tiled(*_gemm_args(a, b, c, n, p, m), kind, nslices, float(tier),
+                                                       int(tile_n), _ptr(ws), need, _stream(a.device)))
     return c
 
 

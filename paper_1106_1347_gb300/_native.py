@@ -68,6 +68,7 @@ SIGNATURES = {
     "mm_emulated_host_workspace_bytes": (sz, [i64, i64, i64, i32, i32, dbl]),
     "mm_emulated_host": (ctypes.c_int, GEMM + [i32, i32, dbl, vp, sz, vp]),
     "mm_emulated": (ctypes.c_int, GEMM + [i32, i32, dbl, vp, sz, vp]),
+    "mm_emulated_tiled": (ctypes.c_int, GEMM + [i32, i32, dbl, i32, vp, sz, vp]),
     "mm_emulated_slices": (ctypes.c_int, [i32, i32, dbl]),
     "mm_emulated_noalloc": (ctypes.c_int, GEMM + [i32, i32, dbl, vp]),
     "mm_emulated_noalloc_capacity": (sz, []),
@@ -84,9 +85,9 @@ SIGNATURES = {
     "mm_tune_strassen": (ctypes.c_int, [i32] + GEMM + [vp, sz, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
     "mm_tune_emulated_workspace_bytes": (sz, [i64, i64, i64, dbl]),
     "mm_tune_emulated": (ctypes.c_int, GEMM + [dbl, vp, sz, vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
-                                                ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
+                                               ctypes.POINTER(i32), ctypes.POINTER(dbl), ctypes.POINTER(i32)]),
     "mm_tune_emulated_choice": (ctypes.c_int, [i64, i64, i64, dbl, ctypes.POINTER(i32), ctypes.POINTER(i32),
-                                                ctypes.POINTER(i32)]),
+                                               ctypes.POINTER(i32), ctypes.POINTER(i32)]),
     "mm_emulated_auto_workspace_bytes": (sz, [i64, i64, i64, dbl]),
     "mm_emulated_auto": (ctypes.c_int, GEMM + [dbl, vp, sz, vp, ctypes.POINTER(i32)]),
     "mm_tune_save": (ctypes.c_int, [ctypes.c_char_p]),

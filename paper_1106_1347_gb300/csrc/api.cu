@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "slice_gemm.cuh"
 
 // Device status word raised by bounded waits (one per device context).
 static __device__ int g_device_status;
@@ -325,21 +326,36 @@ static int slices_or_fail(const char *fn, int32_t kind, int32_t nslices, double 
     return s;
 }
 
-int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
-                double *C, int64_t ldc, int32_t kind, int32_t nslices, double tier, void *ws, size_t ws_bytes,
-                void *stream) {
-    int rc = check_gemm_args("mm_emulated", N, P, M, A, lda, B, ldb, C, ldc);
+static int emulated_call(const char *fn, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda,
+                         const double *B, int64_t ldb, double *C, int64_t ldc, int32_t kind, int32_t nslices,
+                         double tier, int32_t tile_n, void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_gemm_args(fn, N, P, M, A, lda, B, ldb, C, ldc);
     if (rc) return rc;
-    const int s = slices_or_fail("mm_emulated", kind, nslices, tier);
+    const int s = slices_or_fail(fn, kind, nslices, tier);
     if (s < 0) return s;
-    if (P > (int64_t(1) << 20)) return fail(MM_ERR_UNSUPPORTED, "mm_emulated: P > 2^20");
+    if (tile_n != 0 && !emu::slice_bn_ok(s, tile_n))
+        return fail(MM_ERR_ARG, "%s: tile width %d (0, 32, or 64 up to 8 slices)", fn, (int)tile_n);
+    if (P > (int64_t(1) << 20)) return fail(MM_ERR_UNSUPPORTED, "%s: P > 2^20", fn);
     cudaStream_t st = (cudaStream_t)stream;
     if (N == 0 || M == 0) return MM_OK;
     if (P == 0) return run_zero(N, M, C, ldc, st);
     size_t need = emulated_ws_bytes(N, P, M, s, kind);
     if (ws_bytes < need || !ws)
-        return fail(MM_ERR_WORKSPACE, "mm_emulated: workspace %zu bytes < %zu required", ws_bytes, need);
-    return run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st);
+        return fail(MM_ERR_WORKSPACE, "%s: workspace %zu bytes < %zu required", fn, ws_bytes, need);
+    return run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st, tile_n);
+}
+
+int mm_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                double *C, int64_t ldc, int32_t kind, int32_t nslices, double tier, void *ws, size_t ws_bytes,
+                void *stream) {
+    return emulated_call("mm_emulated", N, P, M, A, lda, B, ldb, C, ldc, kind, nslices, tier, 0, ws, ws_bytes, stream);
+}
+
+int mm_emulated_tiled(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
+                      double *C, int64_t ldc, int32_t kind, int32_t nslices, double tier, int32_t tile_n, void *ws,
+                      size_t ws_bytes, void *stream) {
+    return emulated_call("mm_emulated_tiled", N, P, M, A, lda, B, ldb, C, ldc, kind, nslices, tier, tile_n, ws,
+                         ws_bytes, stream);
 }
 
 size_t mm_emulated_host_workspace_bytes(int64_t N, int64_t P, int64_t M, int32_t kind, int32_t nslices,
@@ -455,8 +471,8 @@ int mm_strassen_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64
 }
 
 size_t mm_emulated_auto_workspace_bytes(int64_t N, int64_t P, int64_t M, double tier) {
-    int kind, s, levels;
-    if (N <= 0 || P <= 0 || M <= 0 || emulated_choice(N, P, M, tier, &kind, &s, &levels) < 0) return 0;
+    int kind, s, levels, tile;
+    if (N <= 0 || P <= 0 || M <= 0 || emulated_choice(N, P, M, tier, &kind, &s, &levels, &tile) < 0) return 0;
     return levels == 0 ? emulated_ws_bytes(N, P, M, s, kind)
                        : strassen_emulated_ws_bytes(1, levels, N, P, M, s, kind);
 }
@@ -471,8 +487,8 @@ int mm_emulated_auto(int64_t N, int64_t P, int64_t M, const double *A, int64_t l
     cudaStream_t st = (cudaStream_t)stream;
     if (N == 0 || M == 0) return MM_OK;
     if (P == 0) return run_zero(N, M, C, ldc, st);
-    int kind, s, levels;
-    if (emulated_choice(N, P, M, tier, &kind, &s, &levels) < 0)
+    int kind, s, levels, tile;
+    if (emulated_choice(N, P, M, tier, &kind, &s, &levels, &tile) < 0)
         return fail(MM_ERR_UNSUPPORTED, "%s: tier %g needs more slices than either format holds", fn, tier);
     const size_t need = levels == 0 ? emulated_ws_bytes(N, P, M, s, kind)
                                     : strassen_emulated_ws_bytes(1, levels, N, P, M, s, kind);
@@ -482,8 +498,9 @@ int mm_emulated_auto(int64_t N, int64_t P, int64_t M, const double *A, int64_t l
         used[0] = kind;
         used[1] = s;
         used[2] = levels;
+        used[3] = levels == 0 ? tile : emu::slice_bn(s);
     }
-    return levels == 0 ? run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st)
+    return levels == 0 ? run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st, tile)
                        : run_strassen_emulated(1, levels, N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st);
 }
 

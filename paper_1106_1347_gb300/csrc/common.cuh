@@ -110,7 +110,7 @@ constexpr int kWinogradSafeDepth = 6;
 // The emulated product's slice format, count and Strassen-Winograd levels for
 // a tier (tune.cu): the tuned entry of the shape bucket (returns 1), else the
 // model (returns 0); negative for an invalid or unreachable tier.
-int emulated_choice(int64_t N, int64_t P, int64_t M, double tier, int *kind, int *slices, int *levels);
+int emulated_choice(int64_t N, int64_t P, int64_t M, double tier, int *kind, int *slices, int *levels, int *tile);
 size_t strassen_ws_bytes(int variant, int depth, int64_t Np, int64_t Pp, int64_t Mp);
 int run_strassen(int variant, int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B,
                  int64_t ldb, double *C, int64_t ldc, int depth, int64_t Np, int64_t Pp, int64_t Mp, void *ws,
@@ -126,8 +126,10 @@ int run_strassen_level(int variant, int64_t nodes, int64_t n, int64_t p, int64_t
 int emulated_slices(int32_t kind, int32_t nslices, double tier);
 // kind: MM_SLICE_BF16 or MM_SLICE_FP8E4M3.
 size_t emulated_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind);
+// bn: the slice product's tile width (64 or 32 columns; 0: 64 up to 8 slices, 32 beyond).
 int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
-                 double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st);
+                 double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st,
+                 int bn = 0);
 size_t emulated_group_ws_bytes(const mm_problem *probs, int count, int s, int kind);
 size_t emulated_host_ws_bytes(int64_t N, int64_t P, int64_t M, int s, int kind);
 int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
@@ -141,12 +143,13 @@ struct GroupLaunch {
     const int64_t *begin[5];  // device prefix arrays
     int64_t grid[5];          // CTAs per kernel (grid-stride kernels: any size works)
     int s, kind;              // slice count and format
+    int bn;                   // tile width of the slice product
 };
 size_t group_table_bytes(int count);
 size_t problem_data_bytes(const mm_problem &q, int s, int kind = MM_SLICE_BF16);
 size_t group_data_bytes(const mm_problem *probs, int count, int s, int kind = MM_SLICE_BF16);
 int group_build(const mm_problem *probs, int count, int capacity, int s, void *table_dev, char *const *data,
-                std::vector<unsigned char> &image, GroupLaunch &gl, int kind = MM_SLICE_BF16);
+                std::vector<unsigned char> &image, GroupLaunch &gl, int kind = MM_SLICE_BF16, int bn = 0);
 int group_kernels(const GroupLaunch &gl, cudaStream_t st);
 int64_t group_grid_cap(int kernel);  // fixed grid of grouped kernel `kernel` (0..4)
 void prof_suspend(bool on);  // skip kernel timing while a stream is being captured

@@ -432,7 +432,7 @@ int encode_slices(CUtensorMap *map, void *base, int64_t rows, int64_t Pp, int s,
 // (the rest -- stages, exact chunk, TMEM columns -- follow from s at compile time).
 void fill_common(EmuParams &prm, int s) { prm.s = s; }
 
-size_t slice_smem_bytes(int s) { return (size_t)slice_stages(s) * slice_stage_bytes(s) + 1024; }
+size_t slice_smem_bytes(int s, int bn) { return (size_t)slice_stages(s, bn) * slice_stage_bytes(s, bn) + 1024; }
 
 
 }  // namespace
@@ -535,10 +535,9 @@ int split_a_rows(const EmuWork &w, int64_t r0, int64_t n, int64_t P, const doubl
 // The slice product for rows [r0, r0 + n) and columns [c0, c0 + m) of C (r0
 // a multiple of the tile height, c0 of the tile width; C points at (r0, c0)).
 int slice_product(const EmuWork &w, int64_t r0, int64_t n, int64_t c0, int64_t m, int64_t P, double *C, int64_t ldc,
-                  int s, int kind, cudaStream_t st) {
+                  int s, int kind, cudaStream_t st, int bn) {
     CUtensorMap tmA, tmB;
     const size_t es = fmt_esize(kind);
-    const int bn = slice_bn(s);
     const int64_t nr = mm::ceil_div(n, BM) * BM, mr = mm::ceil_div(m, bn) * bn;
     int rc = encode_slices(&tmA, w.sa + (size_t)r0 * w.L.Pp * es, nr, w.L.Pp, s, BM, kind, w.L.Nr);
     if (!rc) rc = encode_slices(&tmB, w.sb + (size_t)c0 * w.L.Pp * es, mr, w.L.Pp, s, bn, kind, w.L.Mr);
@@ -555,7 +554,7 @@ int slice_product(const EmuWork &w, int64_t r0, int64_t n, int64_t c0, int64_t m
     prm.C = C;
     prm.ldc = ldc;
     prm.status = mm::device_status_ptr();
-    const size_t smem = slice_smem_bytes(s);
+    const size_t smem = slice_smem_bytes(s, bn);
     const cudaError_t attr_err = slice_smem_attributes();
     if (attr_err != cudaSuccess) return mm::cuda_fail(attr_err, "mm_emulated: shared memory attribute");
     const int64_t tiles = (int64_t)prm.tiles_m * prm.tiles_n;
@@ -563,8 +562,8 @@ int slice_product(const EmuWork &w, int64_t r0, int64_t n, int64_t c0, int64_t m
     const bool fp8 = kind == MM_SLICE_FP8E4M3;
     cudaError_t le = cudaSuccess;
     rc = mm::launch(fp8 ? "emu_slice_gemm_tcgen05_fp8" : "emu_slice_gemm_tcgen05", st, [&] {
-        le = fp8 ? launch_slice_gemm_fp8(s, grid, smem, st, tmA, tmB, prm)
-                 : launch_slice_gemm_bf16(s, grid, smem, st, tmA, tmB, prm);
+        le = fp8 ? launch_slice_gemm_fp8(s, bn, grid, smem, st, tmA, tmB, prm)
+                 : launch_slice_gemm_bf16(s, bn, grid, smem, st, tmA, tmB, prm);
     });
     if (!rc && le != cudaSuccess) return mm::cuda_fail(le, "mm_emulated: slice count");
     return rc;
@@ -575,11 +574,14 @@ int slice_product(const EmuWork &w, int64_t r0, int64_t n, int64_t c0, int64_t m
 namespace mm {
 
 int run_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
-                 double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st) {
+                 double *C, int64_t ldc, int s, int kind, void *ws, cudaStream_t st, int bn) {
+    if (bn == 0) bn = slice_bn(s);
+    if (!slice_bn_ok(s, bn))
+        return fail(MM_ERR_ARG, "mm_emulated: tile width %d (64 up to 8 slices, or 32)", bn);
     const EmuWork w = emu_work(N, P, M, s, kind, ws);
     int rc = split_a_rows(w, 0, N, P, A, lda, s, kind, st);
     if (!rc) rc = split_b(w, 0, P, M, B, ldb, s, kind, st);
-    if (!rc) rc = slice_product(w, 0, N, 0, M, P, C, ldc, s, kind, st);
+    if (!rc) rc = slice_product(w, 0, N, 0, M, P, C, ldc, s, kind, st, bn);
     return rc;
 }
 
@@ -710,7 +712,7 @@ int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t 
                 rc = split_b(w, c0, P, m, dB + c0, M, s, kind, st);
                 if (rc) return done(rc);
             }
-            rc = slice_product(w, r0, n, c0, m, P, dC + r0 * M + c0, M, s, kind, st);
+            rc = slice_product(w, r0, n, c0, m, P, dC + r0 * M + c0, M, s, kind, st, slice_bn(s));
             if (rc) return done(rc);
             e = event(&eC);
             if (e == cudaSuccess) e = cudaEventRecord(eC, st);
@@ -853,9 +855,9 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
         rc = launch(fp8 ? "emu_group_slice_gemm_tcgen05_fp8" : "emu_group_slice_gemm_tcgen05", st, [&] {
             const auto *tab = (const EmuProblem *)gl.tab;
             const auto *hdr = (const GroupHeader *)gl.hdr;
-            const size_t smem = slice_smem_bytes(gl.s);
-            le = fp8 ? launch_group_slice_gemm_fp8(gl.s, tiles_grid, smem, st, tab, gl.begin[U_TILES], hdr)
-                     : launch_group_slice_gemm_bf16(gl.s, tiles_grid, smem, st, tab, gl.begin[U_TILES], hdr);
+            const size_t smem = slice_smem_bytes(gl.s, gl.bn);
+            le = fp8 ? launch_group_slice_gemm_fp8(gl.s, gl.bn, tiles_grid, smem, st, tab, gl.begin[U_TILES], hdr)
+                     : launch_group_slice_gemm_bf16(gl.s, gl.bn, tiles_grid, smem, st, tab, gl.begin[U_TILES], hdr);
         });
         if (!rc && le != cudaSuccess) return cuda_fail(le, "grouped emulated product: slice count");
     }
@@ -867,8 +869,10 @@ int group_kernels(const GroupLaunch &gl, cudaStream_t st) {
 // problem i's data region of problem_data_bytes(probs[i], s, kind) bytes; the
 // table is laid out for `capacity` problems (>= count).
 int group_build(const mm_problem *probs, int count, int capacity, int s, void *table_dev, char *const *data,
-                std::vector<unsigned char> &image, GroupLaunch &gl, int kind) {
+                std::vector<unsigned char> &image, GroupLaunch &gl, int kind, int bn) {
     if (capacity < count) return fail(MM_ERR_ARG, "grouped launch: %d problems exceed capacity %d", count, capacity);
+    if (bn == 0) bn = slice_bn(s);
+    if (!slice_bn_ok(s, bn)) return fail(MM_ERR_ARG, "grouped launch: tile width %d", bn);
     const GroupLayout G = group_layout(capacity);
     char *t = (char *)table_dev;
     image.assign(G.table_bytes, 0);
@@ -907,14 +911,14 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
         e.prm.P = q.P;
         e.prm.M = q.M;
         e.prm.tiles_m = (int)ceil_div(q.N, BM);
-        e.prm.tiles_n = (int)ceil_div(q.M, slice_bn(s));
+        e.prm.tiles_n = (int)ceil_div(q.M, bn);
         e.prm.ea = ea;
         e.prm.fb = fb;
         e.prm.C = q.C;
         e.prm.ldc = q.ldc;
         e.prm.status = status;
         int rc = encode_slices(&e.tmA, sa, L.Nr, L.Pp, s, BM, kind);
-        if (!rc) rc = encode_slices(&e.tmB, sb, L.Mr, L.Pp, s, slice_bn(s), kind);
+        if (!rc) rc = encode_slices(&e.tmB, sb, L.Mr, L.Pp, s, bn, kind);
         if (rc) return rc;
         for (int k = 0; k < 5; ++k) begin[k][i] = units[k];
         units[U_ROWS] += L.Pp <= kQuarterRowMax ? ceil_div(q.N, kRowThreads / 8)
@@ -936,6 +940,7 @@ int group_build(const mm_problem *probs, int count, int capacity, int s, void *t
     gl.hdr = t + G.off_hdr;
     gl.s = s;
     gl.kind = kind;
+    gl.bn = bn;
     return MM_OK;
 }
 

@@ -155,8 +155,8 @@ void choose_slices(int method, const mm_request &r, int *s, int *kind) {
     *kind = MM_SLICE_BF16;
     *s = mm::emulated_slices(MM_SLICE_BF16, 0, r.tier);
     if (method != 2) return;
-    int k = 0, n = 0, levels = 0;
-    if (mm::emulated_choice(r.N, r.P, r.M, r.tier, &k, &n, &levels) >= 0) {
+    int k = 0, n = 0, levels = 0, tile = 0;  // a batch runs with the default tile width
+    if (mm::emulated_choice(r.N, r.P, r.M, r.tier, &k, &n, &levels, &tile) >= 0) {
         *kind = k;
         *s = n;
     }

@@ -32,29 +32,31 @@ __host__ __device__ constexpr int fmt_pair_blocks(int kind) {
 // diagonals of 32 columns.
 __host__ __device__ constexpr int fmt_max_slices(int kind) { return kind == MM_SLICE_FP8E4M3 ? 10 : 8; }
 // Output tile width for s slices: 64 columns per diagonal up to 8 slices, 32
-// beyond (so s accumulators still fit TMEM's 512 columns).
+// beyond (so s accumulators still fit TMEM's 512 columns).  Up to 8 slices a
+// narrow tile of 32 columns is the other choice (half the padding on narrow
+// products, at the N = 64 MMA rate); the autotuner picks between the two.
 __host__ __device__ constexpr int slice_bn(int s) { return s > 8 ? 32 : BN; }
+__host__ __device__ constexpr bool slice_bn_ok(int s, int bn) { return bn == 32 || (bn == BN && s <= 8); }
 // Launch-wide constants of the slice product, functions of the slice format
 // and count only (so the kernel, templated on both, has them at compile time):
 // a stage holds one K-block (64 bytes per slice row) of all s slices of A and
 // B; up to 4 stages fit the shared memory; an exact chunk is the exact length
 // of diagonal s - 1; TMEM is allocated in powers of two >= 32 columns.
 constexpr int kSmemLimit = 232448;  // opt-in dynamic shared memory per block on sm_103
-__host__ __device__ constexpr uint32_t slice_stage_bytes(int s) {
-    return (uint32_t)s * (BM + slice_bn(s)) * KB_BYTES;
-}
-__host__ __device__ constexpr int slice_stages(int s) {
-    return (int)((kSmemLimit - 2048) / slice_stage_bytes(s)) < 4 ? (int)((kSmemLimit - 2048) / slice_stage_bytes(s)) : 4;
+__host__ __device__ constexpr uint32_t slice_stage_bytes(int s, int bn) { return (uint32_t)s * (BM + bn) * KB_BYTES; }
+__host__ __device__ constexpr int slice_stages(int s, int bn) {
+    return (int)((kSmemLimit - 2048) / slice_stage_bytes(s, bn)) < 4 ? (int)((kSmemLimit - 2048) / slice_stage_bytes(s, bn))
+                                                                      : 4;
 }
 __host__ __device__ constexpr int slice_chunk_blocks(int kind, int s) {
     return fmt_pair_blocks(kind) / s > 1 ? fmt_pair_blocks(kind) / s : 1;
 }
-__host__ __device__ constexpr uint32_t slice_tmem_cols(int s) {
-    return (uint32_t)(s * slice_bn(s) <= 32    ? 32
-                      : s * slice_bn(s) <= 64  ? 64
-                      : s * slice_bn(s) <= 128 ? 128
-                      : s * slice_bn(s) <= 256 ? 256
-                                               : 512);
+__host__ __device__ constexpr uint32_t slice_tmem_cols(int s, int bn) {
+    return (uint32_t)(s * bn <= 32    ? 32
+                      : s * bn <= 64  ? 64
+                      : s * bn <= 128 ? 128
+                      : s * bn <= 256 ? 256
+                                      : 512);
 }
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -210,8 +212,9 @@ struct TileJob {
 // last chunk of the current one is in the tensor pipe, and its MMAs start as
 // soon as the epilogue has read the accumulators out -- the final rounding and
 // the stores of C overlap them.  The slice count kS is a template parameter,
-// and with it the stage count, the exact chunk and the TMEM columns.
-template <bool kFP8, int kS, class Tiles>
+// and with it the stage count, the exact chunk and the TMEM columns; so is
+// the tile width kBN (64, or 32).
+template <bool kFP8, int kS, int kBN, class Tiles>
 __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, const EmuParams &c,
                                             bool maps_in_global) {
     extern __shared__ uint8_t smem_raw[];
@@ -223,11 +226,12 @@ __device__ __forceinline__ void slice_tiles(const Tiles &tiles, int64_t total, c
     constexpr int bke = fmt_bke(KIND), pair_blocks = fmt_pair_blocks(KIND);
     static_assert(kS >= 1 && kS <= fmt_max_slices(KIND), "1 to 8 BF16 or 1 to 10 FP8-E4M3 slices");
     constexpr int s = kS;
-    constexpr int TBN = slice_bn(s);  // tile width: 64, or 32 past 8 slices
-    constexpr int CPT = TBN / 2;      // columns each epilogue thread drains and rounds
-    constexpr int S = slice_stages(s), CB = slice_chunk_blocks(KIND, s);
+    static_assert(slice_bn_ok(kS, kBN), "64-column tiles up to 8 slices, 32-column tiles for any count");
+    constexpr int TBN = kBN;      // tile width
+    constexpr int CPT = TBN / 2;  // columns each epilogue thread drains and rounds
+    constexpr int S = slice_stages(s, TBN), CB = slice_chunk_blocks(KIND, s);
     constexpr uint32_t a_bytes = (uint32_t)s * BM * KB_BYTES, b_bytes = (uint32_t)s * TBN * KB_BYTES;
-    constexpr uint32_t stage_bytes = slice_stage_bytes(s), tmem_cols = slice_tmem_cols(s);
+    constexpr uint32_t stage_bytes = slice_stage_bytes(s, TBN), tmem_cols = slice_tmem_cols(s, TBN);
     static_assert(a_bytes + b_bytes == stage_bytes, "stage layout");
     uint64_t *full = bars, *empty = bars + 8, *acc_full = bars + 16, *acc_empty = bars + 17, *mma_done = bars + 18;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -458,12 +462,12 @@ struct SingleTiles {
     }
 };
 
-template <bool kFP8, int kS>
+template <bool kFP8, int kS, int kBN>
 __global__ void __launch_bounds__(kThreads, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const EmuParams p) {
     const SingleTiles tiles{&tmA, &tmB, &p};
-    slice_tiles<kFP8, kS>(tiles, (int64_t)p.tiles_m * p.tiles_n, p, false);
+    slice_tiles<kFP8, kS, kBN>(tiles, (int64_t)p.tiles_m * p.tiles_n, p, false);
 }
 
 // ------------------------------------------------------------ grouped launch
@@ -516,66 +520,93 @@ struct GroupTiles {
     }
 };
 
-template <bool kFP8, int kS>
+template <bool kFP8, int kS, int kBN>
 __global__ void __launch_bounds__(kThreads, 1) group_slice_gemm_kernel(const EmuProblem *tab, const int64_t *begin,
                                                                        const GroupHeader *hdr) {
     const int64_t total = hdr->units[U_TILES];
     if (total <= 0) return;
     const GroupTiles tiles{tab, begin, hdr->count};
     const EmuParams c = tab[0].prm;  // one slice format and count per launch: the constants are common
-    slice_tiles<kFP8, kS>(tiles, total, c, true);
+    slice_tiles<kFP8, kS, kBN>(tiles, total, c, true);
 }
 
 // Launchers, one per slice format (defined in slice_gemm_bf16.cu and
 // slice_gemm_fp8.cu): launch the instantiation for slice count s (1..8 BF16,
-// 1..10 FP8-E4M3) with the given grid and dynamic shared memory on st.
-// cudaErrorInvalidValue for an s outside that range (nothing is launched);
-// otherwise cudaSuccess, launch errors are left for cudaGetLastError.
-cudaError_t launch_slice_gemm_bf16(int s, unsigned grid, size_t smem, cudaStream_t st, const CUtensorMap &tmA,
+// 1..10 FP8-E4M3) and tile width bn (64 up to 8 slices, or 32) with the given
+// grid and dynamic shared memory on st.  cudaErrorInvalidValue for an (s, bn)
+// outside that range (nothing is launched); otherwise cudaSuccess, launch
+// errors are left for cudaGetLastError.
+cudaError_t launch_slice_gemm_bf16(int s, int bn, unsigned grid, size_t smem, cudaStream_t st, const CUtensorMap &tmA,
                                    const CUtensorMap &tmB, const EmuParams &prm);
-cudaError_t launch_slice_gemm_fp8(int s, unsigned grid, size_t smem, cudaStream_t st, const CUtensorMap &tmA,
+cudaError_t launch_slice_gemm_fp8(int s, int bn, unsigned grid, size_t smem, cudaStream_t st, const CUtensorMap &tmA,
                                   const CUtensorMap &tmB, const EmuParams &prm);
-cudaError_t launch_group_slice_gemm_bf16(int s, unsigned grid, size_t smem, cudaStream_t st, const EmuProblem *tab,
-                                         const int64_t *begin, const GroupHeader *hdr);
-cudaError_t launch_group_slice_gemm_fp8(int s, unsigned grid, size_t smem, cudaStream_t st, const EmuProblem *tab,
-                                        const int64_t *begin, const GroupHeader *hdr);
+cudaError_t launch_group_slice_gemm_bf16(int s, int bn, unsigned grid, size_t smem, cudaStream_t st,
+                                         const EmuProblem *tab, const int64_t *begin, const GroupHeader *hdr);
+cudaError_t launch_group_slice_gemm_fp8(int s, int bn, unsigned grid, size_t smem, cudaStream_t st,
+                                        const EmuProblem *tab, const int64_t *begin, const GroupHeader *hdr);
 // Opt every instantiation of one format into `bytes` of dynamic shared memory.
 cudaError_t slice_gemm_smem_attributes_bf16(int bytes);
 cudaError_t slice_gemm_smem_attributes_fp8(int bytes);
 
-// Dispatch by slice count over the instantiations (used only by the two
-// instantiating translation units).
+// Dispatch by slice count and tile width over the instantiations (used only by
+// the two instantiating translation units).
 template <bool kFP8, int kS = 1>
-cudaError_t dispatch_slice_gemm(int s, unsigned grid, size_t smem, cudaStream_t st, const CUtensorMap &tmA,
+cudaError_t dispatch_slice_gemm(int s, int bn, unsigned grid, size_t smem, cudaStream_t st, const CUtensorMap &tmA,
                                 const CUtensorMap &tmB, const EmuParams &prm) {
     if (s == kS) {
-        slice_gemm_kernel<kFP8, kS><<<grid, kThreads, smem, st>>>(tmA, tmB, prm);
-        return cudaSuccess;
+        if (bn == 32) {
+            slice_gemm_kernel<kFP8, kS, 32><<<grid, kThreads, smem, st>>>(tmA, tmB, prm);
+            return cudaSuccess;
+        }
+        if constexpr (slice_bn_ok(kS, BN)) {
+            if (bn == BN) {
+                slice_gemm_kernel<kFP8, kS, BN><<<grid, kThreads, smem, st>>>(tmA, tmB, prm);
+                return cudaSuccess;
+            }
+        }
+        return cudaErrorInvalidValue;
     }
     if constexpr (kS < fmt_max_slices(kFP8 ? MM_SLICE_FP8E4M3 : MM_SLICE_BF16))
-        return dispatch_slice_gemm<kFP8, kS + 1>(s, grid, smem, st, tmA, tmB, prm);
+        return dispatch_slice_gemm<kFP8, kS + 1>(s, bn, grid, smem, st, tmA, tmB, prm);
     return cudaErrorInvalidValue;
 }
 
 template <bool kFP8, int kS = 1>
-cudaError_t dispatch_group_slice_gemm(int s, unsigned grid, size_t smem, cudaStream_t st, const EmuProblem *tab,
+cudaError_t dispatch_group_slice_gemm(int s, int bn, unsigned grid, size_t smem, cudaStream_t st, const EmuProblem *tab,
                                       const int64_t *begin, const GroupHeader *hdr) {
     if (s == kS) {
-        group_slice_gemm_kernel<kFP8, kS><<<grid, kThreads, smem, st>>>(tab, begin, hdr);
-        return cudaSuccess;
+        if (bn == 32) {
+            group_slice_gemm_kernel<kFP8, kS, 32><<<grid, kThreads, smem, st>>>(tab, begin, hdr);
+            return cudaSuccess;
+        }
+        if constexpr (slice_bn_ok(kS, BN)) {
+            if (bn == BN) {
+                group_slice_gemm_kernel<kFP8, kS, BN><<<grid, kThreads, smem, st>>>(tab, begin, hdr);
+                return cudaSuccess;
+            }
+        }
+        return cudaErrorInvalidValue;
     }
     if constexpr (kS < fmt_max_slices(kFP8 ? MM_SLICE_FP8E4M3 : MM_SLICE_BF16))
-        return dispatch_group_slice_gemm<kFP8, kS + 1>(s, grid, smem, st, tab, begin, hdr);
+        return dispatch_group_slice_gemm<kFP8, kS + 1>(s, bn, grid, smem, st, tab, begin, hdr);
     return cudaErrorInvalidValue;
+}
+
+template <bool kFP8, int kS, int kBN>
+cudaError_t set_one_slice_gemm_smem(int bytes) {
+    cudaError_t e = cudaFuncSetAttribute((const void *)slice_gemm_kernel<kFP8, kS, kBN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)group_slice_gemm_kernel<kFP8, kS, kBN>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
 }
 
 template <bool kFP8, int kS = 1>
 cudaError_t set_slice_gemm_smem(int bytes) {
-    cudaError_t e = cudaFuncSetAttribute((const void *)slice_gemm_kernel<kFP8, kS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute((const void *)group_slice_gemm_kernel<kFP8, kS>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = set_one_slice_gemm_smem<kFP8, kS, 32>(bytes);
+    if constexpr (slice_bn_ok(kS, BN))
+        if (e == cudaSuccess) e = set_one_slice_gemm_smem<kFP8, kS, BN>(bytes);
     if constexpr (kS < fmt_max_slices(kFP8 ? MM_SLICE_FP8E4M3 : MM_SLICE_BF16))
         if (e == cudaSuccess) return set_slice_gemm_smem<kFP8, kS + 1>(bytes);
     return e;

@@ -1,17 +1,18 @@
 // The BF16 instantiations of the persistent slice product, slice counts 1..8
+// and tile widths 64 and 32
 // (one translation unit per format, so the build compiles them in parallel).
 #include "slice_gemm.cuh"
 
 namespace emu {
 
-cudaError_t launch_slice_gemm_bf16(int s, unsigned grid, size_t smem, cudaStream_t st, const CUtensorMap &tmA,
+cudaError_t launch_slice_gemm_bf16(int s, int bn, unsigned grid, size_t smem, cudaStream_t st, const CUtensorMap &tmA,
                                   const CUtensorMap &tmB, const EmuParams &prm) {
-    return dispatch_slice_gemm<false>(s, grid, smem, st, tmA, tmB, prm);
+    return dispatch_slice_gemm<false>(s, bn, grid, smem, st, tmA, tmB, prm);
 }
 
-cudaError_t launch_group_slice_gemm_bf16(int s, unsigned grid, size_t smem, cudaStream_t st, const EmuProblem *tab,
+cudaError_t launch_group_slice_gemm_bf16(int s, int bn, unsigned grid, size_t smem, cudaStream_t st, const EmuProblem *tab,
                                         const int64_t *begin, const GroupHeader *hdr) {
-    return dispatch_group_slice_gemm<false>(s, grid, smem, st, tab, begin, hdr);
+    return dispatch_group_slice_gemm<false>(s, bn, grid, smem, st, tab, begin, hdr);
 }
 
 cudaError_t slice_gemm_smem_attributes_bf16(int bytes) { return set_slice_gemm_smem<false>(bytes); }

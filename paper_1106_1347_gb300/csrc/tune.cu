@@ -6,19 +6,21 @@
 //     for cutoff == -1;
 //   - for the FP64-accurate emulated product, per (shape bucket, tier): the
 //     slice format (BF16 or FP8-E4M3, each with the slice count the tier
-//     needs) and the number of Strassen-Winograd levels over it, chosen by
-//     timing every candidate; consulted by mm_emulated_auto and by the
-//     serving loop's method 2.
+//     needs), the number of Strassen-Winograd levels over it and, for the
+//     direct product, the slice product's tile width (64 or 32 columns),
+//     chosen by timing every candidate; consulted by mm_emulated_auto and (for
+//     format and count) by the serving loop's method 2.
 // Both live in one in-library table, persisted as a small text file, one entry
 // per line:
 //   strassen <variant> <log2 max dim> <depth>
-//   emulated <log2 N> <log2 P> <log2 M> <tier decade> <format> <slices> <levels>
+//   emulated <log2 N> <log2 P> <log2 M> <tier decade> <format> <slices> <levels> <tile width>
+// (lines without the tile width, as earlier files wrote them, take the default).
 // MM_TUNE_CACHE names a file loaded at first use.  Without an entry the
 // choices fall back to models: the paper's depth floor(log2 X) - 4 for
 // Strassen; for the emulated product the format whose slice pairs cost less at
 // the nominal rates (an FP8 pair costs half a BF16 one, three quarters past 8
-// slices) and the measured
-// level crossovers of strassen_emulated_levels.
+// slices), the measured level crossovers of strassen_emulated_levels, and the
+// 32-column tile only where a 64-column one would be at most half used.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -31,11 +33,12 @@
 #include <utility>
 
 #include "common.cuh"
+#include "slice_gemm.cuh"
 
 namespace {
 
 struct EmuChoice {
-    int kind, slices, levels;
+    int kind, slices, levels, tile;  // tile: the slice product's tile width (0: the default)
     double ms;
 };
 using EmuKey = std::tuple<int, int, int, int>;  // log2 N, log2 P, log2 M, tier decade
@@ -69,18 +72,21 @@ int load_file(const char *path) {
     int n = 0;
     while (fgets(line, sizeof line, f)) {
         char kind[32];
-        int a[7];
+        int a[8];
         if (sscanf(line, "%31s", kind) != 1) continue;
         if (std::string(kind) == "strassen" && sscanf(line, "%*s %d %d %d", &a[0], &a[1], &a[2]) == 3) {
             if (a[0] < 0 || a[0] > 1 || a[2] < 0 || a[2] > 16) continue;
             g_depth[{a[0], a[1]}] = a[2];
             ++n;
-        } else if (std::string(kind) == "emulated" &&
-                   sscanf(line, "%*s %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6]) == 7) {
+        } else if (std::string(kind) == "emulated") {
+            const int got =
+                sscanf(line, "%*s %d %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6], &a[7]);
+            if (got < 7) continue;
+            if (got == 7) a[7] = 0;
             if ((a[4] != MM_SLICE_BF16 && a[4] != MM_SLICE_FP8E4M3) || a[5] < 1 || a[5] > (a[4] ? 10 : 8) ||
-                a[6] < 0 || a[6] > 4)
+                a[6] < 0 || a[6] > 4 || (a[7] != 0 && !emu::slice_bn_ok(a[5], a[7])))
                 continue;
-            g_emu[EmuKey{a[0], a[1], a[2], a[3]}] = EmuChoice{a[4], a[5], a[6], 0.0};
+            g_emu[EmuKey{a[0], a[1], a[2], a[3]}] = EmuChoice{a[4], a[5], a[6], a[7], 0.0};
             ++n;
         }
     }
@@ -107,7 +113,7 @@ int max_tuned_depth(int64_t N, int64_t P, int64_t M) {
 // slice pairs cost less, an FP8-E4M3 pair at half a BF16 pair up to 8 slices
 // (both issue N = 128 MMAs) and at three quarters past 8 (N = 64 MMAs on
 // 32-column accumulators, which issue at about 2/3 of the N = 128 rate).
-int model_emulated(int64_t N, int64_t P, int64_t M, double tier, int *kind, int *slices, int *levels) {
+int model_emulated(int64_t N, int64_t P, int64_t M, double tier, int *kind, int *slices, int *levels, int *tile) {
     const int sb = mm::emulated_slices(MM_SLICE_BF16, 0, tier);
     const int s8 = mm::emulated_slices(MM_SLICE_FP8E4M3, 0, tier);
     if (sb < 0 && s8 < 0) return sb;
@@ -120,6 +126,10 @@ int model_emulated(int64_t N, int64_t P, int64_t M, double tier, int *kind, int 
         *slices = s8;
     }
     *levels = mm::strassen_emulated_levels(-1, N, P, M);
+    // A 32-column tile issues its MMAs at about 2/3 of the 64-column rate, so
+    // it pays only where it saves more than a third of the padded columns.
+    const int64_t w64 = mm::ceil_div(M, (int64_t)64) * 64, w32 = mm::ceil_div(M, (int64_t)32) * 32;
+    *tile = (*levels == 0 && *slices <= 8 && 3 * w32 < 2 * w64) ? 32 : emu::slice_bn(*slices);
     return MM_OK;
 }
 
@@ -153,7 +163,7 @@ bool tuned_strassen_depth(int variant, int64_t N, int64_t P, int64_t M, int *dep
 // The emulated product's format, slice count and Strassen levels for a tier:
 // the tuned entry of the shape bucket, else the model.  Returns 1 (tuned),
 // 0 (model) or a negative status for an invalid tier.
-int emulated_choice(int64_t N, int64_t P, int64_t M, double tier, int *kind, int *slices, int *levels) {
+int emulated_choice(int64_t N, int64_t P, int64_t M, double tier, int *kind, int *slices, int *levels, int *tile) {
     if (!(tier > 0.0)) return MM_ERR_ARG;
     {
         std::lock_guard<std::mutex> g(g_mu);
@@ -163,10 +173,11 @@ int emulated_choice(int64_t N, int64_t P, int64_t M, double tier, int *kind, int
             *kind = it->second.kind;
             *slices = it->second.slices;
             *levels = it->second.levels;
+            *tile = it->second.tile ? it->second.tile : emu::slice_bn(it->second.slices);
             return 1;
         }
     }
-    const int rc = model_emulated(N, P, M, tier, kind, slices, levels);
+    const int rc = model_emulated(N, P, M, tier, kind, slices, levels, tile);
     return rc < 0 ? rc : 0;
 }
 
@@ -247,7 +258,7 @@ size_t mm_tune_emulated_workspace_bytes(int64_t N, int64_t P, int64_t M, double 
 
 int mm_tune_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, const double *B, int64_t ldb,
                      double *C, int64_t ldc, double tier, void *ws, size_t ws_bytes, void *stream, int32_t *best_kind,
-                     int32_t *best_slices, int32_t *best_levels, double *best_ms) {
+                     int32_t *best_slices, int32_t *best_levels, double *best_ms, int32_t *best_tile) {
     int rc = mm::check_gemm_args("mm_tune_emulated", N, P, M, A, lda, B, ldb, C, ldc);
     if (rc) return rc;
     if (N == 0 || P == 0 || M == 0) return mm::fail(MM_ERR_ARG, "mm_tune_emulated: empty product");
@@ -257,24 +268,28 @@ int mm_tune_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t l
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    EmuChoice best{-1, 0, 0, 0.0};
+    EmuChoice best{-1, 0, 0, 0, 0.0};
     for (int kind = MM_SLICE_BF16; kind <= MM_SLICE_FP8E4M3 && rc == MM_OK; ++kind) {
         const int s = mm::emulated_slices(kind, 0, tier);
         if (s < 0) continue;  // the tier needs more slices than this format holds
         for (int L = 0; L <= max_emulated_levels(N, P, M) && rc == MM_OK; ++L) {
             if (emulated_candidate_bytes(N, P, M, kind, s, L) > ws_bytes) continue;
-            float t = 0.f, tmin = 0.f;
-            for (int rep = 0; rep < 3 && rc == MM_OK; ++rep) {  // one warm-up, the faster of two timed runs
-                cudaEventRecord(e0, st);
-                rc = L == 0 ? mm::run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st)
-                            : mm::run_strassen_emulated(1, L, N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st);
-                cudaEventRecord(e1, st);
-                cudaError_t e = cudaEventSynchronize(e1);
-                if (e != cudaSuccess) rc = mm::cuda_fail(e, "mm_tune_emulated");
-                if (rc == MM_OK) cudaEventElapsedTime(&t, e0, e1);
-                if (rep == 1 || (rep == 2 && t < tmin)) tmin = t;
+            // The direct product tries both tile widths its slice count allows.
+            for (int tile : {emu::slice_bn(s), 32}) {
+                if (tile == 32 && (L > 0 || emu::slice_bn(s) == 32)) continue;
+                float t = 0.f, tmin = 0.f;
+                for (int rep = 0; rep < 3 && rc == MM_OK; ++rep) {  // one warm-up, the faster of two timed runs
+                    cudaEventRecord(e0, st);
+                    rc = L == 0 ? mm::run_emulated(N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st, tile)
+                                : mm::run_strassen_emulated(1, L, N, P, M, A, lda, B, ldb, C, ldc, s, kind, ws, st);
+                    cudaEventRecord(e1, st);
+                    cudaError_t e = cudaEventSynchronize(e1);
+                    if (e != cudaSuccess) rc = mm::cuda_fail(e, "mm_tune_emulated");
+                    if (rc == MM_OK) cudaEventElapsedTime(&t, e0, e1);
+                    if (rep == 1 || (rep == 2 && t < tmin)) tmin = t;
+                }
+                if (rc == MM_OK && (best.kind < 0 || tmin < best.ms)) best = EmuChoice{kind, s, L, tile, (double)tmin};
             }
-            if (rc == MM_OK && (best.kind < 0 || tmin < best.ms)) best = EmuChoice{kind, s, L, (double)tmin};
         }
     }
     cudaEventDestroy(e0);
@@ -290,18 +305,20 @@ int mm_tune_emulated(int64_t N, int64_t P, int64_t M, const double *A, int64_t l
     if (best_slices) *best_slices = best.slices;
     if (best_levels) *best_levels = best.levels;
     if (best_ms) *best_ms = best.ms;
+    if (best_tile) *best_tile = best.tile;
     return MM_OK;
 }
 
 int mm_tune_emulated_choice(int64_t N, int64_t P, int64_t M, double tier, int32_t *kind, int32_t *slices,
-                            int32_t *levels) {
+                            int32_t *levels, int32_t *tile) {
     if (N < 0 || P < 0 || M < 0) return mm::fail(MM_ERR_ARG, "mm_tune_emulated_choice: negative size");
-    int k = 0, s = 0, l = 0;
-    const int rc = mm::emulated_choice(N, P, M, tier, &k, &s, &l);
+    int k = 0, s = 0, l = 0, w = 0;
+    const int rc = mm::emulated_choice(N, P, M, tier, &k, &s, &l, &w);
     if (rc < 0) return mm::fail(rc, "mm_tune_emulated_choice: tier must be > 0 and within the formats' reach");
     if (kind) *kind = k;
     if (slices) *slices = s;
     if (levels) *levels = l;
+    if (tile) *tile = w;
     return rc;
 }
 
@@ -312,8 +329,9 @@ int mm_tune_save(const char *path) {
     if (!f) return mm::fail(MM_ERR_ARG, "mm_tune_save: cannot open %s", path);
     for (auto &kv : g_depth) fprintf(f, "strassen %d %d %d\n", kv.first.first, kv.first.second, kv.second);
     for (auto &kv : g_emu)
-        fprintf(f, "emulated %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
-                std::get<2>(kv.first), std::get<3>(kv.first), kv.second.kind, kv.second.slices, kv.second.levels);
+        fprintf(f, "emulated %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                std::get<2>(kv.first), std::get<3>(kv.first), kv.second.kind, kv.second.slices, kv.second.levels,
+                kv.second.tile);
     fclose(f);
     return MM_OK;
 }

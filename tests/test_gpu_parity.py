@@ -297,6 +297,28 @@ def test_emulated_bit_exact_vs_oracle(mm, orc, shape, s):
     assert np.array_equal(got, orc.split_product(a, b, 7, s))
 
 
+@pytest.mark.parametrize("kind,beta", [(0, 7), (1, 5)])
+@pytest.mark.parametrize("s", [1, 3, 6, 8])
+@pytest.mark.parametrize("shape", [(130, 200, 24), (257, 300, 97), (64, 65, 1)])
+def test_emulated_narrow_tile_bit_exact(mm, orc, kind, beta, s, shape):
+    """The 32-column tile gives the 64-column tile's result bit for bit (both
+    are the oracle's definition), ragged widths included."""
+    a, b = pair(*shape, "log", 90 + s)
+    narrow = host(mm.emulated_tiled(dev(a), dev(b), 32, nslices=s, kind=kind))
+    assert np.array_equal(narrow, orc.split_product(a, b, beta, s))
+    assert np.array_equal(narrow, host(mm.emulated_tiled(dev(a), dev(b), 64, nslices=s, kind=kind)))
+
+
+def test_emulated_tile_width_rejected(mm):
+    import paper_1106_1347_gb300 as pkg
+
+    a, b = pair(40, 30, 20, "uni", 95)
+    with pytest.raises(pkg.MMError):
+        mm.emulated_tiled(dev(a), dev(b), 48, nslices=8)
+    with pytest.raises(pkg.MMError):  # 10 FP8 slices only fit 32-column tiles
+        mm.emulated_tiled(dev(a), dev(b), 64, nslices=10, kind=1)
+
+
 @pytest.mark.parametrize("s", [1, 2, 4, 5, 6, 7])
 def test_emulated_other_slice_counts(mm, orc, s):
     a, b = pair(130, 200, 70, "uni", 13)

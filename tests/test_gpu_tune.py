@@ -33,23 +33,25 @@ def dev(x):
 
 
 @pytest.mark.parametrize("shape,tier", [((640, 700, 600), 1e-6), ((2048, 2048, 2048), 1e-14),
-                                        ((1100, 3000, 1030), 1e-9)])
+                                        ((1100, 3000, 1030), 1e-9), ((3000, 2000, 24), 1e-14)])
 def test_tune_emulated_then_auto(mm, orc, tmp_path, shape, tier):
     mm.tune_clear()
     a = S.loguniform(shape[0], shape[1], S.stream_seed(3, 60))
     b = S.loguniform(shape[1], shape[2], S.stream_seed(3, 61))
     ta, tb = dev(a), dev(b)
-    (k0, s0, l0), tuned = mm.emulated_choice(*shape, tier)
+    (k0, s0, l0, w0), tuned = mm.emulated_choice(*shape, tier)
     assert not tuned  # the model's choice before tuning
-    kind, s, levels, ms = mm.tune_emulated(ta, tb, tier=tier)
-    assert ms > 0 and kind in (0, 1) and 1 <= s <= 8 and 0 <= levels <= 2
+    kind, s, levels, ms, tile = mm.tune_emulated(ta, tb, tier=tier)
+    assert ms > 0 and kind in (0, 1) and 1 <= s <= 8 and 0 <= levels <= 2 and tile in (32, 64)
+    assert levels == 0 or tile == 64
     assert s == mm.emulated_slices(0, tier, kind)
-    (k1, s1, l1), tuned = mm.emulated_choice(*shape, tier)
-    assert tuned and (k1, s1, l1) == (kind, s, levels)
+    (k1, s1, l1, w1), tuned = mm.emulated_choice(*shape, tier)
+    assert tuned and (k1, s1, l1, w1) == (kind, s, levels, tile)
     c, used = mm.emulated_auto(ta, tb, tier=tier, return_choice=True)
-    assert used == (kind, s, levels)
+    assert used == (kind, s, levels, tile)
     if levels == 0:
-        ref = mm.emulated(ta, tb, nslices=s, kind=kind)
+        ref = mm.emulated_tiled(ta, tb, tile, nslices=s, kind=kind)
+        assert np.array_equal(ref.cpu().numpy(), mm.emulated(ta, tb, nslices=s, kind=kind).cpu().numpy())
     else:
         ref = mm.strassen_emulated(ta, tb, variant=1, levels=levels, nslices=s, kind=kind)
     assert np.array_equal(c.cpu().numpy(), ref.cpu().numpy())
@@ -64,5 +66,5 @@ def test_tune_emulated_then_auto(mm, orc, tmp_path, shape, tier):
     mm.tune_clear()
     assert not mm.emulated_choice(*shape, tier)[1]
     assert mm.tune_load(path) == 1
-    assert mm.emulated_choice(*shape, tier) == ((kind, s, levels), True)
+    assert mm.emulated_choice(*shape, tier) == ((kind, s, levels, tile), True)
     mm.tune_clear()

@@ -19,10 +19,10 @@ def lib():
     L.mm_tune_clear()
 
 
-def choice(L, n, p, m, tier):
-    k, s, lv = ctypes.c_int32(-1), ctypes.c_int32(-1), ctypes.c_int32(-1)
-    rc = L.mm_tune_emulated_choice(n, p, m, tier, ctypes.byref(k), ctypes.byref(s), ctypes.byref(lv))
-    return rc, (k.value, s.value, lv.value)
+def choice(L, n, p, m, tier, with_tile=False):
+    k, s, lv, tl = ctypes.c_int32(-1), ctypes.c_int32(-1), ctypes.c_int32(-1), ctypes.c_int32(-1)
+    rc = L.mm_tune_emulated_choice(n, p, m, tier, ctypes.byref(k), ctypes.byref(s), ctypes.byref(lv), ctypes.byref(tl))
+    return (rc, (k.value, s.value, lv.value, tl.value)) if with_tile else (rc, (k.value, s.value, lv.value))
 
 
 def test_model_choices_without_entries(lib):
@@ -39,18 +39,31 @@ def test_model_choices_without_entries(lib):
     assert choice(lib, 100, 100, 100, -1.0)[0] < 0
 
 
+def test_model_tile_width(lib):
+    # 64-column tiles unless M is narrow enough that 32-column ones (at about 2/3
+    # of the MMA rate) pad less by more than a third: M <= 32
+    assert choice(lib, 4096, 4096, 32, 1e-14, True) == (0, (0, 8, 0, 32))
+    assert choice(lib, 4096, 4096, 20, 1e-6, True)[1][3] == 32
+    assert choice(lib, 4096, 4096, 33, 1e-14, True)[1][3] == 64
+    assert choice(lib, 4096, 4096, 4096, 1e-14, True)[1][3] == 64
+    # past 8 FP8 slices the tile is 32 columns whatever M is
+    rc, (k, s, lv, tl) = choice(lib, 4096, 4096, 4096, 1e-12, True)
+    assert (k == 1 and s > 8 and tl == 32) or (s <= 8 and tl == 64)
+
+
 def test_recorded_choices_round_trip(lib, tmp_path):
     f = tmp_path / "tune.txt"
     f.write_text("strassen 0 12 5\n"
-                 "emulated 12 12 12 6 0 5 1\n"
-                 "emulated 9 9 9 14 0 8 0\n"
+                 "emulated 12 12 12 6 0 5 1\n"     # no tile width (older files): the default
+                 "emulated 9 9 9 14 0 8 0 32\n"
                  "emulated 1 2 3\n"            # short line: skipped
                  "strassen 5 3 3\n"            # no such variant: skipped
                  "emulated 9 9 9 9 7 8 0\n"    # no such format: skipped
+                 "emulated 9 9 9 3 0 8 0 48\n"  # no such tile width: skipped
                  "comment line\n")
     assert lib.mm_tune_load(str(f).encode()) == 3
-    assert choice(lib, 4096, 4096, 4096, 1e-6) == (1, (0, 5, 1))
-    assert choice(lib, 600, 700, 1000, 1e-14) == (1, (0, 8, 0))  # bucket (9, 9, 9), tier decade 14
+    assert choice(lib, 4096, 4096, 4096, 1e-6, True) == (1, (0, 5, 1, 64))
+    assert choice(lib, 600, 700, 1000, 1e-14, True) == (1, (0, 8, 0, 32))  # bucket (9, 9, 9), tier decade 14
     assert choice(lib, 4096, 4096, 4096, 1e-14)[0] == 0          # other tier decade: the model
     # the loaded Strassen depth drives cutoff = -1: depth 5 at 4096 is cutoff 128's plan
     assert lib.mm_strassen_workspace_bytes(4096, 4096, 4096, -1) == lib.mm_strassen_workspace_bytes(4096, 4096, 4096,
@@ -58,7 +71,7 @@ def test_recorded_choices_round_trip(lib, tmp_path):
     g = tmp_path / "saved.txt"
     assert lib.mm_tune_save(str(g).encode()) == 0
     lines = sorted(g.read_text().splitlines())
-    assert lines == sorted(["strassen 0 12 5", "emulated 12 12 12 6 0 5 1", "emulated 9 9 9 14 0 8 0"])
+    assert lines == sorted(["strassen 0 12 5", "emulated 12 12 12 6 0 5 1 0", "emulated 9 9 9 14 0 8 0 32"])
     lib.mm_tune_clear()
     assert choice(lib, 4096, 4096, 4096, 1e-6)[0] == 0
     assert lib.mm_tune_load(str(g).encode()) == 3
