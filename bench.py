@@ -880,6 +880,13 @@ def run_ours(args):
     from paper_1106_1347_gb300 import build as mmbuild
 
     rank, world, local = dist_env()
+    serving = None
+    if world == 1 and not args.quick and not args.no_serve:
+        # The serving benchmark runs first, in a process of its own, before this
+        # one opens a CUDA context: another process holding an idle context (20 GB
+        # on the device, 2 GB pinned) doubled the serving loop's p99 (0.7x: 6.1 ->
+        # 12.1 ms; 0.3x: 2.2 -> 4.5 ms), and this process holds far more later.
+        serving = serve_in_own_process(local, args)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
@@ -1037,9 +1044,8 @@ def run_ours(args):
         out["plain_fp64"]["fp64_pipe_frac"] = out["plain_fp64"]["value"] / pk64 if pk64 else None
         out["plain_fp64"]["fp64_pipe_frac_against"] = "mma.sync f64 probe"
 
-        # Serving first, in its own process, before the long sections below.
-        if not args.no_serve:
-            out["serving"] = serve_in_own_process(local, args)
+        if serving is not None:
+            out["serving"] = serving
         if args.variants_n > 0:
             out["fp64_methods"] = variants_bench(dev, out["fp64_peak"])
             out["paper_table"] = paper_table(dev)
