@@ -163,8 +163,7 @@ class ClockSampler:
             return self
         # nvidia-smi's start-up (driver and device enumeration) comes before its
         # first sample; the timed region starts only once that sample is in, so
-        # the start-up does not overlap it (end-to-end steps that met it took
-        # 35-76 ms instead of 24).
+        # the start-up does not overlap it.
         self._reader = threading.Thread(target=self._read, daemon=True)
         self._reader.start()
         deadline = time.time() + 10.0
