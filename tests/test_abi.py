@@ -71,6 +71,11 @@ def test_host_side_queries_and_checks(native):
     assert lib.mm_naive(0, 5, 5, None, 5, fake, 5, None, 5, None) == 0
     assert lib.mm_emulated(3, 3, 3, fake, 3, ctypes.c_void_p(0x30000), 3, ctypes.c_void_p(0x50000), 3, 1, 0, 1e-14,
                            None, 0, None) == -4  # 1e-14 needs 12 FP8-E4M3 slices, more than 8
+    # the slice product's tile width: 64 (up to 8 slices) or 32, anything else is refused before any device work
+    w = ctypes.c_void_p(0x30000), ctypes.c_void_p(0x50000)
+    assert lib.mm_emulated_tiled(3, 3, 3, fake, 3, w[0], 3, w[1], 3, 0, 8, 1e-14, 48, None, 0, None) == -1
+    assert lib.mm_emulated_tiled(3, 3, 3, fake, 3, w[0], 3, w[1], 3, 1, 10, 1e-14, 64, None, 0, None) == -1
+    assert lib.mm_emulated_tiled(0, 3, 3, fake, 3, w[0], 3, w[1], 3, 0, 8, 1e-14, 32, None, 0, None) == 0
     assert lib.mm_emulated_slices(1, 0, 1e-6) == 6  # beta = 5: ceil((log2(1e6) + 9) / 5)
     assert lib.mm_emulated_slices(0, 0, 1e-6) == 5  # beta = 7
     assert lib.mm_emulated_slices(2, 0, 1e-6) < 0  # unknown format
