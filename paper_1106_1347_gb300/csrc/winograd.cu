@@ -29,6 +29,19 @@ namespace {
 
 constexpr int kRows = 32;
 
+// x * 2^k with ldexp's result.  When x is normal and the scaled exponent stays
+// in the normal range, the product is exact and is x's bit pattern with k added
+// to the exponent field (integer work only, no FP64 pipe); zeros, subnormals,
+// and results that would leave the normal range go to ldexp.
+__device__ __forceinline__ double pow2_scale(double x, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E != 0 && E != 0x7FF && E + k >= 1 && E + k <= 0x7FE)
+        return __longlong_as_double((long long)(b + ((unsigned long long)(long long)k << 52)));
+    return ldexp(x, k);
+}
+
+
 template <bool kNorm>
 __global__ void __launch_bounds__(32) a_terms_kernel(int64_t N, int64_t P, const double *__restrict__ A, int64_t lda,
                                                      double *__restrict__ y, unsigned long long *norm_bits) {
@@ -125,7 +138,7 @@ __global__ void __launch_bounds__(32) a_terms_rowcol_kernel(int64_t N, int64_t P
         __syncwarp();
         const int npair = (int)min((int64_t)kRows, gamma2 - c0) / 2;
         for (int j = 0; j < npair; ++j)
-            ys = __dadd_rn(ys, __dmul_rn(ldexp(tile[lane][2 * j], -e), ldexp(tile[lane][2 * j + 1], -e)));
+            ys = __dadd_rn(ys, __dmul_rn(pow2_scale(tile[lane][2 * j], -e), pow2_scale(tile[lane][2 * j + 1], -e)));
         __syncwarp();
     }
     if (lane < nrows) {
@@ -149,7 +162,7 @@ __global__ void __launch_bounds__(128) b_terms_rowcol_kernel(int64_t P, int64_t 
     const int64_t gamma = P / 2;
     double s = 0.0;
     for (int64_t j = 0; j < gamma; ++j)
-        s = __dadd_rn(s, __dmul_rn(ldexp(B[(2 * j) * ldb + k], -f), ldexp(B[(2 * j + 1) * ldb + k], -f)));
+        s = __dadd_rn(s, __dmul_rn(pow2_scale(B[(2 * j) * ldb + k], -f), pow2_scale(B[(2 * j + 1) * ldb + k], -f)));
     z[k] = s;
     fb[k] = f;
 }
@@ -232,8 +245,8 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
                 bv *= sb;
             }
             if (kRowCol) {
-                av = ldexp(av, -erow[q]);
-                bv = ldexp(bv, -fcol);
+                av = pow2_scale(av, -erow[q]);
+                bv = pow2_scale(bv, -fcol);
             }
             ra[q] = av;
             rb[q] = bv;
@@ -282,7 +295,7 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
         double alast = 0.0;
         const int ei = kRowCol ? ea[i] : 0;
         if (kScaled) yi = (yi * sa) * sa;
-        if (odd) alast = kRowCol ? ldexp(A[i * lda + (P - 1)], -ei) : A[i * lda + (P - 1)] * sa;
+        if (odd) alast = kRowCol ? pow2_scale(A[i * lda + (P - 1)], -ei) : A[i * lda + (P - 1)] * sa;
 #pragma unroll
         for (int c = 0; c < R; ++c) {
             const int64_t k = j0 + tx + 16 * c;
@@ -292,8 +305,8 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
             double v = __dsub_rn(__dsub_rn(acc[r][c], yi), zk);
             if (kRowCol) {
                 const int fk = fb[k];
-                if (odd) v = __dadd_rn(v, __dmul_rn(alast, ldexp(B[(P - 1) * ldb + k], -fk)));
-                v = ldexp(v, ei + fk);
+                if (odd) v = __dadd_rn(v, __dmul_rn(alast, pow2_scale(B[(P - 1) * ldb + k], -fk)));
+                v = pow2_scale(v, ei + fk);
             } else if (odd) {
                 v = __dadd_rn(v, __dmul_rn(alast, B[(P - 1) * ldb + k] * sb));
             }

@@ -193,6 +193,27 @@ def test_winograd_rowcol_badly_scaled(mm, orc, n):
     assert (np.abs(got - ref) <= 2 * bound).all()
 
 
+@pytest.mark.parametrize("sa,sb", [(-1045, 1023), (1000, -1030), (-1000, 990)])
+def test_winograd_rowcol_extreme_exponents(mm, orc, sa, sb):
+    """Rows of A or columns of B at the ends of the double range (subnormal
+    entries, scalings past the normal exponents): every element within the
+    elementwise bound of the exact product, as for the badly scaled inputs."""
+    n = 96
+    a = S.uniform(n, n, S.stream_seed(2, 40))
+    b = S.uniform(n, n, S.stream_seed(2, 41))
+    a[: n // 2] = np.ldexp(a[: n // 2], sa)
+    b[:, : n // 2] = np.ldexp(b[:, : n // 2], sb)
+    truth = orc.dot2_product(a, b)
+    ref, e, f = orc.winograd_rowcol_scaled(a, b)
+    got = host(mm.winograd_rowcol_scaled(dev(a), dev(b)))
+    keep = np.isfinite(truth) & (np.abs(truth) > 2.0 ** -900)  # products inside the normal range
+    assert keep[: n // 2, : n // 2].all()
+    gamma = n // 2
+    bound = 8 * gamma * (gamma + 5) * 2.0 ** -53 * np.ldexp(1.0, e[:, None] + f[None, :])
+    assert (np.abs(got - truth) <= bound)[keep].all()
+    assert (np.abs(got - ref) <= 2 * bound)[keep].all()
+
+
 def test_winograd_rowcol_power_of_two_invariance(mm):
     """Prescaling rows of A and columns of B by powers of two leaves the scaled
     operands unchanged, so the GPU result scales by exactly 2^(r_i + c_k)."""
