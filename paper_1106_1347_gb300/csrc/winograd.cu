@@ -41,7 +41,6 @@ __device__ __forceinline__ double pow2_scale(double x, int k) {
     return ldexp(x, k);
 }
 
-
 template <bool kNorm>
 __global__ void __launch_bounds__(32) a_terms_kernel(int64_t N, int64_t P, const double *__restrict__ A, int64_t lda,
                                                      double *__restrict__ y, unsigned long long *norm_bits) {
@@ -198,26 +197,22 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
     __shared__ double As[T][TK + 1];
     __shared__ double Bs[TK][T];
     __shared__ double s_scale[2];
-    __shared__ int s_lam;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t i0 = (int64_t)blockIdx.y * T, j0 = (int64_t)blockIdx.x * T;
     const int64_t K2 = (P / 2) * 2;
     if (tid == 0) {
         double sa = 1.0, sb = 1.0;
-        int lam = 0;
         if (kScaled) {
-            lam = brent_lambda(norms[0], norms[1]);
+            const int lam = brent_lambda(norms[0], norms[1]);
             sa = ldexp(1.0, lam);
             sb = ldexp(1.0, -lam);
             if (lambda_out && blockIdx.x == 0 && blockIdx.y == 0) *lambda_out = lam;
         }
         s_scale[0] = sa;
         s_scale[1] = sb;
-        s_lam = lam;
     }
     __syncthreads();
     const double sa = s_scale[0], sb = s_scale[1];
-    const int lam = s_lam;
     double acc[R][R];
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -244,11 +239,11 @@ __global__ void __launch_bounds__(256) winograd_kernel(int64_t N, int64_t P, int
             double av = (gi < N && gk < K2) ? A[gi * lda + gk] : 0.0;
             const int64_t bk = k0 + e / T, bj = j0 + e % T;
             double bv = (bk < K2 && bj < M) ? B[bk * ldb + bj] : 0.0;
-            if (kScaled) {  // MultiplyWithScalar by 2^lambda and 2^-lambda
-                av = pow2_scale(av, lam);
-                bv = pow2_scale(bv, -lam);
+            if (kScaled) {
+                av *= sa;
+                bv *= sb;
             }
-            if (kRowCol) {
+            if (kRowCol) {  // exponent-field scaling: measured faster here than ldexp or a multiplication
                 av = pow2_scale(av, -erow[q]);
                 bv = pow2_scale(bv, -fcol);
             }
