@@ -430,8 +430,8 @@ def grouped_vs_single(dev, count=256):
 def autotuner(dev):
     """The library's autotuner on a few shape buckets: the Strassen depth at
     4096^3 for both variants, and the emulated product's format x Strassen-
-    Winograd levels for several tiers, against the models' choices (the tuned
-    table lives in this process only)."""
+    Winograd levels x tile width for several tiers and shapes (one narrow),
+    against the models' choices (the tuned table lives in this process only)."""
     import torch
 
     import paper_1106_1347_gb300 as mm
@@ -445,14 +445,15 @@ def autotuner(dev):
         depth, ms = mm.tune_strassen(a, b, variant=variant)
         out["strassen"][name] = {"n": 4096, "depth": depth, "ms": ms, "tflops": 2.0 * 4096 ** 3 / (ms * 1e-3) / 1e12}
     del a, b
-    for n, tier in ((1024, 1e-14), (1024, 1e-6), (4096, 1e-9), (4096, 1e-12), (8192, 1e-14)):
-        a = torch.from_numpy(S.loguniform(n, n, S.stream_seed(3, 0))).to(dev)
-        b = torch.from_numpy(S.loguniform(n, n, S.stream_seed(3, 1))).to(dev)
-        model, _ = mm.emulated_choice(n, n, n, tier)
+    for (n, p, m), tier in (((1024, 1024, 1024), 1e-14), ((1024, 1024, 1024), 1e-6), ((4096, 4096, 4096), 1e-9),
+                            ((4096, 4096, 4096), 1e-12), ((8192, 8192, 8192), 1e-14), ((8192, 8192, 32), 1e-14)):
+        a = torch.from_numpy(S.loguniform(n, p, S.stream_seed(3, 0))).to(dev)
+        b = torch.from_numpy(S.loguniform(p, m, S.stream_seed(3, 1))).to(dev)
+        model, _ = mm.emulated_choice(n, p, m, tier)
         kind, slices, levels, ms, tile = mm.tune_emulated(a, b, tier=tier)
-        out["emulated"].append({"n": n, "tier": tier,
+        out["emulated"].append({"n": n, "p": p, "m": m, "tier": tier,
                                 "tuned": {"format": kind, "slices": slices, "levels": levels, "tile": tile},
-                                "ms": ms, "tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+                                "ms": ms, "tflops": 2.0 * n * p * m / (ms * 1e-3) / 1e12,
                                 "model": {"format": model[0], "slices": model[1], "levels": model[2],
                                           "tile": model[3]}})
         del a, b
