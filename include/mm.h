@@ -263,10 +263,12 @@ int mm_emulated_tiled(int64_t N, int64_t P, int64_t M, const double *A, int64_t 
  * and the split.  C is computed in blocks: up to 8 row blocks, and for
  * N >= 4096 and M >= 2048 two column blocks, with row blocks of whole waves of
  * tiles.  One internal copy
- * stream carries the first row block of A, the column blocks of B, then the
- * other row blocks of A; each block is split as soon as it lands, each block
- * product follows the splits it needs, and its block of C is copied back on a
- * second internal stream while later blocks run.  Asynchronous on `stream`
+ * stream carries the first row block of A, B in pieces (with two column
+ * blocks: the first one in two halves, then the second), then the other row
+ * blocks of A; each block is split as soon as it lands, the first row block is
+ * multiplied by each piece of B as it lands, each later block product follows
+ * the splits it needs, and its block of C is copied back on a second internal
+ * stream while later blocks run.  Asynchronous on `stream`
  * (which waits for the last copy back); the
  * host buffers must stay valid and C unread until the stream completes.  With
  * P == 0 the call synchronises `stream` and writes C = 0 on the host.  Results are

@@ -637,11 +637,12 @@ int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t 
     const EmuWork w = emu_work(N, P, M, s, kind, w8);
     // C in blocks: up to 8 row blocks of whole tiles, and for large products
     // (N >= 4096, M >= 2048) two column blocks, with row blocks sized so each
-    // block product fills whole waves (four column blocks measured slower: 16
-    // launches of 4 waves each).  The first product then waits for one block of
-    // A and half of B instead of all of B, and the last block's copy back
-    // trails the products.
-    constexpr int kMaxColBlocks = 2;
+    // block product fills whole waves (four column blocks throughout measured
+    // slower: 16 launches of 4 waves each).  B goes up in pieces -- the first
+    // column block in two halves, then the second block -- and the first row
+    // block is multiplied by each piece as it lands, so the first product waits
+    // for one block of A and a quarter of B; the last block's copy back trails
+    // the products.
     const int64_t cb = N >= 4096 && M >= 2048 ? 2 : 1;
     const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(8 / cb, ceil_div(N, 512 * cb)));
     int64_t R = ceil_div(ceil_div(N, nb), BM) * BM;
@@ -659,11 +660,11 @@ int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t 
             if (waste < best - 1e-9) best = waste, R = tr * BM;
         }
     }
-    int64_t c0s[kMaxColBlocks], ms[kMaxColBlocks];
-    for (int j = 0; j < kMaxColBlocks; ++j) {
-        c0s[j] = std::min<int64_t>(j * Mh, M);
-        ms[j] = std::min<int64_t>(Mh, M - c0s[j]);
-    }
+    // Column blocks (every row block but the first) and pieces of B (the first
+    // row block): [c0, c0 + width).
+    const int64_t Q = cb > 1 ? ceil_div(ceil_div(Mh, 2), (int64_t)BN) * BN : M;
+    const int64_t blk_c0[2] = {0, Mh}, blk_m[2] = {std::min(Mh, M), cb > 1 ? M - Mh : 0};
+    const int64_t pc_c0[3] = {0, Q, Mh}, pc_m[3] = {Q, cb > 1 ? Mh - Q : 0, cb > 1 ? M - Mh : 0};
     std::vector<cudaEvent_t> ev;
     auto event = [&](cudaEvent_t *e) {
         cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
@@ -675,21 +676,33 @@ int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t 
         return r;
     };
     // All uploads go through one copy stream in the order they are needed: the
-    // first block of A, the column blocks of B, then the other blocks of A, so
-    // the link is not shared with blocks that cannot start yet.
-    cudaEvent_t e0, eB[kMaxColBlocks] = {}, eA, eC, eEnd;
+    // first block of A, the pieces of B, then the other blocks of A, so the
+    // link is not shared with blocks that cannot start yet.
+    cudaEvent_t e0, eB[3] = {}, eA, eC, eEnd;
     cudaError_t e = event(&e0);
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.up, e0, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.down, e0, 0);
     if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
     auto upload_b = [&](int j) {
-        if (ms[j] <= 0) return cudaSuccess;
-        cudaError_t r = cudaMemcpy2DAsync(dB + c0s[j], (size_t)M * 8, B + c0s[j], (size_t)ldb * 8, (size_t)ms[j] * 8,
-                                          P, cudaMemcpyHostToDevice, cs.up);
+        if (pc_m[j] <= 0) return cudaSuccess;
+        cudaError_t r = cudaMemcpy2DAsync(dB + pc_c0[j], (size_t)M * 8, B + pc_c0[j], (size_t)ldb * 8,
+                                          (size_t)pc_m[j] * 8, P, cudaMemcpyHostToDevice, cs.up);
         if (r == cudaSuccess) r = event(&eB[j]);
         if (r == cudaSuccess) r = cudaEventRecord(eB[j], cs.up);
         return r;
+    };
+    // The block product of rows [r0, r0 + n) and columns [c0, c0 + m), and its copy back.
+    auto product = [&](int64_t r0, int64_t n, int64_t c0, int64_t m) {
+        int r = slice_product(w, r0, n, c0, m, P, dC + r0 * M + c0, M, s, kind, st, slice_bn(s));
+        if (r) return r;
+        cudaError_t x = event(&eC);
+        if (x == cudaSuccess) x = cudaEventRecord(eC, st);
+        if (x == cudaSuccess) x = cudaStreamWaitEvent(cs.down, eC, 0);
+        if (x == cudaSuccess)
+            x = cudaMemcpy2DAsync(C + r0 * ldc + c0, (size_t)ldc * 8, dC + r0 * M + c0, (size_t)M * 8,
+                                  (size_t)m * 8, n, cudaMemcpyDeviceToHost, cs.down);
+        return x == cudaSuccess ? MM_OK : cuda_fail(x, "mm_emulated_host");
     };
     for (int64_t r0 = 0; r0 < N; r0 += R) {
         const int64_t n = std::min(R, N - r0);
@@ -698,29 +711,26 @@ int run_emulated_host(int64_t N, int64_t P, int64_t M, const double *A, int64_t 
         if (e == cudaSuccess) e = event(&eA);
         if (e == cudaSuccess) e = cudaEventRecord(eA, cs.up);
         if (r0 == 0)
-            for (int j = 0; j < kMaxColBlocks && e == cudaSuccess; ++j) e = upload_b(j);
+            for (int j = 0; j < 3 && e == cudaSuccess; ++j) e = upload_b(j);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, eA, 0);
         if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
         rc = split_a_rows(w, r0, n, P, dA + r0 * P, P, s, kind, st);
         if (rc) return done(rc);
-        for (int j = 0; j < kMaxColBlocks; ++j) {
-            const int64_t c0 = c0s[j], m = ms[j];
-            if (m <= 0) continue;
-            if (r0 == 0) {  // this column block of B is split as soon as it lands
+        if (r0 == 0) {  // each piece of B is split as soon as it lands, then multiplied
+            for (int j = 0; j < 3; ++j) {
+                if (pc_m[j] <= 0) continue;
                 e = cudaStreamWaitEvent(st, eB[j], 0);
                 if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
-                rc = split_b(w, c0, P, m, dB + c0, M, s, kind, st);
+                rc = split_b(w, pc_c0[j], P, pc_m[j], dB + pc_c0[j], M, s, kind, st);
+                if (!rc) rc = product(r0, n, pc_c0[j], pc_m[j]);
                 if (rc) return done(rc);
             }
-            rc = slice_product(w, r0, n, c0, m, P, dC + r0 * M + c0, M, s, kind, st, slice_bn(s));
+            continue;
+        }
+        for (int j = 0; j < 2; ++j) {
+            if (blk_m[j] <= 0) continue;
+            rc = product(r0, n, blk_c0[j], blk_m[j]);
             if (rc) return done(rc);
-            e = event(&eC);
-            if (e == cudaSuccess) e = cudaEventRecord(eC, st);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.down, eC, 0);
-            if (e == cudaSuccess)
-                e = cudaMemcpy2DAsync(C + r0 * ldc + c0, (size_t)ldc * 8, dC + r0 * M + c0, (size_t)M * 8,
-                                      (size_t)m * 8, n, cudaMemcpyDeviceToHost, cs.down);
-            if (e != cudaSuccess) return done(cuda_fail(e, "mm_emulated_host"));
         }
     }
     e = event(&eEnd);
