@@ -160,8 +160,8 @@ bool tuned_strassen_depth(int variant, int64_t N, int64_t P, int64_t M, int *dep
     return true;
 }
 
-// The emulated product's format, slice count and Strassen levels for a tier:
-// the tuned entry of the shape bucket, else the model.  Returns 1 (tuned),
+// The emulated product's format, slice count, Strassen levels and tile width
+// for a tier: the tuned entry of the shape bucket, else the model.  Returns 1 (tuned),
 // 0 (model) or a negative status for an invalid tier.
 int emulated_choice(int64_t N, int64_t P, int64_t M, double tier, int *kind, int *slices, int *levels, int *tile) {
     if (!(tier > 0.0)) return MM_ERR_ARG;
