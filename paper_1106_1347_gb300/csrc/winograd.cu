@@ -41,12 +41,13 @@ __device__ __forceinline__ double pow2_scale(double x, int k) {
     return ldexp(x, k);
 }
 
+// Row group `blk` (rows 32 blk .. 32 blk + 31) of the y pass, one warp.
 template <bool kNorm>
-__global__ void __launch_bounds__(32) a_terms_kernel(int64_t N, int64_t P, const double *__restrict__ A, int64_t lda,
-                                                     double *__restrict__ y, unsigned long long *norm_bits) {
+__device__ __forceinline__ void a_terms_rows(int64_t blk, int64_t N, int64_t P, const double *__restrict__ A,
+                                             int64_t lda, double *__restrict__ y, unsigned long long *norm_bits) {
     __shared__ double tile[kRows][kRows + 1];
     const int lane = threadIdx.x;
-    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    const int64_t row0 = blk * kRows;
     const int64_t nrows = min((int64_t)kRows, N - row0);
     const int64_t gamma2 = (P / 2) * 2;  // columns that form pairs
     double next[kRows];
@@ -76,9 +77,9 @@ __global__ void __launch_bounds__(32) a_terms_kernel(int64_t N, int64_t P, const
     }
 }
 
-__global__ void __launch_bounds__(128) b_terms_kernel(int64_t P, int64_t M, const double *__restrict__ B, int64_t ldb,
-                                                      double *__restrict__ z) {
-    const int64_t k = (int64_t)blockIdx.x * 128 + threadIdx.x;
+// Column k of the z pass, one thread.
+__device__ __forceinline__ void b_terms_col(int64_t k, int64_t P, int64_t M, const double *__restrict__ B, int64_t ldb,
+                                            double *__restrict__ z) {
     if (k >= M) return;
     const int64_t gamma = P / 2;
     double s = 0.0;
@@ -102,13 +103,13 @@ __device__ __forceinline__ int exponent_of(unsigned long long bits) {
     return e;
 }
 
-// Row pass of the per-row/column scaled form: e_i, then y'_i over 2^-e_i A_i,:.
-__global__ void __launch_bounds__(32) a_terms_rowcol_kernel(int64_t N, int64_t P, const double *__restrict__ A,
-                                                            int64_t lda, double *__restrict__ y,
-                                                            int32_t *__restrict__ ea) {
+// Row pass of the per-row/column scaled form for row group `blk`: e_i, then
+// y'_i over 2^-e_i A_i,:.
+__device__ __forceinline__ void a_terms_rowcol_rows(int64_t blk, int64_t N, int64_t P, const double *__restrict__ A,
+                                                    int64_t lda, double *__restrict__ y, int32_t *__restrict__ ea) {
     __shared__ double tile[kRows][kRows + 1];
     const int lane = threadIdx.x;
-    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    const int64_t row0 = blk * kRows;
     const int64_t nrows = min((int64_t)kRows, N - row0);
     const int64_t gamma2 = (P / 2) * 2;
     // Pass 1: the row maximum of |A_ij| on the bit patterns (lane r owns row r).
@@ -146,11 +147,10 @@ __global__ void __launch_bounds__(32) a_terms_rowcol_kernel(int64_t N, int64_t P
     }
 }
 
-// Column pass of the per-row/column scaled form: f_k, then z'_k over 2^-f_k B_:,k.
-__global__ void __launch_bounds__(128) b_terms_rowcol_kernel(int64_t P, int64_t M, const double *__restrict__ B,
-                                                             int64_t ldb, double *__restrict__ z,
-                                                             int32_t *__restrict__ fb) {
-    const int64_t k = (int64_t)blockIdx.x * 128 + threadIdx.x;
+// Column pass of the per-row/column scaled form for column k: f_k, then z'_k
+// over 2^-f_k B_:,k.
+__device__ __forceinline__ void b_terms_rowcol_col(int64_t k, int64_t P, int64_t M, const double *__restrict__ B,
+                                                   int64_t ldb, double *__restrict__ z, int32_t *__restrict__ fb) {
     if (k >= M) return;
     unsigned long long mx = 0;
     for (int64_t j = 0; j < P; ++j) {
@@ -164,6 +164,30 @@ __global__ void __launch_bounds__(128) b_terms_rowcol_kernel(int64_t P, int64_t 
         s = __dadd_rn(s, __dmul_rn(pow2_scale(B[(2 * j) * ldb + k], -f), pow2_scale(B[(2 * j + 1) * ldb + k], -f)));
     z[k] = s;
     fb[k] = f;
+}
+
+// The y and z passes in one launch of 32-thread blocks: blocks [0, nA) take
+// row groups of A, the rest take 32 columns of B each (the two passes are
+// independent, so they run side by side).  kMode as winograd_kernel's.
+template <int kMode>
+__global__ void __launch_bounds__(32) terms_kernel(int64_t N, int64_t P, int64_t M, const double *__restrict__ A,
+                                                   int64_t lda, const double *__restrict__ B, int64_t ldb,
+                                                   double *__restrict__ y, double *__restrict__ z,
+                                                   unsigned long long *norm_bits, int32_t *__restrict__ ea,
+                                                   int32_t *__restrict__ fb, int64_t nA) {
+    const int64_t blk = blockIdx.x;
+    if (blk < nA) {
+        if constexpr (kMode == 2)
+            a_terms_rowcol_rows(blk, N, P, A, lda, y, ea);
+        else
+            a_terms_rows<kMode == 1>(blk, N, P, A, lda, y, norm_bits);
+        return;
+    }
+    const int64_t k = (blk - nA) * 32 + threadIdx.x;
+    if constexpr (kMode == 2)
+        b_terms_rowcol_col(k, P, M, B, ldb, z, fb);
+    else
+        b_terms_col(k, P, M, B, ldb, z);
 }
 
 // Smallest lambda with 1/2 <= 4^lambda a / b <= 2, from frexp pairs (exact).
@@ -343,35 +367,27 @@ int run_winograd(int64_t N, int64_t P, int64_t M, const double *A, int64_t lda, 
     if (mode == 1) {
         cudaError_t e = cudaMemsetAsync(norms, 0, 2 * sizeof(double), st);
         if (e != cudaSuccess) return cuda_fail(e, "mm_winograd_scaled");
-        rc = launch("winograd_a_terms_norm", st, [&] {
-            a_terms_kernel<true><<<(unsigned)ceil_div(N, kRows), 32, 0, st>>>(N, P, A, lda, y,
-                                                                             (unsigned long long *)norms);
-        });
-        if (rc) return rc;
         if (P > 0) {
             // ||B||_inf into norms[1] (NormInf over the rows of B).
             rc = run_norm_inf(P, M, B, ldb, norms + 1, st);
             if (rc) return rc;
         }
-    } else if (mode == 2) {
-        rc = launch("winograd_a_terms_rowcol", st, [&] {
-            a_terms_rowcol_kernel<<<(unsigned)ceil_div(N, kRows), 32, 0, st>>>(N, P, A, lda, y, ea);
-        });
-        if (rc) return rc;
-    } else {
-        rc = launch("winograd_a_terms", st, [&] {
-            a_terms_kernel<false><<<(unsigned)ceil_div(N, kRows), 32, 0, st>>>(N, P, A, lda, y, nullptr);
-        });
+    }
+    {
+        const int64_t nA = ceil_div(N, (int64_t)kRows), nB = ceil_div(M, (int64_t)32);
+        const unsigned g = (unsigned)(nA + nB);
+        unsigned long long *nb = mode == 1 ? (unsigned long long *)norms : nullptr;
+        rc = launch(mode == 2 ? "winograd_terms_rowcol" : mode == 1 ? "winograd_terms_norm" : "winograd_terms", st,
+                    [&] {
+                        if (mode == 2)
+                            terms_kernel<2><<<g, 32, 0, st>>>(N, P, M, A, lda, B, ldb, y, z, nb, ea, fb, nA);
+                        else if (mode == 1)
+                            terms_kernel<1><<<g, 32, 0, st>>>(N, P, M, A, lda, B, ldb, y, z, nb, ea, fb, nA);
+                        else
+                            terms_kernel<0><<<g, 32, 0, st>>>(N, P, M, A, lda, B, ldb, y, z, nb, ea, fb, nA);
+                    });
         if (rc) return rc;
     }
-    if (mode == 2)
-        rc = launch("winograd_b_terms_rowcol", st, [&] {
-            b_terms_rowcol_kernel<<<(unsigned)ceil_div(M, 128), 128, 0, st>>>(P, M, B, ldb, z, fb);
-        });
-    else
-        rc = launch("winograd_b_terms", st,
-                    [&] { b_terms_kernel<<<(unsigned)ceil_div(M, 128), 128, 0, st>>>(P, M, B, ldb, z); });
-    if (rc) return rc;
     static const int sides[3] = {64, 32, 16};
     const int T = pick_tile(N, M, sides, 3);
     dim3 grid((unsigned)ceil_div(M, T), (unsigned)ceil_div(N, T));
