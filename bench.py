@@ -66,9 +66,9 @@ def parse():
     ap.add_argument("--grouped-only", type=int, default=0, metavar="COUNT",
                     help="profiling runs: only the grouped launch of COUNT serving-shaped products")
     ap.add_argument("--method", default="",
-                    help="profiling runs: one FP64 method at n = --n, a warm-up and one timed call (naive, kahan, "
+                    help="profiling runs: one method at n = --n, a warm-up and one timed call (naive, kahan, "
                          "naive_unrolled_4, winograd, strassen, strassen_winograd, strassen_paper, "
-                         "strassen_winograd_paper, strassen_emulated_1)")
+                         "strassen_winograd_paper, strassen_emulated_1, emulated_8)")
     ap.add_argument("--no-cpu-table", action="store_true", help="skip the CPU oracle's run of the paper's test")
     ap.add_argument("--cpu-table-repeats", type=int, default=10)
     args = ap.parse_args()
@@ -1171,11 +1171,12 @@ def main():
                  "strassen_winograd": lambda a, b: mm.strassen_winograd(a, b),
                  "strassen_paper": lambda a, b: mm.strassen(a, b, cutoff=0),
                  "strassen_winograd_paper": lambda a, b: mm.strassen_winograd(a, b, cutoff=0),
-                 "strassen_emulated_1": lambda a, b: mm.strassen_emulated(a, b, variant=1, levels=1, nslices=8)}
+                 "strassen_emulated_1": lambda a, b: mm.strassen_emulated(a, b, variant=1, levels=1, nslices=8),
+                 "emulated_8": lambda a, b: mm.emulated(a, b, nslices=8)}
         if args.method not in calls:
             raise SystemExit(f"unknown --method {args.method}")
         n = args.n
-        if args.method.startswith("strassen_emulated"):  # the bench's log-uniform inputs
+        if "emulated" in args.method:  # the bench's log-uniform inputs
             a = torch.from_numpy(S.loguniform(n, n, S.stream_seed(3, 0))).cuda()
             b = torch.from_numpy(S.loguniform(n, n, S.stream_seed(3, 1))).cuda()
         else:
